@@ -1,0 +1,178 @@
+/*
+ * akra.h -- C ABI of the GB300 (sm_103a) implementation of the AKRA 3.0 hot path:
+ * the matrix-free normal-equation operator  H = A^T N^{-1} A  (+ λ_eff I) and the
+ * (preconditioned) conjugate-gradient solve built on it.
+ *
+ *   A  : E/B convergence harmonics --KS kernel D_l (Eq. 3)--> spin-2 harmonics
+ *        (Eq. 2) --spin-2 synthesis (Eq. 1)--> shear (γ1, γ2) on HEALPix pixels
+ *   N^-1: per-pixel inverse noise variance, zero off the mask (Eq. 4, Eqs. 17-19)
+ *   A^T: the exact transpose of A (Sec. II B, "the adjoint reverses this sequence")
+ *   CG : Sec. II B "The inversion problem"; regulariser λ_eff I (Eq. 14);
+ *        scalar preconditioner P = (<M^2 N^-1> + λ_eff)^{-1} I (Eq. 15).
+ *
+ * Conventions (shared by every entry point)
+ *   - nside: HEALPix resolution (1 <= nside <= 2048); npix = 12 nside^2; pixels in
+ *     RING order.  lmax: band limit, 2 <= lmax <= 4 nside.
+ *   - harmonic vectors ("alm"): [R][2][ntri] complex, ntri = (lmax+1)(lmax+2)/2,
+ *     index [r][field][m(2 lmax + 1 - m)/2 + l] for 0 <= m <= l <= lmax, field 0 = E,
+ *     1 = B; complex = interleaved (re, im).  The fields are real on the sphere
+ *     (x_{l,-m} = (-1)^m conj x_lm), so only m >= 0 is stored; Im(x_{l0}) is ignored on
+ *     input and written as 0 on output.  Harmonic inner products count every real
+ *     degree of freedom: <x,y> = Σ_l [x_l0 y_l0 + 2 Re Σ_{m>0} x_lm conj(y_lm)].
+ *   - maps: [R][2][npix] real, component 0 = γ1, 1 = γ2.
+ *   - precision: AKRA_F64 -> double / complex double; AKRA_F32 -> float /
+ *     complex float; AKRA_MIXED (cg_solve only) -> FP64 inputs and outputs, FP32 inner
+ *     iterations, FP64 outer residual.
+ *   - all array arguments named d_* are DEVICE pointers owned by the caller, 256-byte
+ *     aligned as returned by cudaMalloc (or a torch CUDA tensor), contiguous.
+ *   - stream: a cudaStream_t passed as void* (NULL = legacy default stream).  Calls are
+ *     asynchronous on that stream unless stated otherwise.
+ *   - errors are returned as akra_status, never by exception or abort;
+ *     akra_last_error() returns a thread-local message for the last failure.
+ *   - a plan is not thread-safe: calls on one plan must be serialised by the caller.
+ */
+#ifndef AKRA_H
+#define AKRA_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct akra_plan_s *akra_plan;
+
+typedef enum {
+    AKRA_OK = 0,
+    AKRA_EINVAL = 1,     /* bad argument (sizes, null pointer, precision) */
+    AKRA_ENOMEM = 2,     /* device or host allocation failed */
+    AKRA_ECUDA = 3,      /* a CUDA runtime call failed */
+    AKRA_ENOCONV = 4,    /* CG reached maxiter before the tolerance */
+    AKRA_ENUMERIC = 5,   /* NaN/Inf or a non-positive curvature <p,Hp> in CG */
+    AKRA_ETIMEOUT = 6,   /* the host-side wall-clock budget of a blocking call ran out */
+    AKRA_ENOWEIGHTS = 7  /* an operator needing N^-1 was called before set_weights */
+} akra_status;
+
+typedef enum { AKRA_F64 = 0, AKRA_F32 = 1, AKRA_MIXED = 2 } akra_prec;
+
+/* Result of a CG solve (host struct, filled by akra_cg_solve / akra_cg_solve_b). */
+typedef struct {
+    int iters;            /* CG iterations (AKRA_MIXED: all inner FP32 iterations) */
+    int outer;            /* AKRA_MIXED: outer refinement steps; 0 otherwise */
+    int h_applies_f64;    /* FP64 operator applications (H, and the A^T of b) */
+    int h_applies_f32;    /* FP32 operator applications */
+    double relres;        /* max over RHS of the final relative residual ||b - H x|| / ||b||:
+                             F64/MIXED: recomputed in FP64 at exit; F32: recursive */
+    int status;           /* worst akra_status over the RHS */
+    double *relres_rhs;   /* optional caller-owned host array [R] (may be NULL) */
+    int *iters_rhs;       /* optional caller-owned host array [R] (may be NULL) */
+} akra_cg_info;
+
+/* Read-only description of a plan. */
+typedef struct {
+    int nside, lmax, nring, nunit;    /* nunit = 2 nside ring pairs (north/south + equator) */
+    long long npix, ntri;
+    int has_weights;
+    int n_active_rings;               /* rings with any N^-1 > 0 */
+    double lambda, lambda_eff;        /* λ and λ_eff = λ <N^-1>_M  (Eq. 14) */
+    double precond;                   /* scalar P of Eq. 15 */
+    double omega;                     /* pixel area 4π/npix folded into W = ω M N^-1 */
+    size_t device_bytes;              /* device memory currently held by the plan */
+    long long kernel_launches;        /* kernels this plan has launched so far (host count;
+                                         a captured CG iteration counts its 7 kernels) */
+} akra_plan_desc;
+
+/* Create a plan for (nside, lmax): HEALPix ring tables, spin-2 recurrence tables, ring
+ * FFT twiddles (all on the current device).  *out receives an opaque handle owned by
+ * the library; free it with akra_plan_destroy.  Blocking.
+ * Errors: EINVAL for nside outside [1,2048], lmax outside [2, 4 nside] or out == NULL;
+ * ENOMEM; ECUDA. */
+akra_status akra_plan_create(int nside, int lmax, akra_plan *out);
+
+/* Release every device and host resource of the plan (NULL is ignored).  Blocking. */
+void akra_plan_destroy(akra_plan plan);
+
+/* Thread-local description of the last error on this thread ("" if none). */
+const char *akra_last_error(void);
+
+/* Library version string. */
+const char *akra_version(void);
+
+/* Fill *out with the plan's sizes and weight statistics.  Blocking. */
+akra_status akra_plan_describe(akra_plan plan, akra_plan_desc *out);
+
+/* Set the pixel weights from d_ninv [npix] (double, N^-1_p >= 0, 0 off the mask; the mask
+ * is M_p = [N^-1_p > 0]).  Stores W_p = ω M_p N^-1_p (ω = 4π/npix) in FP64 and FP32,
+ * λ_eff = lambda · mean_{M}(N^-1) (Eq. 14) and P = 1/(mean_all(M N^-1) + λ_eff) (Eq. 15),
+ * and the list of rings with any nonzero weight (the only rings H needs).
+ * Blocking (reads the statistics back).  Errors: EINVAL (NULL, lambda < 0, negative or
+ * non-finite N^-1), ECUDA. */
+akra_status akra_plan_set_weights(akra_plan plan, const double *d_ninv, double lambda,
+                                  void *stream);
+
+/* Spin-2 synthesis (Eqs. 1-2): γ1 + iγ2 = Σ_{l>=2} Σ_m γ_{2,lm} 2Y_lm with
+ * γ_{2,lm} = -(a_E,lm + i a_B,lm).  d_alm [R][2][ntri] (E, B) -> d_map [R][2][npix].
+ * prec: F64 or F32.  Errors: EINVAL, ENOMEM (workspace), ECUDA. */
+akra_status akra_synth_spin2(akra_plan plan, akra_prec prec, const void *d_alm, void *d_map,
+                             int R, void *stream);
+
+/* Exact transpose of akra_synth_spin2 in the real-dof inner product:
+ * (a_E, a_B) = (-(g+h)/2, (i/2)(g-h)) with g_lm = Σ_p (u1+iu2)_p 2Y*_lm(p) and
+ * h_lm = Σ_p (u1-iu2)_p (-2)Y*_lm(p).  d_map [R][2][npix] -> d_alm [R][2][ntri].
+ * No quadrature weights (this is A^T's SHT half, not an inverse transform). */
+akra_status akra_adjoint_synth_spin2(akra_plan plan, akra_prec prec, const void *d_map,
+                                     void *d_alm, int R, void *stream);
+
+/* Forward operator A (Eq. 7 with Eqs. 2-3): (κ_E, κ_B) -> shear maps,
+ * a_E = -D_l κ_E, a_B = -D_l κ_B, then synthesis.  weighted != 0 multiplies the maps by
+ * W = ω M N^-1 (needs set_weights, else ENOWEIGHTS). */
+akra_status akra_apply_A(akra_plan plan, akra_prec prec, const void *d_x, void *d_map,
+                         int weighted, int R, void *stream);
+
+/* Transpose A^T: maps -> (κ_E, κ_B); weighted != 0 multiplies the maps by W first
+ * (so weighted A^T y = A^T W y = b of Eq. 8 up to the ω folded into W). */
+akra_status akra_apply_At(akra_plan plan, akra_prec prec, const void *d_map, void *d_x,
+                          int weighted, int R, void *stream);
+
+/* y = H x = A^T W A x + λ_eff x  (Sec. II B; Eq. 14 operator).  d_x, d_y [R][2][ntri].
+ * Only rings with nonzero W are transformed (the others contribute exactly zero).
+ * d_x and d_y must not overlap.  Errors: EINVAL, ENOWEIGHTS, ENOMEM, ECUDA. */
+akra_status akra_apply_H(akra_plan plan, akra_prec prec, const void *d_x, void *d_y, int R,
+                         void *stream);
+
+/* Solve (A^T W A + λ_eff I) x = A^T W y by PCG with x_0 = 0 (Eq. 14 estimator), stopping
+ * when ||r||/||b|| < tol for every RHS (or maxiter).  d_shear [R][2][npix] (the pixel
+ * shear y), d_x [R][2][ntri] output.  prec F64: everything FP64.  F32: everything FP32
+ * (dot products accumulated in FP64).  MIXED: FP64 in/out, b and the outer residual in
+ * FP64, inner CG in FP32 (iterative refinement).  The loop runs on the device (one CUDA
+ * graph per iteration block); the host only polls a device status.  Blocking; info may be
+ * NULL.  Returns the worst per-RHS status: OK, ENOCONV, ENUMERIC, ETIMEOUT (wall-clock
+ * budget from akra_set_timeout), or an argument/CUDA error. */
+akra_status akra_cg_solve(akra_plan plan, akra_prec prec, const void *d_shear, void *d_x,
+                          int R, double tol, int maxiter, akra_cg_info *info, void *stream);
+
+/* As akra_cg_solve but for a given harmonic right-hand side d_b [R][2][ntri]
+ * (used for the implicit-adjoint solve of a gradient).  Same precisions and errors. */
+akra_status akra_cg_solve_b(akra_plan plan, akra_prec prec, const void *d_b, void *d_x,
+                            int R, double tol, int maxiter, akra_cg_info *info, void *stream);
+
+/* Host-side wall-clock budget (seconds, > 0) for blocking solves; default 3600. */
+akra_status akra_set_timeout(double seconds);
+
+/* Pick the Legendre tile shape (units per thread, threads per block) for this plan,
+ * precision and RHS count by timing the candidates on `stream`; the choice is cached in
+ * the plan and used by every later call with the same (prec, R).  Blocking. */
+akra_status akra_autotune(akra_plan plan, akra_prec prec, int R, void *stream);
+
+/* Time the four stages of one H application (Legendre synthesis, ring FFT x W x FFT,
+ * Legendre adjoint, epilogue) with CUDA events on `stream`, averaged over `reps` runs after
+ * one warm-up, on the plan's own scratch input.  ms_out[0..3] receive the per-stage
+ * milliseconds and ms_out[4] the whole H.  Blocking.  Errors: EINVAL, ENOWEIGHTS, ENOMEM,
+ * ECUDA. */
+akra_status akra_time_H_stages(akra_plan plan, akra_prec prec, int R, int reps, void *stream,
+                               double *ms_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AKRA_H */

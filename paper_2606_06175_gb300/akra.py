@@ -1,0 +1,272 @@
+"""Thin ctypes binding of libakra.so (the C ABI in include/akra.h).
+
+Argument marshalling only: every step of the operator chain and of the solver runs in the
+library's CUDA kernels.  Tensors are torch CUDA tensors (device memory and streams); the
+functions keep the C names.  There is no CPU fallback: without the built library on a CUDA
+device every call raises.
+
+Layouts (see include/akra.h):
+  alm  [R, 2, ntri] complex128 (F64) / complex64 (F32), packed m-major, (E, B)
+  maps [R, 2, npix] float64 / float32, RING order, (γ1, γ2)
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+from . import build as _build
+
+F64, F32, MIXED = 0, 1, 2
+_STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOCONV", 5: "ENUMERIC",
+           6: "ETIMEOUT", 7: "ENOWEIGHTS"}
+
+
+class AkraError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__("%s: %s" % (_STATUS.get(status, status), msg))
+        self.status = status
+
+
+class CgInfo(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("outer", ctypes.c_int), ("h_applies_f64", ctypes.c_int),
+                ("h_applies_f32", ctypes.c_int), ("relres", ctypes.c_double), ("status", ctypes.c_int),
+                ("relres_rhs", ctypes.POINTER(ctypes.c_double)), ("iters_rhs", ctypes.POINTER(ctypes.c_int))]
+
+
+class PlanDesc(ctypes.Structure):
+    _fields_ = [("nside", ctypes.c_int), ("lmax", ctypes.c_int), ("nring", ctypes.c_int),
+                ("nunit", ctypes.c_int), ("npix", ctypes.c_longlong), ("ntri", ctypes.c_longlong),
+                ("has_weights", ctypes.c_int), ("n_active_rings", ctypes.c_int),
+                ("lambda_", ctypes.c_double), ("lambda_eff", ctypes.c_double),
+                ("precond", ctypes.c_double), ("omega", ctypes.c_double),
+                ("device_bytes", ctypes.c_size_t), ("kernel_launches", ctypes.c_longlong)]
+
+
+EXPORTS = ["akra_plan_create", "akra_plan_destroy", "akra_last_error", "akra_version",
+           "akra_plan_describe", "akra_plan_set_weights", "akra_synth_spin2",
+           "akra_adjoint_synth_spin2", "akra_apply_A", "akra_apply_At", "akra_apply_H",
+           "akra_cg_solve", "akra_cg_solve_b", "akra_set_timeout", "akra_autotune",
+           "akra_time_H_stages"]
+
+_lib_handle = None
+
+
+def library_path() -> str:
+    return _build.OUT
+
+
+def load(build_if_missing: bool = False):
+    """Load libakra.so (raises if it is missing; never falls back to anything else)."""
+    global _lib_handle
+    if _lib_handle is not None:
+        return _lib_handle
+    path = library_path()
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise RuntimeError("libakra.so is not built (run paper_2606_06175_gb300/build.py)")
+        _build.build()
+    lib = ctypes.CDLL(path)
+    vp, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    sig = {
+        "akra_plan_create": ([i, i, ctypes.POINTER(vp)], i),
+        "akra_plan_destroy": ([vp], None),
+        "akra_last_error": ([], ctypes.c_char_p),
+        "akra_version": ([], ctypes.c_char_p),
+        "akra_plan_describe": ([vp, ctypes.POINTER(PlanDesc)], i),
+        "akra_plan_set_weights": ([vp, vp, d, vp], i),
+        "akra_synth_spin2": ([vp, i, vp, vp, i, vp], i),
+        "akra_adjoint_synth_spin2": ([vp, i, vp, vp, i, vp], i),
+        "akra_apply_A": ([vp, i, vp, vp, i, i, vp], i),
+        "akra_apply_At": ([vp, i, vp, vp, i, i, vp], i),
+        "akra_apply_H": ([vp, i, vp, vp, i, vp], i),
+        "akra_cg_solve": ([vp, i, vp, vp, i, d, i, ctypes.POINTER(CgInfo), vp], i),
+        "akra_cg_solve_b": ([vp, i, vp, vp, i, d, i, ctypes.POINTER(CgInfo), vp], i),
+        "akra_set_timeout": ([d], i),
+        "akra_autotune": ([vp, i, i, vp], i),
+        "akra_time_H_stages": ([vp, i, i, i, vp, ctypes.POINTER(ctypes.c_double)], i),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    _lib_handle = lib
+    return lib
+
+
+def _check(status: int):
+    if status != 0:
+        raise AkraError(status, load().akra_last_error().decode())
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t: torch.Tensor):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Plan:
+    """Owning handle of an akra_plan (nside, lmax)."""
+
+    def __init__(self, handle, nside, lmax):
+        self.handle = handle
+        self.nside = nside
+        self.lmax = lmax
+        self.npix = 12 * nside * nside
+        self.ntri = (lmax + 1) * (lmax + 2) // 2
+
+    def close(self):
+        if self.handle:
+            load().akra_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _cdtype(prec):
+    return torch.complex128 if prec == F64 else torch.complex64
+
+
+def _rdtype(prec):
+    return torch.float64 if prec == F64 else torch.float32
+
+
+def _need(t: torch.Tensor, shape, dtype, name):
+    if not (t.is_cuda and t.dtype == dtype and t.is_contiguous() and tuple(t.shape) == tuple(shape)):
+        raise ValueError("%s must be a contiguous CUDA %s tensor of shape %s (got %s %s %s)"
+                         % (name, dtype, tuple(shape), t.device, t.dtype, tuple(t.shape)))
+
+
+def akra_version() -> str:
+    return load().akra_version().decode()
+
+
+def akra_plan_create(nside: int, lmax: int) -> Plan:
+    h = ctypes.c_void_p()
+    _check(load().akra_plan_create(nside, lmax, ctypes.byref(h)))
+    return Plan(h, nside, lmax)
+
+
+def akra_plan_destroy(plan: Plan):
+    plan.close()
+
+
+def akra_plan_describe(plan: Plan) -> dict:
+    d = PlanDesc()
+    _check(load().akra_plan_describe(plan.handle, ctypes.byref(d)))
+    return {f: getattr(d, f) for f, _ in PlanDesc._fields_}
+
+
+def akra_plan_set_weights(plan: Plan, ninv: torch.Tensor, lam: float = 1e-3, stream=None):
+    _need(ninv, (plan.npix,), torch.float64, "ninv")
+    _check(load().akra_plan_set_weights(plan.handle, _ptr(ninv), float(lam), _stream(stream)))
+
+
+def akra_synth_spin2(plan: Plan, prec: int, alm: torch.Tensor, out: torch.Tensor = None, stream=None):
+    R = alm.shape[0]
+    _need(alm, (R, 2, plan.ntri), _cdtype(prec), "alm")
+    if out is None:
+        out = torch.empty((R, 2, plan.npix), dtype=_rdtype(prec), device=alm.device)
+    _need(out, (R, 2, plan.npix), _rdtype(prec), "out")
+    _check(load().akra_synth_spin2(plan.handle, prec, _ptr(alm), _ptr(out), R, _stream(stream)))
+    return out
+
+
+def akra_adjoint_synth_spin2(plan: Plan, prec: int, maps: torch.Tensor, out: torch.Tensor = None,
+                             stream=None):
+    R = maps.shape[0]
+    _need(maps, (R, 2, plan.npix), _rdtype(prec), "maps")
+    if out is None:
+        out = torch.empty((R, 2, plan.ntri), dtype=_cdtype(prec), device=maps.device)
+    _need(out, (R, 2, plan.ntri), _cdtype(prec), "out")
+    _check(load().akra_adjoint_synth_spin2(plan.handle, prec, _ptr(maps), _ptr(out), R, _stream(stream)))
+    return out
+
+
+def akra_apply_A(plan: Plan, prec: int, x: torch.Tensor, weighted: bool = False, out=None, stream=None):
+    R = x.shape[0]
+    _need(x, (R, 2, plan.ntri), _cdtype(prec), "x")
+    if out is None:
+        out = torch.empty((R, 2, plan.npix), dtype=_rdtype(prec), device=x.device)
+    _need(out, (R, 2, plan.npix), _rdtype(prec), "out")
+    _check(load().akra_apply_A(plan.handle, prec, _ptr(x), _ptr(out), int(weighted), R, _stream(stream)))
+    return out
+
+
+def akra_apply_At(plan: Plan, prec: int, maps: torch.Tensor, weighted: bool = False, out=None,
+                  stream=None):
+    R = maps.shape[0]
+    _need(maps, (R, 2, plan.npix), _rdtype(prec), "maps")
+    if out is None:
+        out = torch.empty((R, 2, plan.ntri), dtype=_cdtype(prec), device=maps.device)
+    _need(out, (R, 2, plan.ntri), _cdtype(prec), "out")
+    _check(load().akra_apply_At(plan.handle, prec, _ptr(maps), _ptr(out), int(weighted), R,
+                                _stream(stream)))
+    return out
+
+
+def akra_apply_H(plan: Plan, prec: int, x: torch.Tensor, out: torch.Tensor = None, stream=None):
+    R = x.shape[0]
+    _need(x, (R, 2, plan.ntri), _cdtype(prec), "x")
+    if out is None:
+        out = torch.empty_like(x)
+    _need(out, (R, 2, plan.ntri), _cdtype(prec), "out")
+    _check(load().akra_apply_H(plan.handle, prec, _ptr(x), _ptr(out), R, _stream(stream)))
+    return out
+
+
+def _solve(fn, plan, prec, src, out, R, tol, maxiter, stream, raise_on_noconv):
+    if out is None:
+        out = torch.empty((R, 2, plan.ntri), dtype=_cdtype(F64 if prec == MIXED else prec), device=src.device)
+    rel = (ctypes.c_double * R)()
+    its = (ctypes.c_int * R)()
+    info = CgInfo()
+    info.relres_rhs = rel
+    info.iters_rhs = its
+    st = fn(plan.handle, prec, _ptr(src), _ptr(out), R, float(tol), int(maxiter), ctypes.byref(info),
+            _stream(stream))
+    if st != 0 and (raise_on_noconv or st not in (4, 5)):
+        _check(st)
+    res = {"iters": info.iters, "outer": info.outer, "h_applies_f64": info.h_applies_f64,
+           "h_applies_f32": info.h_applies_f32, "relres": info.relres, "status": st,
+           "relres_rhs": list(rel), "iters_rhs": list(its)}
+    return out, res
+
+
+def akra_cg_solve(plan: Plan, prec: int, shear: torch.Tensor, out=None, tol: float = 1e-6,
+                  maxiter: int = 1000, stream=None, raise_on_noconv: bool = False):
+    R = shear.shape[0]
+    _need(shear, (R, 2, plan.npix), torch.float32 if prec == F32 else torch.float64, "shear")
+    return _solve(load().akra_cg_solve, plan, prec, shear, out, R, tol, maxiter, stream, raise_on_noconv)
+
+
+def akra_cg_solve_b(plan: Plan, prec: int, b: torch.Tensor, out=None, tol: float = 1e-6,
+                    maxiter: int = 1000, stream=None, raise_on_noconv: bool = False):
+    R = b.shape[0]
+    _need(b, (R, 2, plan.ntri), _cdtype(F64 if prec == MIXED else prec), "b")
+    return _solve(load().akra_cg_solve_b, plan, prec, b, out, R, tol, maxiter, stream, raise_on_noconv)
+
+
+def akra_set_timeout(seconds: float):
+    _check(load().akra_set_timeout(float(seconds)))
+
+
+def akra_autotune(plan: Plan, prec: int, R: int = 1, stream=None):
+    _check(load().akra_autotune(plan.handle, prec, R, _stream(stream)))
+
+
+def akra_time_H_stages(plan: Plan, prec: int, R: int = 1, reps: int = 3, stream=None) -> dict:
+    """Per-stage milliseconds of one H application (CUDA events on `stream`)."""
+    ms = (ctypes.c_double * 5)()
+    _check(load().akra_time_H_stages(plan.handle, prec, R, reps, _stream(stream), ms))
+    return {"legendre_synth": ms[0], "ring_fft": ms[1], "legendre_adjoint": ms[2],
+            "epilogue": ms[3], "total": ms[4]}

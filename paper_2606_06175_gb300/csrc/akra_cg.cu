@@ -1,0 +1,741 @@
+// akra_cg.cu -- (preconditioned) conjugate gradients on H = A^T W A + λ_eff I
+// (Sec. II B "The inversion problem"; Eq. 14 regulariser; Eq. 15 scalar preconditioner),
+// plain FP64 / FP32 and FP32-inner with FP64 iterative refinement.
+//
+// One CG iteration is a fixed kernel sequence captured once into a CUDA graph:
+//   q = H p  (Legendre synthesis, ring FFT x W x FFT, Legendre adjoint, epilogue + λ_eff p)
+//   <p,q>  -> α = <r,z>/<p,q>                               (FP64 accumulation)
+//   x += α p, r -= α q, <r,r> -> stop test, β                (FP64 accumulation)
+//   p = P r + β p
+// Every kernel returns at once when the device flag `all_done` is set, so the host can
+// launch iterations ahead and only polls the flag (bounded by a wall-clock budget).
+// Dot products use the real-dof metric: <x,y> = Σ_l [x_l0 y_l0 + 2 Re Σ_{m>0} x conj(y)].
+#include <algorithm>
+#include <chrono>
+#include <thread>
+
+#include "akra_internal.cuh"
+
+namespace akra {
+
+struct CgState {          // one per RHS (device)
+    double rz, pq, alpha, beta, rr, bnorm2, relres, tol;
+    int done, iters, status, pad;
+};
+
+struct CgCtl {            // one per solver precision (device)
+    int all_done;         // read by every iteration kernel
+    int counter;          // last-block ticket
+    int maxiter;
+    int R;
+    double precond;
+};
+
+constexpr int RED_NB = 296;    // reduction blocks (2 per SM on 148+ SMs)
+constexpr int RED_NT = 256;
+
+struct CgGraph {
+    cudaGraphExec_t exec = nullptr;
+    unsigned gen = 0;
+};
+
+// ---------------------------------------------------------------------------
+// vector kernels
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ double wdot(long long idx, int L, cx_t<T> a, cx_t<T> b)
+{
+    // m = 0 entries (idx <= L inside a field) count once and are real; m > 0 twice
+    return idx <= L ? (double)a.x * (double)b.x
+                    : 2.0 * ((double)a.x * (double)b.x + (double)a.y * (double)b.y);
+}
+
+// block-reduce one double per RHS into scratch[r * RED_NB + blockIdx.x]; returns true on the
+// last block to finish (which may then read every partial)
+__device__ bool block_partials(double *vals, int R, double *scratch, CgCtl *ctl)
+{
+    __shared__ double sh[RED_NT];
+    __shared__ bool last;
+    for (int r = 0; r < R; r++) {
+        sh[threadIdx.x] = vals[r];
+        __syncthreads();
+        for (int off = RED_NT / 2; off > 0; off >>= 1) {
+            if (threadIdx.x < off) sh[threadIdx.x] += sh[threadIdx.x + off];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) scratch[(size_t)r * RED_NB + blockIdx.x] = sh[0];
+        __syncthreads();
+    }
+    __threadfence();
+    if (threadIdx.x == 0) last = atomicAdd(&ctl->counter, 1) == (int)gridDim.x - 1;
+    __syncthreads();
+    return last;
+}
+
+__device__ double sum_partials(const double *scratch, int r)
+{
+    double s = 0;
+    for (int b = 0; b < RED_NB; b++) s += scratch[(size_t)r * RED_NB + b];
+    return s;
+}
+
+constexpr int kMaxRhsLocal = 64;
+
+// initial state: x = 0, r = b, p = P r, rz = P <r,r>, bnorm2 = <b,b>
+template <typename T>
+__global__ void __launch_bounds__(RED_NT)
+k_cg_init(int L, long long ntri, const cx_t<T> *b, cx_t<T> *x, cx_t<T> *r, cx_t<T> *p, CgState *st,
+          CgCtl *ctl, double *scratch, double tol, int maxiter)
+{
+    const int R = ctl->R;
+    const double P = ctl->precond;
+    double acc[kMaxRhsLocal];
+    for (int q = 0; q < R; q++) acc[q] = 0;
+    const long long n = 2 * ntri;
+    for (int q = 0; q < R; q++) {
+        for (long long i = blockIdx.x * (long long)RED_NT + threadIdx.x; i < n;
+             i += (long long)gridDim.x * RED_NT) {
+            const size_t o = (size_t)q * n + i;
+            const cx_t<T> v = b[o];
+            x[o] = cx_t<T>{0, 0};
+            r[o] = v;
+            p[o] = cx_t<T>{(T)(P * v.x), (T)(P * v.y)};
+            acc[q] += wdot<T>(i % ntri, L, v, v);
+        }
+    }
+    if (block_partials(acc, R, scratch, ctl)) {
+        for (int q = threadIdx.x; q < R; q += RED_NT) {
+            const double bb = sum_partials(scratch, q);
+            CgState s{};
+            s.bnorm2 = bb;
+            s.rr = bb;
+            s.rz = P * bb;
+            s.tol = tol;
+            s.relres = bb > 0 ? 1.0 : 0.0;
+            s.done = bb > 0 ? 0 : 1;
+            s.status = AKRA_OK;
+            if (!isfinite(bb)) {
+                s.done = 1;
+                s.status = AKRA_ENUMERIC;
+            }
+            st[q] = s;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int all = 1;
+            for (int q = 0; q < R; q++) all &= st[q].done;
+            ctl->all_done = all;
+            ctl->maxiter = maxiter;
+            ctl->counter = 0;
+        }
+    }
+}
+
+// <p, q> -> α
+template <typename T>
+__global__ void __launch_bounds__(RED_NT)
+k_cg_dot_pq(int L, long long ntri, const cx_t<T> *p, const cx_t<T> *q, CgState *st, CgCtl *ctl,
+            double *scratch)
+{
+    if (ctl->all_done) return;
+    const int R = ctl->R;
+    double acc[kMaxRhsLocal];
+    const long long n = 2 * ntri;
+    for (int r = 0; r < R; r++) {
+        acc[r] = 0;
+        if (st[r].done) continue;
+        for (long long i = blockIdx.x * (long long)RED_NT + threadIdx.x; i < n;
+             i += (long long)gridDim.x * RED_NT) {
+            const size_t o = (size_t)r * n + i;
+            acc[r] += wdot<T>(i % ntri, L, p[o], q[o]);
+        }
+    }
+    if (block_partials(acc, R, scratch, ctl)) {
+        for (int r = threadIdx.x; r < R; r += RED_NT) {
+            if (st[r].done) continue;
+            const double pq = sum_partials(scratch, r);
+            st[r].pq = pq;
+            if (!(pq > 0) || !isfinite(pq)) {
+                st[r].status = AKRA_ENUMERIC;
+                st[r].done = 1;
+                st[r].alpha = 0;
+            } else {
+                st[r].alpha = st[r].rz / pq;
+            }
+        }
+        if (threadIdx.x == 0) ctl->counter = 0;
+    }
+}
+
+// x += α p, r -= α q, <r,r> -> relres, stop test, β
+template <typename T>
+__global__ void __launch_bounds__(RED_NT)
+k_cg_update_xr(int L, long long ntri, const cx_t<T> *p, const cx_t<T> *q, cx_t<T> *x, cx_t<T> *rv,
+               CgState *st, CgCtl *ctl, double *scratch)
+{
+    if (ctl->all_done) return;
+    const int R = ctl->R;
+    double acc[kMaxRhsLocal];
+    const long long n = 2 * ntri;
+    for (int r = 0; r < R; r++) {
+        acc[r] = 0;
+        if (st[r].done) continue;
+        const T a = (T)st[r].alpha;
+        for (long long i = blockIdx.x * (long long)RED_NT + threadIdx.x; i < n;
+             i += (long long)gridDim.x * RED_NT) {
+            const size_t o = (size_t)r * n + i;
+            const cx_t<T> pv = p[o], qv = q[o];
+            cx_t<T> xv = x[o], rr = rv[o];
+            xv.x = fma(a, pv.x, xv.x);
+            xv.y = fma(a, pv.y, xv.y);
+            rr.x = fma(-a, qv.x, rr.x);
+            rr.y = fma(-a, qv.y, rr.y);
+            x[o] = xv;
+            rv[o] = rr;
+            acc[r] += wdot<T>(i % ntri, L, rr, rr);
+        }
+    }
+    if (block_partials(acc, R, scratch, ctl)) {
+        const double P = ctl->precond;
+        for (int r = threadIdx.x; r < R; r += RED_NT) {
+            CgState s = st[r];
+            if (s.done) continue;
+            const double rr = sum_partials(scratch, r);
+            s.rr = rr;
+            s.iters += 1;
+            s.relres = sqrt(rr / s.bnorm2);
+            const double rz_new = P * rr;
+            s.beta = rz_new / s.rz;
+            s.rz = rz_new;
+            if (!isfinite(rr)) {
+                s.status = AKRA_ENUMERIC;
+                s.done = 1;
+            } else if (s.relres < s.tol) {
+                s.done = 1;
+            } else if (s.iters >= ctl->maxiter) {
+                s.status = AKRA_ENOCONV;
+                s.done = 1;
+            }
+            st[r] = s;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int all = 1;
+            for (int r = 0; r < R; r++) all &= st[r].done;
+            ctl->all_done = all;
+            ctl->counter = 0;
+        }
+    }
+}
+
+// p = P r + β p
+template <typename T>
+__global__ void __launch_bounds__(RED_NT)
+k_cg_update_p(long long ntri, const cx_t<T> *rv, cx_t<T> *p, const CgState *st, const CgCtl *ctl)
+{
+    if (ctl->all_done) return;
+    const int R = ctl->R;
+    const T P = (T)ctl->precond;
+    const long long n = 2 * ntri;
+    for (int r = 0; r < R; r++) {
+        if (st[r].done) continue;
+        const T b = (T)st[r].beta;
+        for (long long i = blockIdx.x * (long long)RED_NT + threadIdx.x; i < n;
+             i += (long long)gridDim.x * RED_NT) {
+            const size_t o = (size_t)r * n + i;
+            const cx_t<T> rr = rv[o];
+            cx_t<T> pv = p[o];
+            pv.x = fma(b, pv.x, P * rr.x);
+            pv.y = fma(b, pv.y, P * rr.y);
+            p[o] = pv;
+        }
+    }
+}
+
+// out = b - h; per-RHS ||out||^2 and ||b||^2 into res[2r], res[2r+1] (FP64 accumulation)
+template <typename T>
+__global__ void __launch_bounds__(RED_NT)
+k_residual(int L, long long ntri, int R, const cx_t<T> *b, const cx_t<T> *h, cx_t<T> *out,
+           double *res, CgCtl *ctl, double *scratch)
+{
+    double acc[2 * kMaxRhsLocal];
+    const long long n = 2 * ntri;
+    for (int r = 0; r < R; r++) {
+        acc[2 * r] = acc[2 * r + 1] = 0;
+        for (long long i = blockIdx.x * (long long)RED_NT + threadIdx.x; i < n;
+             i += (long long)gridDim.x * RED_NT) {
+            const size_t o = (size_t)r * n + i;
+            const cx_t<T> bv = b[o], hv = h[o];
+            const cx_t<T> d{bv.x - hv.x, bv.y - hv.y};
+            if (out) out[o] = d;
+            acc[2 * r] += wdot<T>(i % ntri, L, d, d);
+            acc[2 * r + 1] += wdot<T>(i % ntri, L, bv, bv);
+        }
+    }
+    if (block_partials(acc, 2 * R, scratch, ctl)) {
+        for (int q = threadIdx.x; q < 2 * R; q += RED_NT) res[q] = sum_partials(scratch, q);
+        if (threadIdx.x == 0) ctl->counter = 0;
+    }
+}
+
+// r32 = (float) (r64 * s_r), s_r = 1/||r64_r||  (per RHS scale from res[2r])
+__global__ void k_cast_scaled(long long n, int R, const double2 *r64, const double *res, float2 *r32)
+{
+    for (int r = 0; r < R; r++) {
+        const double nr = sqrt(res[2 * r]);
+        const double s = nr > 0 ? 1.0 / nr : 0.0;
+        for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+             i += (long long)gridDim.x * blockDim.x) {
+            const double2 v = r64[(size_t)r * n + i];
+            r32[(size_t)r * n + i] = make_float2((float)(v.x * s), (float)(v.y * s));
+        }
+    }
+}
+
+// x64 += ||r64_r|| * d32
+__global__ void k_axpy_mixed(long long n, int R, const float2 *d32, const double *res, double2 *x64)
+{
+    for (int r = 0; r < R; r++) {
+        const double nr = sqrt(res[2 * r]);
+        for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+             i += (long long)gridDim.x * blockDim.x) {
+            const float2 d = d32[(size_t)r * n + i];
+            double2 x = x64[(size_t)r * n + i];
+            x.x += nr * (double)d.x;
+            x.y += nr * (double)d.y;
+            x64[(size_t)r * n + i] = x;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// workspace layout (plan->cg): FP64 region of 5 vectors, FP32 region of 5 vectors
+//   F64 CG:  b x r p q in the FP64 region
+//   F32 CG and the MIXED inner CG: b x r p q in the FP32 region
+//   MIXED outer: b64 x64 r64 t64 in the FP64 region (slots 0..3)
+// plan->red: [CgState R] x 2 precisions, CgCtl x 2, scratch doubles, residual doubles
+// ---------------------------------------------------------------------------
+struct CgBufs {
+    void *v64[5];
+    void *v32[5];
+    CgState *st[2];
+    CgCtl *ctl[2];
+    double *scratch;
+    double *res;
+};
+
+static akra_status cg_reserve(akra_plan p, int R, CgBufs &b)
+{
+    if (R > kMaxRhsLocal) {
+        set_error("CG: at most %d right-hand sides per solve", kMaxRhsLocal);
+        return AKRA_EINVAL;
+    }
+    const size_t V64 = (size_t)R * 2 * p->ntri * sizeof(double2);
+    const size_t V32 = (size_t)R * 2 * p->ntri * sizeof(float2);
+    AKRA_TRY(ws_reserve(p, p->cg, 5 * V64 + 5 * V32));
+    const size_t nst = (size_t)kMaxRhsLocal;
+    const size_t red = 2 * nst * sizeof(CgState) + 2 * 64 + (size_t)RED_NB * 2 * nst * sizeof(double) +
+                       2 * nst * sizeof(double);
+    AKRA_TRY(ws_reserve(p, p->red, red));
+    char *c = (char *)p->cg.ptr;
+    for (int i = 0; i < 5; i++) b.v64[i] = c + i * V64;
+    for (int i = 0; i < 5; i++) b.v32[i] = c + 5 * V64 + i * V32;
+    char *d = (char *)p->red.ptr;
+    b.st[0] = (CgState *)d;
+    b.st[1] = (CgState *)(d + nst * sizeof(CgState));
+    b.ctl[0] = (CgCtl *)(d + 2 * nst * sizeof(CgState));
+    b.ctl[1] = (CgCtl *)(d + 2 * nst * sizeof(CgState) + 64);
+    b.scratch = (double *)(d + 2 * nst * sizeof(CgState) + 128);
+    b.res = b.scratch + (size_t)RED_NB * 2 * nst;
+    if (!p->h_pinned) {
+        if (cudaMallocHost(&p->h_pinned, 2 * nst * sizeof(CgState) + 256 + 2 * nst * sizeof(double)) !=
+            cudaSuccess) {
+            cudaGetLastError();
+            set_error("CG: pinned host allocation failed");
+            return AKRA_ENOMEM;
+        }
+    }
+    return AKRA_OK;
+}
+
+template <typename T> struct PrecIdx;
+template <> struct PrecIdx<double> { static constexpr int v = 0; };
+template <> struct PrecIdx<float> { static constexpr int v = 1; };
+
+template <typename T>
+static void **vecs(CgBufs &b) { return PrecIdx<T>::v == 0 ? b.v64 : b.v32; }
+
+// capture (or reuse) the graph of one CG iteration for precision T and R RHS
+template <typename T>
+static akra_status cg_graph(akra_plan p, int R, CgBufs &b, cudaGraphExec_t *out)
+{
+    const long long key = PrecIdx<T>::v * 1000 + R;
+    CgGraph *g = p->graphs.count(key) ? p->graphs[key] : nullptr;
+    if (g && g->exec && g->gen == p->ws_gen) {
+        *out = g->exec;
+        return AKRA_OK;
+    }
+    if (!g) {
+        g = new CgGraph();
+        p->graphs[key] = g;
+    }
+    if (g->exec) {
+        cudaGraphExecDestroy(g->exec);
+        g->exec = nullptr;
+    }
+    // reserve the operator workspaces before capture (no allocation may happen inside)
+    const LegShape s = leg_shape(p, PrecIdx<T>::v == 0 ? AKRA_F64 : AKRA_F32, R);
+    AKRA_TRY(ws_reserve(p, p->phi, (size_t)R * p->nring * (2 * (size_t)p->lmax + 1) * sizeof(cx_t<T>)));
+    const int nch = (p->n_active_units + s.NT * s.P - 1) / (s.NT * s.P);
+    AKRA_TRY(ws_reserve(p, p->partial, (size_t)nch * R * p->ntri * 4 * sizeof(T)));
+    AKRA_TRY(cg_reserve(p, R, b));   // pointers are stable now (nothing grows below)
+    void **v = vecs<T>(b);
+    CgState *st = b.st[PrecIdx<T>::v];
+    CgCtl *ctl = b.ctl[PrecIdx<T>::v];
+    cudaStream_t cs = p->stream;
+    AKRA_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    p->cur_skip = &ctl->all_done;
+    akra_status s1 = op_H<T>(p, v[3], v[4], R, cs);
+    p->cur_skip = nullptr;
+    if (s1 == AKRA_OK) {
+        k_cg_dot_pq<T><<<RED_NB, RED_NT, 0, cs>>>(p->lmax, p->ntri, (const cx_t<T> *)v[3],
+                                                  (const cx_t<T> *)v[4], st, ctl, b.scratch);
+        k_cg_update_xr<T><<<RED_NB, RED_NT, 0, cs>>>(p->lmax, p->ntri, (const cx_t<T> *)v[3],
+                                                     (const cx_t<T> *)v[4], (cx_t<T> *)v[1],
+                                                     (cx_t<T> *)v[2], st, ctl, b.scratch);
+        k_cg_update_p<T><<<RED_NB, RED_NT, 0, cs>>>(p->ntri, (const cx_t<T> *)v[2], (cx_t<T> *)v[3],
+                                                    st, ctl);
+    }
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(cs, &graph);
+    if (s1 != AKRA_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return s1;
+    }
+    AKRA_CUDA_TRY(e);
+    e = cudaGraphInstantiate(&g->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    AKRA_CUDA_TRY(e);
+    g->gen = p->ws_gen;
+    *out = g->exec;
+    return AKRA_OK;
+}
+
+static double g_timeout_s = 3600.0;
+
+// wait for the event with a wall-clock budget (no unbounded device wait)
+static akra_status bounded_wait(cudaEvent_t ev, std::chrono::steady_clock::time_point deadline)
+{
+    for (;;) {
+        const cudaError_t e = cudaEventQuery(ev);
+        if (e == cudaSuccess) return AKRA_OK;
+        if (e != cudaErrorNotReady) {
+            set_error("CG: %s", cudaGetErrorString(e));
+            return AKRA_ECUDA;
+        }
+        if (std::chrono::steady_clock::now() > deadline) {
+            set_error("CG: wall-clock budget exhausted");
+            return AKRA_ETIMEOUT;
+        }
+        std::this_thread::yield();
+    }
+}
+
+// run CG for precision T on the plan-owned vectors (b already in slot 0); returns the per-RHS
+// states in host memory hst[R]
+template <typename T>
+static akra_status cg_run(akra_plan p, int R, CgBufs &b, double tol, int maxiter, CgState *hst,
+                          std::chrono::steady_clock::time_point deadline)
+{
+    cudaGraphExec_t exec;
+    AKRA_TRY(cg_graph<T>(p, R, b, &exec));
+    void **v = vecs<T>(b);
+    CgState *st = b.st[PrecIdx<T>::v];
+    CgCtl *ctl = b.ctl[PrecIdx<T>::v];
+    cudaStream_t cs = p->stream;
+    CgCtl hctl{};
+    hctl.R = R;
+    hctl.precond = p->precond;
+    hctl.maxiter = maxiter;
+    AKRA_CUDA_TRY(cudaMemcpyAsync(ctl, &hctl, sizeof(CgCtl), cudaMemcpyHostToDevice, cs));
+    k_cg_init<T><<<RED_NB, RED_NT, 0, cs>>>(p->lmax, p->ntri, (const cx_t<T> *)v[0], (cx_t<T> *)v[1],
+                                            (cx_t<T> *)v[2], (cx_t<T> *)v[3], st, ctl, b.scratch, tol,
+                                            maxiter);
+    AKRA_CUDA_TRY(cudaGetLastError());
+    p->launches++;
+    int *h_done = (int *)p->h_pinned;
+    int launched = 0;
+    int chunk = 2;
+    while (launched < maxiter) {
+        const int k = std::min(chunk, maxiter - launched);
+        for (int i = 0; i < k; i++) AKRA_CUDA_TRY(cudaGraphLaunch(exec, cs));
+        p->launches += 7LL * k;
+        launched += k;
+        AKRA_CUDA_TRY(cudaMemcpyAsync(h_done, &ctl->all_done, sizeof(int), cudaMemcpyDeviceToHost, cs));
+        AKRA_CUDA_TRY(cudaEventRecord(p->ev_a, cs));
+        AKRA_TRY(bounded_wait(p->ev_a, deadline));
+        if (*h_done) break;
+        chunk = std::min(chunk * 2, 16);
+    }
+    AKRA_CUDA_TRY(cudaMemcpyAsync(hst, st, sizeof(CgState) * R, cudaMemcpyDeviceToHost, cs));
+    AKRA_CUDA_TRY(cudaEventRecord(p->ev_a, cs));
+    AKRA_TRY(bounded_wait(p->ev_a, deadline));
+    return AKRA_OK;
+}
+
+// FP64 (or FP32) true residual of x against b: res[2r] = ||b - Hx||^2, res[2r+1] = ||b||^2
+template <typename T>
+static akra_status true_residual(akra_plan p, int R, CgBufs &b, const void *bv, const void *xv,
+                                 void *tmp, void *rout, double *hres,
+                                 std::chrono::steady_clock::time_point deadline)
+{
+    cudaStream_t cs = p->stream;
+    AKRA_TRY(op_H<T>(p, xv, tmp, R, cs));
+    k_residual<T><<<RED_NB, RED_NT, 0, cs>>>(p->lmax, p->ntri, R, (const cx_t<T> *)bv,
+                                             (const cx_t<T> *)tmp, (cx_t<T> *)rout, b.res,
+                                             b.ctl[PrecIdx<T>::v], b.scratch);
+    AKRA_CUDA_TRY(cudaGetLastError());
+    p->launches++;
+    AKRA_CUDA_TRY(cudaMemcpyAsync(hres, b.res, sizeof(double) * 2 * R, cudaMemcpyDeviceToHost, cs));
+    AKRA_CUDA_TRY(cudaEventRecord(p->ev_a, cs));
+    return bounded_wait(p->ev_a, deadline);
+}
+
+static void fill_info(akra_cg_info *info, int R, const std::vector<double> &relres,
+                      const std::vector<int> &iters, const std::vector<int> &status)
+{
+    if (!info) return;
+    double mx = 0;
+    int worst = AKRA_OK;
+    for (int r = 0; r < R; r++) {
+        mx = std::max(mx, relres[r]);
+        if (status[r] != AKRA_OK && (worst == AKRA_OK || status[r] > worst)) worst = status[r];
+        if (info->relres_rhs) info->relres_rhs[r] = relres[r];
+        if (info->iters_rhs) info->iters_rhs[r] = iters[r];
+    }
+    info->relres = mx;
+    info->status = worst;
+}
+
+// solve H x = b; `bsrc` is the caller's harmonic b, or nullptr when b is already in place
+static akra_status solve_b(akra_plan p, akra_prec prec, const void *bsrc, void *d_x, int R, double tol,
+                           int maxiter, akra_cg_info *info, cudaStream_t user, bool b_in_place,
+                           CgBufs &b, int h64_already)
+{
+    const auto t0 = std::chrono::steady_clock::now();
+    const auto deadline = t0 + std::chrono::microseconds((long long)(g_timeout_s * 1e6));
+    cudaStream_t cs = p->stream;
+    const size_t V64 = (size_t)R * 2 * p->ntri * sizeof(double2);
+    const size_t V32 = (size_t)R * 2 * p->ntri * sizeof(float2);
+    std::vector<double> relres(R, 0.0);
+    std::vector<int> iters(R, 0), status(R, AKRA_OK);
+    std::vector<CgState> hst(R);
+    std::vector<double> hres(2 * R);
+    int h64 = h64_already, h32 = 0, outer = 0, total_iters = 0;
+
+    if (prec == AKRA_F64 || prec == AKRA_F32) {
+        const bool d = prec == AKRA_F64;
+        void **v = d ? b.v64 : b.v32;
+        const size_t V = d ? V64 : V32;
+        if (!b_in_place) AKRA_CUDA_TRY(cudaMemcpyAsync(v[0], bsrc, V, cudaMemcpyDeviceToDevice, cs));
+        akra_status s = d ? cg_run<double>(p, R, b, tol, maxiter, hst.data(), deadline)
+                          : cg_run<float>(p, R, b, tol, maxiter, hst.data(), deadline);
+        if (s != AKRA_OK) return s;
+        for (int r = 0; r < R; r++) {
+            iters[r] = hst[r].iters;
+            status[r] = hst[r].status;
+            relres[r] = hst[r].relres;
+            total_iters = std::max(total_iters, hst[r].iters);
+        }
+        (d ? h64 : h32) += total_iters;
+        if (d) {
+            // report the true FP64 residual at exit
+            AKRA_TRY(true_residual<double>(p, R, b, v[0], v[1], v[4], nullptr, hres.data(), deadline));
+            h64 += 1;
+            for (int r = 0; r < R; r++) relres[r] = hres[2 * r + 1] > 0 ? sqrt(hres[2 * r] / hres[2 * r + 1]) : 0;
+        }
+        AKRA_CUDA_TRY(cudaMemcpyAsync(d_x, v[1], V, cudaMemcpyDeviceToDevice, cs));
+    } else {
+        // MIXED: FP64 outer residual, FP32 inner CG (iterative refinement)
+        void *b64 = b.v64[0], *x64 = b.v64[1], *r64 = b.v64[2], *t64 = b.v64[3];
+        if (!b_in_place) AKRA_CUDA_TRY(cudaMemcpyAsync(b64, bsrc, V64, cudaMemcpyDeviceToDevice, cs));
+        AKRA_CUDA_TRY(cudaMemsetAsync(x64, 0, V64, cs));
+        AKRA_CUDA_TRY(cudaMemsetAsync(t64, 0, V64, cs));
+        // r = b - H·0 = b  (residual kernel with h = 0 gives ||r||, ||b||)
+        k_residual<double><<<RED_NB, RED_NT, 0, cs>>>(p->lmax, p->ntri, R, (const double2 *)b64,
+                                                     (const double2 *)t64, (double2 *)r64, b.res,
+                                                     b.ctl[0], b.scratch);
+        AKRA_CUDA_TRY(cudaGetLastError());
+        p->launches++;
+        // the ctl counter must be zero before the first last-block reduction
+        AKRA_CUDA_TRY(cudaMemcpyAsync(hres.data(), b.res, sizeof(double) * 2 * R, cudaMemcpyDeviceToHost, cs));
+        AKRA_CUDA_TRY(cudaEventRecord(p->ev_a, cs));
+        AKRA_TRY(bounded_wait(p->ev_a, deadline));
+        const int max_outer = 30;
+        double worst = 0;
+        for (int r = 0; r < R; r++) {
+            relres[r] = hres[2 * r + 1] > 0 ? sqrt(hres[2 * r] / hres[2 * r + 1]) : 0;
+            worst = std::max(worst, relres[r]);
+        }
+        int inner_budget = maxiter;
+        while (worst >= tol) {
+            if (outer >= max_outer || inner_budget <= 0) {
+                for (int r = 0; r < R; r++)
+                    if (relres[r] >= tol) status[r] = AKRA_ENOCONV;
+                break;
+            }
+            // inner tolerance: what this outer step must gain, but not below FP32 reach
+            const double tin = std::max(5e-6, std::min(0.1, 0.05 * tol / worst));
+            k_cast_scaled<<<RED_NB, RED_NT, 0, cs>>>(2 * p->ntri, R, (const double2 *)r64, b.res,
+                                                     (float2 *)b.v32[0]);
+            AKRA_CUDA_TRY(cudaGetLastError());
+            p->launches++;
+            AKRA_TRY(cg_run<float>(p, R, b, tin, inner_budget, hst.data(), deadline));
+            int it = 0;
+            for (int r = 0; r < R; r++) {
+                it = std::max(it, hst[r].iters);
+                iters[r] += hst[r].iters;
+                if (hst[r].status == AKRA_ENUMERIC) status[r] = AKRA_ENUMERIC;
+            }
+            total_iters += it;
+            h32 += it;
+            inner_budget -= it;
+            k_axpy_mixed<<<RED_NB, RED_NT, 0, cs>>>(2 * p->ntri, R, (const float2 *)b.v32[1], b.res,
+                                                    (double2 *)x64);
+            AKRA_CUDA_TRY(cudaGetLastError());
+            p->launches++;
+            AKRA_TRY(true_residual<double>(p, R, b, b64, x64, t64, r64, hres.data(), deadline));
+            h64 += 1;
+            outer += 1;
+            worst = 0;
+            for (int r = 0; r < R; r++) {
+                relres[r] = hres[2 * r + 1] > 0 ? sqrt(hres[2 * r] / hres[2 * r + 1]) : 0;
+                if (!std::isfinite(relres[r])) status[r] = AKRA_ENUMERIC;
+                worst = std::max(worst, relres[r]);
+            }
+            bool bad = false;
+            for (int r = 0; r < R; r++) bad |= status[r] == AKRA_ENUMERIC;
+            if (bad) break;
+        }
+        AKRA_CUDA_TRY(cudaMemcpyAsync(d_x, x64, V64, cudaMemcpyDeviceToDevice, cs));
+    }
+    // the caller's stream continues after the copies on the internal stream
+    AKRA_CUDA_TRY(cudaEventRecord(p->ev_b, cs));
+    AKRA_CUDA_TRY(cudaStreamWaitEvent(user, p->ev_b, 0));
+    AKRA_CUDA_TRY(cudaEventRecord(p->ev_a, cs));
+    AKRA_TRY(bounded_wait(p->ev_a, deadline));
+    if (info) {
+        info->iters = total_iters;
+        info->outer = outer;
+        info->h_applies_f64 = h64;
+        info->h_applies_f32 = h32;
+    }
+    fill_info(info, R, relres, iters, status);
+    int worst = AKRA_OK;
+    for (int r = 0; r < R; r++)
+        if (status[r] != AKRA_OK && (worst == AKRA_OK || status[r] > worst)) worst = status[r];
+    if (worst != AKRA_OK) set_error("CG: %s", worst == AKRA_ENOCONV ? "maxiter reached before tol"
+                                                                    : "non-finite or non-positive curvature");
+    return (akra_status)worst;
+}
+
+void cg_release_graphs(akra_plan p)
+{
+    for (auto &kv : p->graphs) {
+        if (kv.second) {
+            if (kv.second->exec) cudaGraphExecDestroy(kv.second->exec);
+            delete kv.second;
+        }
+    }
+    p->graphs.clear();
+    if (p->h_pinned) {
+        cudaFreeHost(p->h_pinned);
+        p->h_pinned = nullptr;
+    }
+}
+
+static akra_status check_cg(akra_plan p, akra_prec prec, const void *a, const void *x, int R, double tol,
+                            int maxiter, const char *who)
+{
+    if (!p || !a || !x) {
+        set_error("%s: NULL plan or array", who);
+        return AKRA_EINVAL;
+    }
+    if (prec != AKRA_F64 && prec != AKRA_F32 && prec != AKRA_MIXED) {
+        set_error("%s: unknown precision", who);
+        return AKRA_EINVAL;
+    }
+    if (R < 1 || R > kMaxRhsLocal) {
+        set_error("%s: R = %d outside [1, %d]", who, R, kMaxRhsLocal);
+        return AKRA_EINVAL;
+    }
+    if (!(tol > 0) || maxiter < 1) {
+        set_error("%s: tol must be > 0 and maxiter >= 1", who);
+        return AKRA_EINVAL;
+    }
+    if (!p->has_weights) {
+        set_error("%s: called before akra_plan_set_weights", who);
+        return AKRA_ENOWEIGHTS;
+    }
+    return AKRA_OK;
+}
+
+// the internal stream starts after everything already queued on the caller's stream
+static akra_status join_user(akra_plan p, cudaStream_t user, CgBufs &b)
+{
+    AKRA_CUDA_TRY(cudaEventRecord(p->ev_b, user));
+    AKRA_CUDA_TRY(cudaStreamWaitEvent(p->stream, p->ev_b, 0));
+    // last-block tickets start at zero
+    AKRA_CUDA_TRY(cudaMemsetAsync(b.ctl[0], 0, sizeof(CgCtl), p->stream));
+    AKRA_CUDA_TRY(cudaMemsetAsync(b.ctl[1], 0, sizeof(CgCtl), p->stream));
+    return AKRA_OK;
+}
+
+}  // namespace akra
+
+using namespace akra;
+
+extern "C" akra_status akra_set_timeout(double seconds)
+{
+    if (!(seconds > 0)) {
+        set_error("akra_set_timeout: seconds must be > 0");
+        return AKRA_EINVAL;
+    }
+    g_timeout_s = seconds;
+    return AKRA_OK;
+}
+
+extern "C" akra_status akra_cg_solve_b(akra_plan p, akra_prec prec, const void *d_b, void *d_x, int R,
+                                       double tol, int maxiter, akra_cg_info *info, void *stream)
+{
+    AKRA_TRY(check_cg(p, prec, d_b, d_x, R, tol, maxiter, "akra_cg_solve_b"));
+    cudaStream_t user = (cudaStream_t)stream;
+    CgBufs b;
+    AKRA_TRY(cg_reserve(p, R, b));
+    AKRA_TRY(join_user(p, user, b));
+    return solve_b(p, prec, d_b, d_x, R, tol, maxiter, info, user, false, b, 0);
+}
+
+extern "C" akra_status akra_cg_solve(akra_plan p, akra_prec prec, const void *d_shear, void *d_x, int R,
+                                     double tol, int maxiter, akra_cg_info *info, void *stream)
+{
+    AKRA_TRY(check_cg(p, prec, d_shear, d_x, R, tol, maxiter, "akra_cg_solve"));
+    cudaStream_t user = (cudaStream_t)stream;
+    CgBufs b;
+    AKRA_TRY(cg_reserve(p, R, b));
+    AKRA_TRY(join_user(p, user, b));
+    // b = A^T W y, in FP64 unless the whole solve is FP32
+    akra_status s;
+    int h64 = 0;
+    if (prec == AKRA_F32) {
+        // the caller's shear is FP32 for an F32 solve
+        s = op_adjoint<float>(p, LegMode::KS, d_shear, b.v32[0], true, R, p->stream);
+    } else {
+        s = op_adjoint<double>(p, LegMode::KS, d_shear, b.v64[0], true, R, p->stream);
+        h64 = 1;
+    }
+    if (s != AKRA_OK) return s;
+    // the adjoint may have grown a workspace; refresh the buffer pointers
+    AKRA_TRY(cg_reserve(p, R, b));
+    return solve_b(p, prec, nullptr, d_x, R, tol, maxiter, info, user, true, b, h64);
+}

@@ -1,0 +1,193 @@
+// akra_internal.cuh -- internal declarations of the sm_103a AKRA library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/akra.h"
+
+namespace akra {
+
+// ---------------------------------------------------------------------------
+// error handling: every failure becomes an akra_status plus a thread-local message
+// ---------------------------------------------------------------------------
+void set_error(const char *fmt, ...);
+
+#define AKRA_CUDA_TRY(expr)                                                              \
+    do {                                                                                 \
+        cudaError_t _e = (expr);                                                         \
+        if (_e != cudaSuccess) {                                                         \
+            akra::set_error("%s:%d: %s failed: %s", __FILE__, __LINE__, #expr,           \
+                            cudaGetErrorString(_e));                                     \
+            return AKRA_ECUDA;                                                           \
+        }                                                                                \
+    } while (0)
+
+#define AKRA_TRY(expr)                                                                   \
+    do {                                                                                 \
+        akra_status _s = (expr);                                                         \
+        if (_s != AKRA_OK) return _s;                                                    \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// small vector types
+// ---------------------------------------------------------------------------
+template <typename T> struct Cx;
+template <> struct Cx<float> { using type = float2; };
+template <> struct Cx<double> { using type = double2; };
+template <typename T> using cx_t = typename Cx<T>::type;
+
+template <typename T> struct V4t;
+template <> struct V4t<float> { using type = float4; };
+template <> struct V4t<double> { using type = double4_32a; };
+template <typename T> using v4_t = typename V4t<T>::type;
+
+// scaled-recurrence parameters: a value v with exponent index e < 0 stands for
+// v * 2^(Q e); a rescale by 2^-Q happens when |v| > 2^(Q/2); contributions start when e == 0
+template <typename T> struct Scale;
+template <> struct Scale<float> {
+    static constexpr int Q = 64;
+    __host__ __device__ static constexpr float hi() { return 4294967296.0f; }                  // 2^32
+    __host__ __device__ static constexpr float inv() { return 5.421010862427522e-20f; }        // 2^-64
+};
+template <> struct Scale<double> {
+    static constexpr int Q = 600;
+    __host__ __device__ static constexpr double hi() { return 0x1p300; }
+    __host__ __device__ static constexpr double inv() { return 0x1p-600; }
+};
+
+// ---------------------------------------------------------------------------
+// plan tables
+// ---------------------------------------------------------------------------
+struct RingInfo {          // one HEALPix ring (row r = ring index - 1)
+    double z, st;          // cos θ, sin θ
+    long long first;       // first pixel (RING order)
+    long long tw_off;      // offset of this ring length's table of e^{iπ t/n}, t in [0, 2n)
+    int nphi;              // pixels on the ring, n
+    int sigma;             // pixel phases φ_j = π(2j + σ)/n
+    int ilen;              // n = 4 * ilen (index into the FFT factor table)
+    int pad;
+};
+
+struct UnitInfo {          // one north/south ring pair (or the equator ring alone)
+    double x;              // cos θ of the north ring (>= 0)
+    double ls, lc;         // log2 sin(θ/2), log2 cos(θ/2) of the north ring
+    int ring_n, ring_s;    // rows of the two rings; ring_s = -1 for the equator
+};
+
+constexpr int kMaxFactors = 16;
+struct FftFactors {
+    int nf;
+    int f[kMaxFactors];    // radices, generic (>7) primes first
+};
+
+constexpr int kMaxNside = 2048;
+
+// Legendre tile shape (chosen per precision and RHS count; see autotune)
+struct LegShape {
+    int P;                 // ring pairs per thread
+    int NT;                // threads per block
+    int RG;                // RHS handled together by one block
+};
+
+struct Workspace {
+    void *ptr = nullptr;
+    size_t bytes = 0;
+};
+
+struct CgGraph;            // CUDA-graph state of one CG configuration (akra_cg.cu)
+
+}  // namespace akra
+
+struct akra_plan_s {
+    int nside = 0, lmax = 0, nring = 0, nunit = 0;
+    long long npix = 0, ntri = 0;
+    int device = 0;
+
+    // geometry and recurrence tables (device)
+    akra::RingInfo *d_rings = nullptr;
+    akra::UnitInfo *d_units = nullptr;
+    akra::FftFactors *d_factors = nullptr;   // [nside + 1] by ring length index
+    double4_32a *d_coef64 = nullptr;            // [ntri] {A, A B, A 2m/(l(l+1)), 0}
+    float4 *d_coef32 = nullptr;
+    double *d_seedC = nullptr;               // [lmax + 1] log2 seed prefactor per m
+    double *d_D64 = nullptr;                 // [lmax + 1] KS kernel D_l
+    float *d_D32 = nullptr;
+    double2 *d_tw64 = nullptr;               // ring twiddles e^{iπ t/n}
+    float2 *d_tw32 = nullptr;
+    int *d_all_rings = nullptr;              // [nring] 0..nring-1
+    int *d_all_units = nullptr;              // [nunit] 0..nunit-1
+
+    // weights
+    bool has_weights = false;
+    double lambda = 0, lambda_eff = 0, precond = 1, omega = 0;
+    double *d_W64 = nullptr;                 // [npix] ω M N^-1
+    float *d_W32 = nullptr;
+    int *d_active_rings = nullptr;           // rings with any W != 0
+    int n_active_rings = 0;
+    int *d_active_units = nullptr;           // units with an active ring
+    int n_active_units = 0;
+    unsigned char *d_ring_active = nullptr;  // [nring] flag
+
+    // workspaces (grown on demand)
+    akra::Workspace phi, partial, cg, red;
+    cudaStream_t stream = nullptr;           // internal stream for captured CG graphs
+    cudaEvent_t ev_a = nullptr, ev_b = nullptr;
+    std::map<long long, akra::LegShape> shapes;   // key: prec*1000 + R
+    std::map<long long, akra::CgGraph *> graphs;
+    unsigned ws_gen = 0;                     // bumped whenever a workspace is reallocated
+    const int *cur_skip = nullptr;           // device flag: operator kernels return early if set
+    void *h_pinned = nullptr;                // pinned host mirror for status polling
+    size_t bytes_tables = 0;
+    long long launches = 0;                  // kernels launched (host-side count)
+};
+
+namespace akra {
+
+// workspace growth (device); returns ENOMEM on failure
+akra_status ws_reserve(akra_plan p, Workspace &w, size_t bytes);
+size_t plan_device_bytes(akra_plan p);
+
+// the operator pieces (all asynchronous on `st`)
+enum class LegMode { Synth, KS };   // per-l factor f_l = -1 (pure spin-2 SHT) or D_l (KS)
+
+LegShape leg_shape(akra_plan p, akra_prec prec, int R);
+int legendre_chunks(int nunits, const LegShape &s);
+void cg_release_graphs(akra_plan p);   // akra_cg.cu
+
+// alm [R][2][ntri] -> Φ [R][nring][2L+1] on the listed units
+template <typename T>
+akra_status legendre_synth(akra_plan p, const LegShape &s, LegMode mode, const void *alm, void *phi,
+                           int R, const int *units, int nunits, cudaStream_t st);
+// Φ' [R][nring][2L+1] -> partial sums [chunks][R][ntri] (vec4) on the listed units
+template <typename T>
+akra_status legendre_adjoint(akra_plan p, const LegShape &s, const void *phi, void *partial,
+                             int R, const int *units, int nunits, int *nchunks_out,
+                             cudaStream_t st);
+// partial sums -> alm (with f_l/2, E/B recombination and optional + λ x)
+template <typename T>
+akra_status adjoint_epilogue(akra_plan p, LegMode mode, const void *partial, int nchunks,
+                             const void *x_reg, double lam, void *alm_out, int R, cudaStream_t st);
+
+enum class FftMode { Synth = 0, Adjoint = 1, Happly = 2 };
+template <typename T>
+akra_status ring_fft(akra_plan p, FftMode mode, void *phi, const void *map_in, void *map_out,
+                     bool weighted, int R, const int *rings, int nrings, cudaStream_t st);
+
+// whole operators
+template <typename T>
+akra_status op_synth(akra_plan p, LegMode mode, const void *alm, void *map, bool weighted, int R,
+                     cudaStream_t st);
+template <typename T>
+akra_status op_adjoint(akra_plan p, LegMode mode, const void *map, void *alm, bool weighted, int R,
+                       cudaStream_t st);
+template <typename T>
+akra_status op_H(akra_plan p, const void *x, void *y, int R, cudaStream_t st);
+
+}  // namespace akra

@@ -1,0 +1,558 @@
+// akra_legendre.cu -- spin-2 Legendre stages of the synthesis (Eq. 1) and of its exact
+// transpose, fused with the KS factor (Eq. 3) and the E/B <-> spin ±2 recombination (Eq. 2).
+//
+// Work unit: one m and one ring pair (north ring θ, south ring π-θ; the equator ring alone).
+// Two recurrences run in ℓ, one per spin s = ±2 (x = cos θ, A_l, B_l the normalised
+// Wigner-d coefficients):
+//     sλ_{l+1} = (A_l x + s A_l m/(l(l+1))) sλ_l - A_l B_l sλ_{l-1}
+// (kept separate: near the poles one spin is O(1) and the other tiny, and any mixed
+// combination would leak the large one's rounding into the small one).  The mirror ring
+// follows from  sλ_lm(π-θ) = (-1)^{l+m} (-s)λ_lm(θ), so one pair of recurrences feeds both
+// rings through even/odd (l+m) accumulators.  Seeds at l0 = max(m,2) are formed in FP64 in
+// log2 form; the recurrence carries a per-unit exponent index e (value = v 2^(Q e)) and
+// contributes only once e == 0.
+#include "akra_internal.cuh"
+
+namespace akra {
+
+constexpr int TL = 64;  // l-steps staged in shared memory per tile (even)
+
+// seeds 2λ_{l0 m} (vp) and (-2)λ_{l0 m} (vm) with a shared exponent index e
+template <typename T>
+__device__ __forceinline__ void seed_pair(int m, double Cm, double ls, double lc, T &vp, T &vm,
+                                          int &e)
+{
+    constexpr int Q = Scale<T>::Q;
+    const int a = m + 2, b = m >= 2 ? m - 2 : 2 - m;
+    const double Lp = Cm + a * ls + b * lc;   // log2 |2λ_{l0 m}|
+    const double Lm = Cm + b * ls + a * lc;   // log2 |(-2)λ_{l0 m}|
+    const double sp = (m & 1) ? -1.0 : 1.0;
+    const double sm = (m >= 2) ? sp : 1.0;
+    int ee = (int)floor((fmax(Lp, Lm) + 0.5 * Q) / Q);
+    if (ee > 0) ee = 0;
+    const double vplus = sp * exp2(Lp - (double)Q * ee);
+    const double vminus = sm * exp2(Lm - (double)Q * ee);
+    vp = (T)vplus;
+    vm = (T)vminus;
+    e = ee;
+}
+
+// ---------------------------------------------------------------------------
+// synthesis: Φ(ring, ±m) for every ring of the listed units
+// ---------------------------------------------------------------------------
+template <typename T, int P, int RG, int NT>
+__global__ void __launch_bounds__(NT)
+k_leg_synth(int L, int nring, long long ntri, int nchunks, int nunits,
+            const int *__restrict__ units, const UnitInfo *__restrict__ uinfo,
+            const v4_t<T> *__restrict__ coef, const double *__restrict__ seedC,
+            const T *__restrict__ fl, const cx_t<T> *__restrict__ alm, int R,
+            cx_t<T> *__restrict__ phi, const unsigned char *__restrict__ ring_active,
+            const int *__restrict__ skip)
+{
+    using C2 = cx_t<T>;
+    using V4 = v4_t<T>;
+    __shared__ V4 s_coef[TL];
+    __shared__ V4 s_alm[TL][RG];
+    if (skip && *skip) return;
+
+    const int m = blockIdx.x / nchunks;
+    const int chunk = blockIdx.x - m * nchunks;
+    const int r0 = blockIdx.y * RG;
+    const int l0 = m > 2 ? m : 2;
+    const int tid = threadIdx.x;
+    const long long mbase = (long long)m * (2 * L + 1 - m) / 2;
+
+    T x[P], vp[P], vm[P], vpo[P], vmo[P];
+    int e[P], uid[P];
+    T acc[P][RG][16];
+#pragma unroll
+    for (int k = 0; k < P; k++) {
+        const int iu = (chunk * P + k) * NT + tid;
+        uid[k] = iu < nunits ? (units ? units[iu] : iu) : -1;
+        x[k] = 0;
+        vp[k] = vm[k] = 0;
+        e[k] = 0;
+        if (uid[k] >= 0) {
+            const UnitInfo ui = uinfo[uid[k]];
+            x[k] = (T)ui.x;
+            seed_pair<T>(m, seedC[m], ui.ls, ui.lc, vp[k], vm[k], e[k]);
+        }
+        vpo[k] = vmo[k] = 0;
+#pragma unroll
+        for (int r = 0; r < RG; r++)
+#pragma unroll
+            for (int j = 0; j < 16; j++) acc[k][r][j] = 0;
+    }
+
+    for (int lt = l0; lt <= L; lt += TL) {
+        __syncthreads();
+        for (int i = tid; i < TL; i += NT) {
+            const int l = lt + i;
+            s_coef[i] = (l <= L) ? coef[mbase + l] : V4{0, 0, 0, 0};
+        }
+        for (int i = tid; i < TL * RG; i += NT) {
+            const int li = i / RG, rr = i - li * RG;
+            const int l = lt + li, r = r0 + rr;
+            V4 v{0, 0, 0, 0};
+            if (l <= L && r < R) {
+                C2 E = alm[((size_t)r * 2 + 0) * ntri + mbase + l];
+                C2 B = alm[((size_t)r * 2 + 1) * ntri + mbase + l];
+                const T f = fl ? fl[l] : T(-1);
+                if (m == 0) E.y = B.y = 0;
+                // c = f (E + iB), d = f (E - iB)
+                v = V4{f * (E.x - B.y), f * (E.y + B.x), f * (E.x + B.y), f * (E.y - B.x)};
+            }
+            s_alm[li][rr] = v;
+        }
+        __syncthreads();
+        const int nl = min(TL, L - lt + 1);
+        bool live = true;
+#pragma unroll
+        for (int k = 0; k < P; k++) live &= (e[k] == 0);
+        const bool all_live = __all_sync(0xffffffffu, live);
+
+        // one l-step: contract at l (slot S = parity of l - l0), then recur to l+1.
+        // vp = 2λ, vm = (-2)λ; accumulators per slot: P1 = Σ c 2λ, P2 = Σ d (-2)λ,
+        // P3 = Σ c (-2)λ, P4 = Σ d 2λ (complex)
+#define AKRA_SYNTH_STEP(I, S, GATED)                                                        \
+    {                                                                                       \
+        const V4 c = s_coef[I];                                                             \
+        bool any = true;                                                                    \
+        if (GATED) {                                                                        \
+            bool a_ = false;                                                                \
+            _Pragma("unroll") for (int k = 0; k < P; k++) a_ |= (e[k] == 0);                \
+            any = __any_sync(0xffffffffu, a_);                                              \
+        }                                                                                   \
+        if (any) {                                                                          \
+            _Pragma("unroll") for (int k = 0; k < P; k++) {                                 \
+                const T lp = (GATED && e[k] != 0) ? T(0) : vp[k];                           \
+                const T lm = (GATED && e[k] != 0) ? T(0) : vm[k];                           \
+                _Pragma("unroll") for (int r = 0; r < RG; r++) {                            \
+                    const V4 a = s_alm[I][r];                                               \
+                    T *ac = &acc[k][r][(S) * 8];                                            \
+                    ac[0] = fma(a.x, lp, ac[0]);                                            \
+                    ac[1] = fma(a.y, lp, ac[1]);                                            \
+                    ac[2] = fma(a.z, lm, ac[2]);                                            \
+                    ac[3] = fma(a.w, lm, ac[3]);                                            \
+                    ac[4] = fma(a.x, lm, ac[4]);                                            \
+                    ac[5] = fma(a.y, lm, ac[5]);                                            \
+                    ac[6] = fma(a.z, lp, ac[6]);                                            \
+                    ac[7] = fma(a.w, lp, ac[7]);                                            \
+                }                                                                           \
+            }                                                                               \
+        }                                                                                   \
+        _Pragma("unroll") for (int k = 0; k < P; k++) {                                     \
+            const T t1 = fma(c.x, x[k], c.z);                                               \
+            const T t2 = fma(c.x, x[k], -c.z);                                              \
+            const T np = fma(t1, vp[k], -c.y * vpo[k]);                                     \
+            const T nm = fma(t2, vm[k], -c.y * vmo[k]);                                     \
+            vpo[k] = vp[k];                                                                 \
+            vmo[k] = vm[k];                                                                 \
+            vp[k] = np;                                                                     \
+            vm[k] = nm;                                                                     \
+            if (GATED && e[k] < 0 &&                                                        \
+                (fabs(vp[k]) > Scale<T>::hi() || fabs(vm[k]) > Scale<T>::hi())) {           \
+                vp[k] *= Scale<T>::inv();                                                   \
+                vm[k] *= Scale<T>::inv();                                                   \
+                vpo[k] *= Scale<T>::inv();                                                  \
+                vmo[k] *= Scale<T>::inv();                                                  \
+                e[k]++;                                                                     \
+            }                                                                               \
+        }                                                                                   \
+    }
+
+        if (all_live) {
+            for (int i = 0; i < nl; i += 2) {
+                AKRA_SYNTH_STEP(i, 0, false)
+                AKRA_SYNTH_STEP(i + 1, 1, false)
+            }
+        } else {
+            for (int i = 0; i < nl; i += 2) {
+                AKRA_SYNTH_STEP(i, 0, true)
+                AKRA_SYNTH_STEP(i + 1, 1, true)
+            }
+        }
+#undef AKRA_SYNTH_STEP
+    }
+
+    // combine parities into the north and south rings and write Φ(±m)
+    const bool swap = ((l0 + m) & 1) != 0;   // slot A holds odd (l+m) when l0+m is odd
+    const size_t row = 2 * (size_t)L + 1;
+#pragma unroll
+    for (int k = 0; k < P; k++) {
+        if (uid[k] < 0) continue;
+        const UnitInfo ui = uinfo[uid[k]];
+#pragma unroll
+        for (int rr = 0; rr < RG; rr++) {
+            const int r = r0 + rr;
+            if (r >= R) continue;
+            T se[8], so[8];
+#pragma unroll
+            for (int j = 0; j < 8; j++) {
+                se[j] = swap ? acc[k][rr][8 + j] : acc[k][rr][j];
+                so[j] = swap ? acc[k][rr][j] : acc[k][rr][8 + j];
+            }
+            // north: Φ(m) = P1,  conj Φ(-m) = P2        (even + odd)
+            // south: Φ(m) = P3,  conj Φ(-m) = P4        (even - odd)
+#pragma unroll
+            for (int side = 0; side < 2; side++) {
+                const int ring = side == 0 ? ui.ring_n : ui.ring_s;
+                if (ring < 0) continue;
+                if (ring_active && !ring_active[ring]) continue;
+                const int o = side == 0 ? 0 : 4;
+                const T sg = side == 0 ? T(1) : T(-1);
+                const T fr = se[o + 0] + sg * so[o + 0], fi = se[o + 1] + sg * so[o + 1];
+                const T gr = se[o + 2] + sg * so[o + 2], gi = se[o + 3] + sg * so[o + 3];
+                C2 *prow = phi + ((size_t)r * nring + ring) * row + L;
+                prow[m] = C2{fr, fi};
+                if (m > 0) prow[-m] = C2{gr, -gi};
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// adjoint: partial[chunk][r][idx(l,m)] = Σ_{units in chunk} (E-part, B-part) at each l
+//   E-part = Σ_rings [2λ P + (-2)λ Q],  B-part = Σ_rings [2λ P - (-2)λ Q]
+//   with P = G(m), Q = conj(G(-m)) of the ring's Φ' row.  With the mirror relation and
+//   U1 = P_N + Q_S, U2 = Q_N + P_S, U3 = P_N - Q_S, U4 = P_S - Q_N:
+//     (l+m) even: E += 2λ U1 + (-2)λ U2,  B += 2λ U3 + (-2)λ U4
+//     (l+m) odd : E += 2λ U3 - (-2)λ U4,  B += 2λ U1 - (-2)λ U2
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T shfl_x(T v, int off)
+{
+    return __shfl_xor_sync(0xffffffffu, v, off);
+}
+
+template <typename T, int P, int RG, int NT>
+__global__ void __launch_bounds__(NT)
+k_leg_adjoint(int L, int nring, long long ntri, int nchunks, int nunits,
+              const int *__restrict__ units, const UnitInfo *__restrict__ uinfo,
+              const v4_t<T> *__restrict__ coef, const double *__restrict__ seedC,
+              const cx_t<T> *__restrict__ phi, int R, T *__restrict__ partial,
+              const unsigned char *__restrict__ ring_active, const int *__restrict__ skip)
+{
+    if (skip && *skip) return;
+    using C2 = cx_t<T>;
+    using V4 = v4_t<T>;
+    constexpr int NW = NT / 32;
+    constexpr int K = 8 / RG;   // l-steps per transpose-reduce block: K * 4 * RG = 32 values
+    static_assert(K >= 2 && K * 4 * RG == 32, "RG must be 1, 2 or 4");
+    __shared__ V4 s_coef[TL];
+    __shared__ T s_red[NW][TL][RG][4];
+
+    const int m = blockIdx.x / nchunks;
+    const int chunk = blockIdx.x - m * nchunks;
+    const int r0 = blockIdx.y * RG;
+    const int l0 = m > 2 ? m : 2;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const long long mbase = (long long)m * (2 * L + 1 - m) / 2;
+    const size_t row = 2 * (size_t)L + 1;
+    const bool swap = ((l0 + m) & 1) != 0;
+
+    T x[P], vp[P], vm[P], vpo[P], vmo[P];
+    int e[P];
+    // per unit and RHS, the partners of 2λ and (-2)λ in slot A (l - l0 even):
+    //   E += 2λ X1 + (-2)λ X2,  B += 2λ X3 + (-2)λ X4;   slot B: E += 2λ X3 - (-2)λ X4,
+    //   B += 2λ X1 - (-2)λ X2   (X = U1..U4, or U3, -U4, U1, -U2 when l0+m is odd)
+    C2 X1[P][RG], X2[P][RG], X3[P][RG], X4[P][RG];
+#pragma unroll
+    for (int k = 0; k < P; k++) {
+        const int iu = (chunk * P + k) * NT + tid;
+        const int u = iu < nunits ? (units ? units[iu] : iu) : -1;
+        x[k] = 0;
+        vp[k] = vm[k] = vpo[k] = vmo[k] = 0;
+        e[k] = 0;
+        UnitInfo ui;
+        ui.ring_n = ui.ring_s = -1;
+        if (u >= 0) {
+            ui = uinfo[u];
+            x[k] = (T)ui.x;
+            seed_pair<T>(m, seedC[m], ui.ls, ui.lc, vp[k], vm[k], e[k]);
+        }
+#pragma unroll
+        for (int rr = 0; rr < RG; rr++) {
+            const int r = r0 + rr;
+            C2 Pv[2], Qv[2];
+#pragma unroll
+            for (int side = 0; side < 2; side++) {
+                const int ring = side == 0 ? ui.ring_n : ui.ring_s;
+                Pv[side] = C2{0, 0};
+                Qv[side] = C2{0, 0};
+                if (ring < 0 || r >= R) continue;
+                if (ring_active && !ring_active[ring]) continue;
+                const C2 *prow = phi + ((size_t)r * nring + ring) * row + L;
+                const C2 g = prow[m], gm = prow[-m];
+                Pv[side] = g;
+                Qv[side] = C2{gm.x, -gm.y};
+            }
+            const C2 u1{Pv[0].x + Qv[1].x, Pv[0].y + Qv[1].y};
+            const C2 u2{Qv[0].x + Pv[1].x, Qv[0].y + Pv[1].y};
+            const C2 u3{Pv[0].x - Qv[1].x, Pv[0].y - Qv[1].y};
+            const C2 u4{Pv[1].x - Qv[0].x, Pv[1].y - Qv[0].y};
+            X1[k][rr] = swap ? u3 : u1;
+            X2[k][rr] = swap ? C2{-u4.x, -u4.y} : u2;
+            X3[k][rr] = swap ? u1 : u3;
+            X4[k][rr] = swap ? C2{-u2.x, -u2.y} : u4;
+        }
+    }
+
+    for (int lt = l0; lt <= L; lt += TL) {
+        __syncthreads();
+        for (int i = tid; i < TL; i += NT) {
+            const int l = lt + i;
+            s_coef[i] = (l <= L) ? coef[mbase + l] : V4{0, 0, 0, 0};
+        }
+        __syncthreads();
+        const int nl = min(TL, L - lt + 1);
+        bool live = true;
+#pragma unroll
+        for (int k = 0; k < P; k++) live &= (e[k] == 0);
+        const bool all_live = __all_sync(0xffffffffu, live);
+        const int nkb = (nl + K - 1) / K;
+
+        for (int kb = 0; kb < nkb; kb++) {
+            T ta[K][RG][4];
+#pragma unroll
+            for (int kk = 0; kk < K; kk++)
+#pragma unroll
+                for (int rr = 0; rr < RG; rr++)
+#pragma unroll
+                    for (int q = 0; q < 4; q++) ta[kk][rr][q] = 0;
+#pragma unroll
+            for (int kk = 0; kk < K; kk++) {
+                const int i = kb * K + kk;
+                const V4 c = s_coef[i];
+                const bool slotA = (kk & 1) == 0;
+                bool any = true;
+                if (!all_live) {
+                    bool a_ = false;
+#pragma unroll
+                    for (int k = 0; k < P; k++) a_ |= (e[k] == 0);
+                    any = __any_sync(0xffffffffu, a_);
+                }
+                if (any) {
+#pragma unroll
+                    for (int k = 0; k < P; k++) {
+                        const T lp = (!all_live && e[k] != 0) ? T(0) : vp[k];
+                        const T lm0 = (!all_live && e[k] != 0) ? T(0) : vm[k];
+                        const T lm = slotA ? lm0 : -lm0;
+#pragma unroll
+                        for (int rr = 0; rr < RG; rr++) {
+                            const C2 eP = slotA ? X1[k][rr] : X3[k][rr];
+                            const C2 eM = slotA ? X2[k][rr] : X4[k][rr];
+                            const C2 bP = slotA ? X3[k][rr] : X1[k][rr];
+                            const C2 bM = slotA ? X4[k][rr] : X2[k][rr];
+                            T *t = ta[kk][rr];
+                            t[0] = fma(lp, eP.x, fma(lm, eM.x, t[0]));
+                            t[1] = fma(lp, eP.y, fma(lm, eM.y, t[1]));
+                            t[2] = fma(lp, bP.x, fma(lm, bM.x, t[2]));
+                            t[3] = fma(lp, bP.y, fma(lm, bM.y, t[3]));
+                        }
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < P; k++) {
+                    const T t1 = fma(c.x, x[k], c.z);
+                    const T t2 = fma(c.x, x[k], -c.z);
+                    const T np = fma(t1, vp[k], -c.y * vpo[k]);
+                    const T nm = fma(t2, vm[k], -c.y * vmo[k]);
+                    vpo[k] = vp[k];
+                    vmo[k] = vm[k];
+                    vp[k] = np;
+                    vm[k] = nm;
+                    if (!all_live && e[k] < 0 &&
+                        (fabs(vp[k]) > Scale<T>::hi() || fabs(vm[k]) > Scale<T>::hi())) {
+                        vp[k] *= Scale<T>::inv();
+                        vm[k] *= Scale<T>::inv();
+                        vpo[k] *= Scale<T>::inv();
+                        vmo[k] *= Scale<T>::inv();
+                        e[k]++;
+                    }
+                }
+            }
+            // warp transpose-reduce: 32 values per lane -> lane j holds the warp sum of value j
+            T v[32];
+#pragma unroll
+            for (int kk = 0; kk < K; kk++)
+#pragma unroll
+                for (int rr = 0; rr < RG; rr++)
+#pragma unroll
+                    for (int q = 0; q < 4; q++) v[(kk * RG + rr) * 4 + q] = ta[kk][rr][q];
+#pragma unroll
+            for (int off = 16; off >= 1; off >>= 1) {
+                const bool upper = (lane & off) != 0;
+#pragma unroll
+                for (int i = 0; i < off; i++) {
+                    const T send = upper ? v[i] : v[i + off];
+                    const T keep = upper ? v[i + off] : v[i];
+                    v[i] = keep + shfl_x(send, off);
+                }
+            }
+            {
+                const int kk = lane / (4 * RG), rr = (lane / 4) % RG, q = lane & 3;
+                s_red[warp][kb * K + kk][rr][q] = v[0];
+            }
+        }
+        __syncthreads();
+        // sum the warps and write this chunk's partial sums for the tile
+        for (int i = tid; i < nl * RG * 4; i += NT) {
+            const int step = i / (RG * 4), rem = i - step * RG * 4, rr = rem >> 2, q = rem & 3;
+            const int r = r0 + rr;
+            if (r >= R) continue;
+            T s = 0;
+#pragma unroll
+            for (int w = 0; w < NW; w++) s += s_red[w][step][rr][q];
+            partial[(((size_t)chunk * R + r) * ntri + mbase + lt + step) * 4 + q] = s;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// epilogue: sum chunk partials, apply f_l/2 and the spin ±2 -> E/B recombination
+//   E = (f/2) E-part,  B = (-i f/2) B-part,  optional + λ x
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_adj_epilogue(int L, long long ntri, int nchunks, int R,
+                               const T *__restrict__ partial, const T *__restrict__ fl,
+                               const cx_t<T> *__restrict__ xreg, T lam, cx_t<T> *__restrict__ out,
+                               const int *__restrict__ skip)
+{
+    if (skip && *skip) return;
+    using C2 = cx_t<T>;
+    const int m = blockIdx.x, r = blockIdx.y;
+    const long long mbase = (long long)m * (2 * L + 1 - m) / 2;
+    for (int l = m + threadIdx.x; l <= L; l += blockDim.x) {
+        const long long idx = mbase + l;
+        T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+        if (l >= 2) {
+            for (int c = 0; c < nchunks; c++) {
+                const T *pp = partial + (((size_t)c * R + r) * ntri + idx) * 4;
+                a0 += pp[0];
+                a1 += pp[1];
+                a2 += pp[2];
+                a3 += pp[3];
+            }
+        }
+        const T h = (fl ? fl[l] : T(-1)) * T(0.5);
+        C2 E{h * a0, h * a1};
+        C2 B{h * a3, -h * a2};
+        if (xreg) {
+            C2 xe = xreg[((size_t)r * 2 + 0) * ntri + idx];
+            C2 xb = xreg[((size_t)r * 2 + 1) * ntri + idx];
+            E.x += lam * xe.x;
+            E.y += lam * xe.y;
+            B.x += lam * xb.x;
+            B.y += lam * xb.y;
+        }
+        if (m == 0) E.y = B.y = 0;
+        out[((size_t)r * 2 + 0) * ntri + idx] = E;
+        out[((size_t)r * 2 + 1) * ntri + idx] = B;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+template <typename T> const v4_t<T> *coef_ptr(akra_plan p);
+template <> const float4 *coef_ptr<float>(akra_plan p) { return p->d_coef32; }
+template <> const double4_32a *coef_ptr<double>(akra_plan p) { return p->d_coef64; }
+template <typename T> const T *D_ptr(akra_plan p);
+template <> const float *D_ptr<float>(akra_plan p) { return p->d_D32; }
+template <> const double *D_ptr<double>(akra_plan p) { return p->d_D64; }
+
+template <typename T, int P, int RG, int NT>
+static void launch_synth(akra_plan p, LegMode mode, const void *alm, void *phi, int R,
+                         const int *units, int nunits, cudaStream_t st)
+{
+    const int nchunks = (nunits + NT * P - 1) / (NT * P);
+    dim3 grid((unsigned)(p->lmax + 1) * nchunks, (R + RG - 1) / RG);
+    k_leg_synth<T, P, RG, NT><<<grid, NT, 0, st>>>(
+        p->lmax, p->nring, p->ntri, nchunks, nunits, units, p->d_units, coef_ptr<T>(p),
+        p->d_seedC, mode == LegMode::KS ? D_ptr<T>(p) : nullptr, (const cx_t<T> *)alm, R,
+        (cx_t<T> *)phi, units == p->d_all_units ? nullptr : p->d_ring_active, p->cur_skip);
+}
+
+template <typename T, int P, int RG, int NT>
+static int launch_adjoint(akra_plan p, const void *phi, void *partial, int R, const int *units,
+                          int nunits, cudaStream_t st)
+{
+    const int nchunks = (nunits + NT * P - 1) / (NT * P);
+    dim3 grid((unsigned)(p->lmax + 1) * nchunks, (R + RG - 1) / RG);
+    k_leg_adjoint<T, P, RG, NT><<<grid, NT, 0, st>>>(
+        p->lmax, p->nring, p->ntri, nchunks, nunits, units, p->d_units, coef_ptr<T>(p),
+        p->d_seedC, (const cx_t<T> *)phi, R, (T *)partial,
+        units == p->d_all_units ? nullptr : p->d_ring_active, p->cur_skip);
+    return nchunks;
+}
+
+// shape dispatch: (P, RG) combinations compiled for each precision, NT = 128
+template <typename T>
+akra_status legendre_synth(akra_plan p, const LegShape &s, LegMode mode, const void *alm,
+                           void *phi, int R, const int *units, int nunits, cudaStream_t st)
+{
+    if (nunits <= 0) return AKRA_OK;
+#define AKRA_S(PP, RR)                                                                      \
+    if (s.P == PP && s.RG == RR) {                                                          \
+        launch_synth<T, PP, RR, 128>(p, mode, alm, phi, R, units, nunits, st);              \
+        AKRA_CUDA_TRY(cudaGetLastError());                                                  \
+        p->launches++;                                                                      \
+        return AKRA_OK;                                                                     \
+    }
+    AKRA_S(1, 1) AKRA_S(2, 1) AKRA_S(4, 1) AKRA_S(1, 2) AKRA_S(2, 2) AKRA_S(1, 4)
+#undef AKRA_S
+    set_error("no synthesis kernel for P=%d RG=%d", s.P, s.RG);
+    return AKRA_EINVAL;
+}
+
+template <typename T>
+akra_status legendre_adjoint(akra_plan p, const LegShape &s, const void *phi, void *partial,
+                             int R, const int *units, int nunits, int *nchunks_out,
+                             cudaStream_t st)
+{
+    *nchunks_out = 0;
+    if (nunits <= 0) return AKRA_OK;
+#define AKRA_A(PP, RR)                                                                      \
+    if (s.P == PP && s.RG == RR) {                                                          \
+        *nchunks_out = launch_adjoint<T, PP, RR, 128>(p, phi, partial, R, units, nunits, st); \
+        AKRA_CUDA_TRY(cudaGetLastError());                                                  \
+        p->launches++;                                                                      \
+        return AKRA_OK;                                                                     \
+    }
+    AKRA_A(1, 1) AKRA_A(2, 1) AKRA_A(4, 1) AKRA_A(1, 2) AKRA_A(2, 2) AKRA_A(1, 4)
+#undef AKRA_A
+    set_error("no adjoint kernel for P=%d RG=%d", s.P, s.RG);
+    return AKRA_EINVAL;
+}
+
+template <typename T>
+akra_status adjoint_epilogue(akra_plan p, LegMode mode, const void *partial, int nchunks,
+                             const void *x_reg, double lam, void *alm_out, int R, cudaStream_t st)
+{
+    dim3 grid(p->lmax + 1, R);
+    k_adj_epilogue<T><<<grid, 128, 0, st>>>(p->lmax, p->ntri, nchunks, R, (const T *)partial,
+                                            mode == LegMode::KS ? D_ptr<T>(p) : nullptr,
+                                            (const cx_t<T> *)x_reg, (T)lam, (cx_t<T> *)alm_out,
+                                            p->cur_skip);
+    AKRA_CUDA_TRY(cudaGetLastError());
+    p->launches++;
+    return AKRA_OK;
+}
+
+int legendre_chunks(int nunits, const LegShape &s) { return (nunits + s.NT * s.P - 1) / (s.NT * s.P); }
+
+template akra_status legendre_synth<float>(akra_plan, const LegShape &, LegMode, const void *, void *,
+                                           int, const int *, int, cudaStream_t);
+template akra_status legendre_synth<double>(akra_plan, const LegShape &, LegMode, const void *,
+                                            void *, int, const int *, int, cudaStream_t);
+template akra_status legendre_adjoint<float>(akra_plan, const LegShape &, const void *, void *, int,
+                                             const int *, int, int *, cudaStream_t);
+template akra_status legendre_adjoint<double>(akra_plan, const LegShape &, const void *, void *, int,
+                                              const int *, int, int *, cudaStream_t);
+template akra_status adjoint_epilogue<float>(akra_plan, LegMode, const void *, int, const void *,
+                                             double, void *, int, cudaStream_t);
+template akra_status adjoint_epilogue<double>(akra_plan, LegMode, const void *, int, const void *,
+                                              double, void *, int, cudaStream_t);
+
+}  // namespace akra

@@ -1,0 +1,738 @@
+// akra_plan.cu -- plan creation (HEALPix ring geometry, recurrence coefficients, ring
+// twiddles), pixel weights, operator composition and the C entry points for the
+// transforms and H.  The CG entry points live in akra_cg.cu.
+#include <cstdarg>
+#include <cstring>
+#include <algorithm>
+#include <mutex>
+
+#include "akra_internal.cuh"
+
+namespace akra {
+
+static thread_local char g_err[1024] = "";
+
+void set_error(const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+// ---------------------------------------------------------------------------
+// K1: HEALPix RING geometry (Gorski et al. 2005; the pixelisation of Sec. III B)
+//   ring i (1..4N-1), i' = min(i, 4N-i):
+//     polar  i' < N : 1 - z = i'^2/(3N^2), n = 4i', σ = 1, first = 2i'(i'-1)
+//     belt  i' >= N : 1 - z = (2i'-N)/(3N), n = 4N, σ = (i'-N+1) mod 2,
+//                     first = 2N(N-1) + 4N(i'-N)
+//   south rings mirror: z -> -z, first = npix - first(i') - n.
+//   unit u (0..2N-1): north ring u+1 and its mirror 4N-u-1 (none for the equator u = 2N-1)
+// ---------------------------------------------------------------------------
+__global__ void k_geometry(int N, RingInfo *rings, UnitInfo *units)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const long long NN = N;
+    const long long npix = 12 * NN * NN;
+    auto ring_of = [&](int ring, RingInfo &ri, double &omz) {
+        const bool north = ring <= 2 * N;
+        const long long i = north ? ring : 4 * NN - ring;
+        long long first;
+        if (i < N) {
+            omz = (double)(i * i) / (3.0 * (double)(NN * NN));
+            ri.nphi = (int)(4 * i);
+            ri.sigma = 1;
+            ri.ilen = (int)i;
+            first = 2 * i * (i - 1);
+        } else {
+            omz = (double)(2 * i - NN) / (3.0 * (double)NN);
+            ri.nphi = (int)(4 * NN);
+            ri.sigma = (int)((i - NN + 1) & 1);
+            ri.ilen = N;
+            first = 2 * NN * (NN - 1) + 4 * NN * (i - NN);
+        }
+        ri.z = north ? 1.0 - omz : omz - 1.0;
+        ri.st = sqrt(omz * (2.0 - omz));
+        ri.first = north ? first : npix - first - ri.nphi;
+        ri.tw_off = 4LL * ri.ilen * (ri.ilen - 1);
+        ri.pad = 0;
+    };
+    if (t < 4 * N - 1) {
+        RingInfo ri;
+        double omz;
+        ring_of(t + 1, ri, omz);
+        rings[t] = ri;
+    }
+    if (t < 2 * N) {
+        RingInfo ri;
+        double omz;   // 1 - cos θ of the north ring, exact from the ring formulas
+        ring_of(t + 1, ri, omz);
+        UnitInfo u;
+        u.x = ri.z;
+        u.ls = 0.5 * log2(0.5 * omz);          // sin^2(θ/2) = (1 - z)/2
+        u.lc = 0.5 * log2(0.5 * (2.0 - omz));  // cos^2(θ/2) = (1 + z)/2
+        u.ring_n = t;
+        u.ring_s = (t + 1 < 2 * N) ? (4 * N - (t + 1)) - 1 : -1;
+        units[t] = u;
+    }
+}
+
+// Recurrence coefficients per (l, m) for the λp/λm recurrence (Wigner-d, normalised, s = 2):
+//   A_l = sqrt((2l+3)/(2l+1)) (l+1)(2l+1) / sqrt(((l+1)^2-m^2)((l+1)^2-4))
+//   B_l = sqrt((l^2-m^2)(l^2-4))/(l(2l+1)) sqrt((2l+1)/(2l-1))   (0 at l = l0)
+//   entry {A_l, A_l B_l, A_l 2m/(l(l+1)), 0}
+__global__ void k_coef(int L, double4_32a *c64, float4 *c32)
+{
+    const int m = blockIdx.x;
+    const long long mbase = (long long)m * (2 * L + 1 - m) / 2;
+    const int l0 = m > 2 ? m : 2;
+    for (int l = m + threadIdx.x; l <= L; l += blockDim.x) {
+        double a = 0, b = 0, c = 0;
+        if (l >= l0) {
+            const double dl = l, mm = (double)m * m, lp1 = l + 1.0;
+            a = sqrt((2 * dl + 3) / (2 * dl + 1)) * lp1 * (2 * dl + 1) /
+                sqrt((lp1 * lp1 - mm) * (lp1 * lp1 - 4.0));
+            const double B = (l == l0) ? 0.0
+                                       : sqrt((dl * dl - mm) * (dl * dl - 4.0)) / (dl * (2 * dl + 1)) *
+                                             sqrt((2 * dl + 1) / (2 * dl - 1));
+            b = a * B;
+            c = a * 2.0 * m / (dl * (dl + 1));
+        }
+        c64[mbase + l] = make_double4_32a(a, b, c, 0.0);
+        c32[mbase + l] = make_float4((float)a, (float)b, (float)c, 0.f);
+    }
+}
+
+// log2 of the seed prefactor sqrt((2 l0 + 1)/(4π) (2 l0)!/(a! b!)), a = m+2, b = |m-2|,
+// l0 = max(m, 2) (single-term Goldberg sum at l = l0); also D_l of Eq. 3.
+__global__ void k_seed(int L, double *seedC, double *D64, float *D32)
+{
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m > L) return;
+    const int l0 = m > 2 ? m : 2, a = m + 2, b = m >= 2 ? m - 2 : 2 - m;
+    seedC[m] = 0.5 * (log2(2.0 * l0 + 1.0) - log2(4.0 * 3.14159265358979323846) +
+                      (lgamma(2.0 * l0 + 1.0) - lgamma(a + 1.0) - lgamma(b + 1.0)) /
+                          0.69314718055994530942);
+    const double l = m;
+    const double D = m >= 2 ? -sqrt((l - 1) * (l + 2) / (l * (l + 1))) : 0.0;
+    D64[m] = D;
+    D32[m] = (float)D;
+}
+
+// e^{iπ t/n} for every ring length n = 4i (i = 1..N), t in [0, 2n), at offset 4i(i-1)
+__global__ void k_twiddles(int N, double2 *tw64, float2 *tw32)
+{
+    const int i = blockIdx.y + 1;
+    const int n = 4 * i;
+    const long long off = 4LL * i * (i - 1);
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < 2 * n; t += gridDim.x * blockDim.x) {
+        double s, c;
+        sincospi((double)t / (double)n, &s, &c);
+        tw64[off + t] = make_double2(c, s);
+        tw32[off + t] = make_float2((float)c, (float)s);
+    }
+}
+
+__global__ void k_iota(int n, int *out)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) out[t] = t;
+}
+
+// per ring: W = ω M N^-1 in both precisions; count of masked pixels, Σ N^-1 over them,
+// and the number of invalid (negative or non-finite) entries
+__global__ void k_weights(const RingInfo *rings, const double *ninv, double omega, double *W64,
+                          float *W32, double *ring_sum, double *ring_cnt, double *ring_bad)
+{
+    const RingInfo ri = rings[blockIdx.x];
+    double s = 0, c = 0, bad = 0;
+    for (int j = threadIdx.x; j < ri.nphi; j += blockDim.x) {
+        const double v = ninv[ri.first + j];
+        const bool ok = isfinite(v) && v >= 0;
+        const double w = (ok && v > 0) ? omega * v : 0.0;
+        W64[ri.first + j] = w;
+        W32[ri.first + j] = (float)w;
+        if (!ok) bad += 1;
+        if (ok && v > 0) {
+            s += v;
+            c += 1;
+        }
+    }
+    __shared__ double sh[3][256];
+    sh[0][threadIdx.x] = s;
+    sh[1][threadIdx.x] = c;
+    sh[2][threadIdx.x] = bad;
+    __syncthreads();
+    for (int off = blockDim.x / 2; off > 0; off >>= 1) {
+        if (threadIdx.x < off)
+            for (int q = 0; q < 3; q++) sh[q][threadIdx.x] += sh[q][threadIdx.x + off];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        ring_sum[blockIdx.x] = sh[0][0];
+        ring_cnt[blockIdx.x] = sh[1][0];
+        ring_bad[blockIdx.x] = sh[2][0];
+    }
+}
+
+// radices of n = 4i: odd primes first (direct passes, smallest Ns), then 4s and a 2
+static FftFactors factorize(int n)
+{
+    FftFactors f{};
+    int m = n;
+    std::vector<int> small, big;
+    while (m % 4 == 0) { small.push_back(4); m /= 4; }
+    while (m % 2 == 0) { small.push_back(2); m /= 2; }
+    for (int d = 3; (long long)d * d <= m; d += 2)
+        while (m % d == 0) { big.push_back(d); m /= d; }
+    if (m > 1) big.push_back(m);
+    for (int d : big) f.f[f.nf++] = d;
+    for (int d : small) f.f[f.nf++] = d;
+    return f;
+}
+
+akra_status ws_reserve(akra_plan p, Workspace &w, size_t bytes)
+{
+    if (bytes <= w.bytes) return AKRA_OK;
+    if (w.ptr) {
+        AKRA_CUDA_TRY(cudaDeviceSynchronize());
+        cudaFree(w.ptr);
+        w.ptr = nullptr;
+        w.bytes = 0;
+    }
+    p->ws_gen++;   // captured CG graphs that refer to the old buffer are now stale
+    if (cudaMalloc(&w.ptr, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        w.ptr = nullptr;
+        set_error("workspace allocation of %zu bytes failed", bytes);
+        return AKRA_ENOMEM;
+    }
+    w.bytes = bytes;
+    return AKRA_OK;
+}
+
+size_t plan_device_bytes(akra_plan p)
+{
+    return p->bytes_tables + p->phi.bytes + p->partial.bytes + p->cg.bytes + p->red.bytes;
+}
+
+LegShape leg_shape(akra_plan p, akra_prec prec, int R)
+{
+    const long long key = (long long)prec * 1000 + (R > 999 ? 999 : R);
+    auto it = p->shapes.find(key);
+    if (it != p->shapes.end()) return it->second;
+    // defaults: FP32 4 ring pairs per thread, FP64 2 (DFMA-bound; fewer registers)
+    if (prec == AKRA_F64) return R >= 2 ? LegShape{1, 128, 2} : LegShape{2, 128, 1};
+    if (R >= 4) return LegShape{1, 128, 4};
+    if (R >= 2) return LegShape{2, 128, 2};
+    return LegShape{4, 128, 1};
+}
+
+template <typename T> static akra_prec prec_of();
+template <> akra_prec prec_of<float>() { return AKRA_F32; }
+template <> akra_prec prec_of<double>() { return AKRA_F64; }
+
+static size_t phi_bytes(akra_plan p, size_t elem, int R)
+{
+    return (size_t)R * p->nring * (2 * (size_t)p->lmax + 1) * elem;
+}
+
+template <typename T>
+akra_status op_synth(akra_plan p, LegMode mode, const void *alm, void *map, bool weighted, int R,
+                     cudaStream_t st)
+{
+    AKRA_TRY(ws_reserve(p, p->phi, phi_bytes(p, sizeof(cx_t<T>), R)));
+    const LegShape s = leg_shape(p, prec_of<T>(), R);
+    AKRA_TRY(legendre_synth<T>(p, s, mode, alm, p->phi.ptr, R, p->d_all_units, p->nunit, st));
+    return ring_fft<T>(p, FftMode::Synth, p->phi.ptr, nullptr, map, weighted, R, p->d_all_rings,
+                       p->nring, st);
+}
+
+
+
+template <typename T>
+akra_status op_adjoint(akra_plan p, LegMode mode, const void *map, void *alm, bool weighted, int R,
+                       cudaStream_t st)
+{
+    const LegShape s = leg_shape(p, prec_of<T>(), R);
+    AKRA_TRY(ws_reserve(p, p->phi, phi_bytes(p, sizeof(cx_t<T>), R)));
+    AKRA_TRY(ws_reserve(p, p->partial, (size_t)legendre_chunks(p->nunit, s) * R * p->ntri * 4 *
+                                           sizeof(T)));
+    AKRA_TRY(ring_fft<T>(p, FftMode::Adjoint, p->phi.ptr, map, nullptr, weighted, R,
+                         p->d_all_rings, p->nring, st));
+    int nch = 0;
+    AKRA_TRY(legendre_adjoint<T>(p, s, p->phi.ptr, p->partial.ptr, R, p->d_all_units, p->nunit,
+                                 &nch, st));
+    return adjoint_epilogue<T>(p, mode, p->partial.ptr, nch, nullptr, 0.0, alm, R, st);
+}
+
+template <typename T>
+akra_status op_H(akra_plan p, const void *x, void *y, int R, cudaStream_t st)
+{
+    const LegShape s = leg_shape(p, prec_of<T>(), R);
+    AKRA_TRY(ws_reserve(p, p->phi, phi_bytes(p, sizeof(cx_t<T>), R)));
+    AKRA_TRY(ws_reserve(p, p->partial, (size_t)legendre_chunks(p->n_active_units, s) * R *
+                                           p->ntri * 4 * sizeof(T)));
+    AKRA_TRY(legendre_synth<T>(p, s, LegMode::KS, x, p->phi.ptr, R, p->d_active_units,
+                               p->n_active_units, st));
+    AKRA_TRY(ring_fft<T>(p, FftMode::Happly, p->phi.ptr, nullptr, nullptr, true, R,
+                         p->d_active_rings, p->n_active_rings, st));
+    int nch = 0;
+    AKRA_TRY(legendre_adjoint<T>(p, s, p->phi.ptr, p->partial.ptr, R, p->d_active_units,
+                                 p->n_active_units, &nch, st));
+    return adjoint_epilogue<T>(p, LegMode::KS, p->partial.ptr, nch, x, p->lambda_eff, y, R, st);
+}
+
+template akra_status op_synth<float>(akra_plan, LegMode, const void *, void *, bool, int, cudaStream_t);
+template akra_status op_synth<double>(akra_plan, LegMode, const void *, void *, bool, int, cudaStream_t);
+template akra_status op_adjoint<float>(akra_plan, LegMode, const void *, void *, bool, int, cudaStream_t);
+template akra_status op_adjoint<double>(akra_plan, LegMode, const void *, void *, bool, int, cudaStream_t);
+template akra_status op_H<float>(akra_plan, const void *, void *, int, cudaStream_t);
+template akra_status op_H<double>(akra_plan, const void *, void *, int, cudaStream_t);
+
+}  // namespace akra
+
+using namespace akra;
+
+// ---------------------------------------------------------------------------
+// C entry points
+// ---------------------------------------------------------------------------
+extern "C" const char *akra_last_error(void) { return g_err; }
+
+extern "C" const char *akra_version(void) { return "akra-gb300 1.0 (sm_103a)"; }
+
+template <typename P> static akra_status dev_alloc(akra_plan p, P **ptr, size_t bytes)
+{
+    if (cudaMalloc((void **)ptr, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("plan table allocation of %zu bytes failed", bytes);
+        return AKRA_ENOMEM;
+    }
+    p->bytes_tables += bytes;
+    return AKRA_OK;
+}
+
+namespace akra { akra_status ring_fft_prepare(akra_plan p); }
+
+static akra_status plan_build(akra_plan p)
+{
+    const int N = p->nside, L = p->lmax;
+    AKRA_TRY(dev_alloc(p, &p->d_rings, sizeof(RingInfo) * p->nring));
+    AKRA_TRY(dev_alloc(p, &p->d_units, sizeof(UnitInfo) * p->nunit));
+    AKRA_TRY(dev_alloc(p, &p->d_factors, sizeof(FftFactors) * (N + 1)));
+    AKRA_TRY(dev_alloc(p, &p->d_coef64, sizeof(double4_32a) * p->ntri));
+    AKRA_TRY(dev_alloc(p, &p->d_coef32, sizeof(float4) * p->ntri));
+    AKRA_TRY(dev_alloc(p, &p->d_seedC, sizeof(double) * (L + 1)));
+    AKRA_TRY(dev_alloc(p, &p->d_D64, sizeof(double) * (L + 1)));
+    AKRA_TRY(dev_alloc(p, &p->d_D32, sizeof(float) * (L + 1)));
+    const size_t ntw = 4ull * N * (N + 1);
+    AKRA_TRY(dev_alloc(p, &p->d_tw64, sizeof(double2) * ntw));
+    AKRA_TRY(dev_alloc(p, &p->d_tw32, sizeof(float2) * ntw));
+    AKRA_TRY(dev_alloc(p, &p->d_all_rings, sizeof(int) * p->nring));
+    AKRA_TRY(dev_alloc(p, &p->d_all_units, sizeof(int) * p->nunit));
+    AKRA_TRY(dev_alloc(p, &p->d_active_rings, sizeof(int) * p->nring));
+    AKRA_TRY(dev_alloc(p, &p->d_active_units, sizeof(int) * p->nunit));
+    AKRA_TRY(dev_alloc(p, &p->d_ring_active, p->nring));
+    AKRA_TRY(dev_alloc(p, &p->d_W64, sizeof(double) * p->npix));
+    AKRA_TRY(dev_alloc(p, &p->d_W32, sizeof(float) * p->npix));
+
+    std::vector<FftFactors> fac(N + 1);
+    for (int i = 1; i <= N; i++) fac[i] = factorize(4 * i);
+    AKRA_CUDA_TRY(cudaMemcpy(p->d_factors, fac.data(), sizeof(FftFactors) * (N + 1),
+                             cudaMemcpyHostToDevice));
+    const int nthr = 256;
+    k_geometry<<<(p->nring + nthr - 1) / nthr, nthr>>>(N, p->d_rings, p->d_units);
+    AKRA_CUDA_TRY(cudaGetLastError());
+    k_coef<<<L + 1, 256>>>(L, p->d_coef64, p->d_coef32);
+    AKRA_CUDA_TRY(cudaGetLastError());
+    k_seed<<<(L + 1 + 127) / 128, 128>>>(L, p->d_seedC, p->d_D64, p->d_D32);
+    AKRA_CUDA_TRY(cudaGetLastError());
+    k_twiddles<<<dim3(4, N), 256>>>(N, p->d_tw64, p->d_tw32);
+    AKRA_CUDA_TRY(cudaGetLastError());
+    k_iota<<<(p->nring + 255) / 256, 256>>>(p->nring, p->d_all_rings);
+    k_iota<<<(p->nunit + 255) / 256, 256>>>(p->nunit, p->d_all_units);
+    AKRA_CUDA_TRY(cudaGetLastError());
+    AKRA_CUDA_TRY(cudaMemset(p->d_ring_active, 1, p->nring));
+    AKRA_TRY(ring_fft_prepare(p));
+    AKRA_CUDA_TRY(cudaStreamCreateWithFlags(&p->stream, cudaStreamNonBlocking));
+    AKRA_CUDA_TRY(cudaEventCreateWithFlags(&p->ev_a, cudaEventDisableTiming));
+    AKRA_CUDA_TRY(cudaEventCreateWithFlags(&p->ev_b, cudaEventDisableTiming));
+    AKRA_CUDA_TRY(cudaDeviceSynchronize());
+    return AKRA_OK;
+}
+
+extern "C" akra_status akra_plan_create(int nside, int lmax, akra_plan *out)
+{
+    if (!out) {
+        set_error("akra_plan_create: out is NULL");
+        return AKRA_EINVAL;
+    }
+    *out = nullptr;
+    if (nside < 1 || nside > kMaxNside) {
+        set_error("akra_plan_create: nside %d outside [1, %d]", nside, kMaxNside);
+        return AKRA_EINVAL;
+    }
+    if (lmax < 2 || lmax > 4 * nside) {
+        set_error("akra_plan_create: lmax %d outside [2, 4 nside = %d]", lmax, 4 * nside);
+        return AKRA_EINVAL;
+    }
+    akra_plan p = new (std::nothrow) akra_plan_s();
+    if (!p) {
+        set_error("akra_plan_create: host allocation failed");
+        return AKRA_ENOMEM;
+    }
+    p->nside = nside;
+    p->lmax = lmax;
+    p->nring = 4 * nside - 1;
+    p->nunit = 2 * nside;
+    p->npix = 12LL * nside * nside;
+    p->ntri = (long long)(lmax + 1) * (lmax + 2) / 2;
+    p->omega = 4.0 * 3.14159265358979323846 / (double)p->npix;
+    cudaGetDevice(&p->device);
+    akra_status s = plan_build(p);
+    if (s != AKRA_OK) {
+        akra_plan_destroy(p);
+        return s;
+    }
+    *out = p;
+    return AKRA_OK;
+}
+
+
+
+extern "C" void akra_plan_destroy(akra_plan p)
+{
+    if (!p) return;
+    cudaDeviceSynchronize();
+    cg_release_graphs(p);
+    void *ptrs[] = {p->d_rings, p->d_units, p->d_factors, p->d_coef64, p->d_coef32, p->d_seedC,
+                    p->d_D64, p->d_D32, p->d_tw64, p->d_tw32, p->d_all_rings, p->d_all_units,
+                    p->d_active_rings, p->d_active_units, p->d_ring_active, p->d_W64, p->d_W32,
+                    p->phi.ptr, p->partial.ptr, p->cg.ptr, p->red.ptr};
+    for (void *q : ptrs)
+        if (q) cudaFree(q);
+    if (p->stream) cudaStreamDestroy(p->stream);
+    if (p->ev_a) cudaEventDestroy(p->ev_a);
+    if (p->ev_b) cudaEventDestroy(p->ev_b);
+    delete p;
+}
+
+extern "C" akra_status akra_plan_describe(akra_plan p, akra_plan_desc *out)
+{
+    if (!p || !out) {
+        set_error("akra_plan_describe: NULL argument");
+        return AKRA_EINVAL;
+    }
+    out->nside = p->nside;
+    out->lmax = p->lmax;
+    out->nring = p->nring;
+    out->nunit = p->nunit;
+    out->npix = p->npix;
+    out->ntri = p->ntri;
+    out->has_weights = p->has_weights ? 1 : 0;
+    out->n_active_rings = p->n_active_rings;
+    out->lambda = p->lambda;
+    out->lambda_eff = p->lambda_eff;
+    out->precond = p->precond;
+    out->omega = p->omega;
+    out->device_bytes = plan_device_bytes(p);
+    out->kernel_launches = p->launches;
+    return AKRA_OK;
+}
+
+extern "C" akra_status akra_plan_set_weights(akra_plan p, const double *d_ninv, double lambda,
+                                             void *stream)
+{
+    if (!p || !d_ninv || !(lambda >= 0) || !std::isfinite(lambda)) {
+        set_error("akra_plan_set_weights: NULL plan/ninv or invalid lambda");
+        return AKRA_EINVAL;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const int nr = p->nring;
+    double *d_stats = nullptr;
+    if (cudaMalloc(&d_stats, sizeof(double) * 3 * nr) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("akra_plan_set_weights: scratch allocation failed");
+        return AKRA_ENOMEM;
+    }
+    k_weights<<<nr, 256, 0, st>>>(p->d_rings, d_ninv, p->omega, p->d_W64, p->d_W32, d_stats,
+                                  d_stats + nr, d_stats + 2 * nr);
+    std::vector<double> h(3 * (size_t)nr);
+    cudaError_t e1 = cudaGetLastError();
+    cudaError_t e2 = cudaMemcpyAsync(h.data(), d_stats, sizeof(double) * 3 * nr,
+                                     cudaMemcpyDeviceToHost, st);
+    cudaError_t e3 = cudaStreamSynchronize(st);
+    cudaFree(d_stats);
+    if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
+        set_error("akra_plan_set_weights: CUDA failure %s",
+                  cudaGetErrorString(e1 != cudaSuccess ? e1 : e2 != cudaSuccess ? e2 : e3));
+        return AKRA_ECUDA;
+    }
+    double sum = 0, cnt = 0, bad = 0;
+    std::vector<unsigned char> active(nr);
+    std::vector<int> rings;
+    for (int r = 0; r < nr; r++) {
+        sum += h[r];
+        cnt += h[nr + r];
+        bad += h[2 * nr + r];
+        active[r] = h[nr + r] > 0 ? 1 : 0;
+        if (active[r]) rings.push_back(r);
+    }
+    if (bad > 0) {
+        set_error("akra_plan_set_weights: %.0f negative or non-finite N^-1 entries", bad);
+        return AKRA_EINVAL;
+    }
+    std::vector<int> units;
+    const int N = p->nside;
+    for (int u = 0; u < p->nunit; u++) {
+        const int rn = u, rs = (u + 1 < 2 * N) ? 4 * N - (u + 1) - 1 : -1;
+        if (active[rn] || (rs >= 0 && active[rs])) units.push_back(u);
+    }
+    AKRA_CUDA_TRY(cudaMemcpy(p->d_ring_active, active.data(), nr, cudaMemcpyHostToDevice));
+    if (!rings.empty())
+        AKRA_CUDA_TRY(cudaMemcpy(p->d_active_rings, rings.data(), sizeof(int) * rings.size(),
+                                 cudaMemcpyHostToDevice));
+    if (!units.empty())
+        AKRA_CUDA_TRY(cudaMemcpy(p->d_active_units, units.data(), sizeof(int) * units.size(),
+                                 cudaMemcpyHostToDevice));
+    p->n_active_rings = (int)rings.size();
+    p->n_active_units = (int)units.size();
+    p->lambda = lambda;
+    p->lambda_eff = cnt > 0 ? lambda * sum / cnt : 0.0;
+    p->precond = 1.0 / (sum / (double)p->npix + p->lambda_eff);
+    if (!std::isfinite(p->precond)) p->precond = 1.0;
+    p->has_weights = true;
+    return AKRA_OK;
+}
+
+static akra_status check_common(akra_plan p, akra_prec prec, const void *a, const void *b, int R,
+                                const char *who)
+{
+    if (!p || !a || !b) {
+        set_error("%s: NULL plan or array", who);
+        return AKRA_EINVAL;
+    }
+    if (prec != AKRA_F64 && prec != AKRA_F32) {
+        set_error("%s: precision must be AKRA_F64 or AKRA_F32", who);
+        return AKRA_EINVAL;
+    }
+    if (R < 1 || R > 65535) {
+        set_error("%s: R = %d outside [1, 65535]", who, R);
+        return AKRA_EINVAL;
+    }
+    return AKRA_OK;
+}
+
+extern "C" akra_status akra_synth_spin2(akra_plan p, akra_prec prec, const void *d_alm,
+                                        void *d_map, int R, void *stream)
+{
+    AKRA_TRY(check_common(p, prec, d_alm, d_map, R, "akra_synth_spin2"));
+    cudaStream_t st = (cudaStream_t)stream;
+    return prec == AKRA_F64 ? op_synth<double>(p, LegMode::Synth, d_alm, d_map, false, R, st)
+                            : op_synth<float>(p, LegMode::Synth, d_alm, d_map, false, R, st);
+}
+
+extern "C" akra_status akra_adjoint_synth_spin2(akra_plan p, akra_prec prec, const void *d_map,
+                                                void *d_alm, int R, void *stream)
+{
+    AKRA_TRY(check_common(p, prec, d_map, d_alm, R, "akra_adjoint_synth_spin2"));
+    cudaStream_t st = (cudaStream_t)stream;
+    return prec == AKRA_F64 ? op_adjoint<double>(p, LegMode::Synth, d_map, d_alm, false, R, st)
+                            : op_adjoint<float>(p, LegMode::Synth, d_map, d_alm, false, R, st);
+}
+
+extern "C" akra_status akra_apply_A(akra_plan p, akra_prec prec, const void *d_x, void *d_map,
+                                    int weighted, int R, void *stream)
+{
+    AKRA_TRY(check_common(p, prec, d_x, d_map, R, "akra_apply_A"));
+    if (weighted && !p->has_weights) {
+        set_error("akra_apply_A: weighted operator before akra_plan_set_weights");
+        return AKRA_ENOWEIGHTS;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    return prec == AKRA_F64 ? op_synth<double>(p, LegMode::KS, d_x, d_map, weighted != 0, R, st)
+                            : op_synth<float>(p, LegMode::KS, d_x, d_map, weighted != 0, R, st);
+}
+
+extern "C" akra_status akra_apply_At(akra_plan p, akra_prec prec, const void *d_map, void *d_x,
+                                     int weighted, int R, void *stream)
+{
+    AKRA_TRY(check_common(p, prec, d_map, d_x, R, "akra_apply_At"));
+    if (weighted && !p->has_weights) {
+        set_error("akra_apply_At: weighted operator before akra_plan_set_weights");
+        return AKRA_ENOWEIGHTS;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    return prec == AKRA_F64 ? op_adjoint<double>(p, LegMode::KS, d_map, d_x, weighted != 0, R, st)
+                            : op_adjoint<float>(p, LegMode::KS, d_map, d_x, weighted != 0, R, st);
+}
+
+extern "C" akra_status akra_apply_H(akra_plan p, akra_prec prec, const void *d_x, void *d_y, int R,
+                                    void *stream)
+{
+    AKRA_TRY(check_common(p, prec, d_x, d_y, R, "akra_apply_H"));
+    if (!p->has_weights) {
+        set_error("akra_apply_H: called before akra_plan_set_weights");
+        return AKRA_ENOWEIGHTS;
+    }
+    if (d_x == d_y) {
+        set_error("akra_apply_H: d_x and d_y must not overlap");
+        return AKRA_EINVAL;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    return prec == AKRA_F64 ? op_H<double>(p, d_x, d_y, R, st) : op_H<float>(p, d_x, d_y, R, st);
+}
+
+// ---------------------------------------------------------------------------
+// autotuner: time every compiled Legendre tile shape (synthesis + adjoint over the units
+// the operator will use) and keep the fastest for this (precision, R)
+// ---------------------------------------------------------------------------
+template <typename T>
+static akra_status tune_one(akra_plan p, akra_prec prec, int R, cudaStream_t st)
+{
+    std::vector<LegShape> cands;
+    if (R >= 4) cands.push_back({1, 128, 4});
+    if (R >= 2) {
+        cands.push_back({2, 128, 2});
+        cands.push_back({1, 128, 2});
+    }
+    cands.push_back({4, 128, 1});
+    cands.push_back({2, 128, 1});
+    cands.push_back({1, 128, 1});
+    const int *units = p->has_weights ? p->d_active_units : p->d_all_units;
+    const int nunits = p->has_weights ? p->n_active_units : p->nunit;
+    if (nunits == 0) return AKRA_OK;
+    size_t max_part = 0;
+    for (auto &c : cands)
+        max_part = std::max(max_part, (size_t)legendre_chunks(nunits, c) * (size_t)R * (size_t)p->ntri * 4 * sizeof(T));
+    AKRA_TRY(ws_reserve(p, p->phi, (size_t)R * p->nring * (2 * (size_t)p->lmax + 1) * sizeof(cx_t<T>)));
+    AKRA_TRY(ws_reserve(p, p->partial, max_part));
+    void *alm = nullptr;
+    const size_t abytes = (size_t)R * 2 * p->ntri * sizeof(cx_t<T>);
+    if (cudaMalloc(&alm, abytes) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("akra_autotune: scratch allocation failed");
+        return AKRA_ENOMEM;
+    }
+    cudaMemsetAsync(alm, 0, abytes, st);
+    cudaMemsetAsync(p->phi.ptr, 0, p->phi.bytes, st);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    LegShape pick = cands.back();
+    akra_status s = AKRA_OK;
+    for (auto &c : cands) {
+        float tot = 0;
+        for (int rep = 0; rep < 3 && s == AKRA_OK; rep++) {
+            int nch = 0;
+            cudaEventRecord(e0, st);
+            s = legendre_synth<T>(p, c, LegMode::KS, alm, p->phi.ptr, R, units, nunits, st);
+            if (s == AKRA_OK) s = legendre_adjoint<T>(p, c, p->phi.ptr, p->partial.ptr, R, units, nunits, &nch, st);
+            cudaEventRecord(e1, st);
+            cudaEventSynchronize(e1);
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0) tot += ms;   // the first run is a warm-up
+        }
+        if (s != AKRA_OK) break;
+        if (tot < best) {
+            best = tot;
+            pick = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(alm);
+    if (s != AKRA_OK) return s;
+    p->shapes[(long long)prec * 1000 + (R > 999 ? 999 : R)] = pick;
+    p->ws_gen++;   // captured CG iterations used the previous shape
+    return AKRA_OK;
+}
+
+extern "C" akra_status akra_autotune(akra_plan p, akra_prec prec, int R, void *stream)
+{
+    if (!p || R < 1 || R > 65535 || (prec != AKRA_F64 && prec != AKRA_F32 && prec != AKRA_MIXED)) {
+        set_error("akra_autotune: invalid argument");
+        return AKRA_EINVAL;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    if (prec == AKRA_F64 || prec == AKRA_MIXED) AKRA_TRY(tune_one<double>(p, AKRA_F64, R, st));
+    if (prec == AKRA_F32 || prec == AKRA_MIXED) AKRA_TRY(tune_one<float>(p, AKRA_F32, R, st));
+    return AKRA_OK;
+}
+
+// ---------------------------------------------------------------------------
+// stage timing of one H application (diagnostics for the roofline report)
+// ---------------------------------------------------------------------------
+template <typename T>
+static akra_status time_stages(akra_plan p, int R, int reps, cudaStream_t st, double *ms)
+{
+    const akra_prec prec = prec_of<T>();
+    const LegShape s = leg_shape(p, prec, R);
+    const int nch = legendre_chunks(p->n_active_units, s);
+    AKRA_TRY(ws_reserve(p, p->phi, phi_bytes(p, sizeof(cx_t<T>), R)));
+    AKRA_TRY(ws_reserve(p, p->partial, (size_t)nch * R * p->ntri * 4 * sizeof(T)));
+    void *x = nullptr, *y = nullptr;
+    const size_t ab = (size_t)R * 2 * p->ntri * sizeof(cx_t<T>);
+    if (cudaMalloc(&x, ab) != cudaSuccess || cudaMalloc(&y, ab) != cudaSuccess) {
+        cudaGetLastError();
+        if (x) cudaFree(x);
+        set_error("akra_time_H_stages: scratch allocation failed");
+        return AKRA_ENOMEM;
+    }
+    cudaMemsetAsync(x, 0, ab, st);
+    cudaEvent_t ev[5];
+    for (auto &e : ev) cudaEventCreate(&e);
+    double acc[5] = {0, 0, 0, 0, 0};
+    akra_status s1 = AKRA_OK;
+    for (int rep = 0; rep <= reps && s1 == AKRA_OK; rep++) {
+        int n2 = 0;
+        cudaEventRecord(ev[0], st);
+        s1 = legendre_synth<T>(p, s, LegMode::KS, x, p->phi.ptr, R, p->d_active_units, p->n_active_units, st);
+        cudaEventRecord(ev[1], st);
+        if (s1 == AKRA_OK)
+            s1 = ring_fft<T>(p, FftMode::Happly, p->phi.ptr, nullptr, nullptr, true, R, p->d_active_rings,
+                             p->n_active_rings, st);
+        cudaEventRecord(ev[2], st);
+        if (s1 == AKRA_OK)
+            s1 = legendre_adjoint<T>(p, s, p->phi.ptr, p->partial.ptr, R, p->d_active_units,
+                                     p->n_active_units, &n2, st);
+        cudaEventRecord(ev[3], st);
+        if (s1 == AKRA_OK) s1 = adjoint_epilogue<T>(p, LegMode::KS, p->partial.ptr, n2, x, p->lambda_eff, y, R, st);
+        cudaEventRecord(ev[4], st);
+        cudaEventSynchronize(ev[4]);
+        if (rep == 0) continue;   // warm-up
+        for (int k = 0; k < 4; k++) {
+            float t = 0;
+            cudaEventElapsedTime(&t, ev[k], ev[k + 1]);
+            acc[k] += t;
+        }
+        float t = 0;
+        cudaEventElapsedTime(&t, ev[0], ev[4]);
+        acc[4] += t;
+    }
+    for (auto &e : ev) cudaEventDestroy(e);
+    cudaFree(x);
+    cudaFree(y);
+    if (s1 != AKRA_OK) return s1;
+    AKRA_CUDA_TRY(cudaGetLastError());
+    for (int k = 0; k < 5; k++) ms[k] = acc[k] / reps;
+    return AKRA_OK;
+}
+
+extern "C" akra_status akra_time_H_stages(akra_plan p, akra_prec prec, int R, int reps, void *stream,
+                                          double *ms_out)
+{
+    if (!p || !ms_out || reps < 1 || R < 1 || (prec != AKRA_F64 && prec != AKRA_F32)) {
+        set_error("akra_time_H_stages: invalid argument");
+        return AKRA_EINVAL;
+    }
+    if (!p->has_weights) {
+        set_error("akra_time_H_stages: called before akra_plan_set_weights");
+        return AKRA_ENOWEIGHTS;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    return prec == AKRA_F64 ? time_stages<double>(p, R, reps, st, ms_out)
+                            : time_stages<float>(p, R, reps, st, ms_out);
+}

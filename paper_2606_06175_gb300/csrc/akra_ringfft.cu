@@ -1,0 +1,312 @@
+// akra_ringfft.cu -- per-ring phase sums of the spin-2 synthesis and of its transpose
+// (the φ half of SHT^-1 / SHT in Sec. II B), fused with the pixel-space diagonal
+// W = ω M N^-1 (Sec. II B, "Pixel space (diagonal)").
+//
+// Ring with n pixels at φ_j = π(2j+σ)/n.  Synthesis direction:
+//   f_j = Σ_{m=-L}^{L} Φ(m) e^{imφ_j} = Σ_k e^{2πijk/n} F[k],
+//   F[k] = e^{iπσk/n} Σ_{q: |k+nq|<=L} (-1)^{σq} Φ(k+nq)          (fold)
+// Transpose direction (w_j = W_j f_j or the caller's map):
+//   Φ'(m) = Σ_j w_j e^{-imφ_j} = e^{-iπσk/n} (-1)^{σq} Σ_j w_j e^{-2πijk/n},  m = k + nq.
+// The length-n DFTs run in shared memory, one CTA per ring: a mixed-radix Stockham
+// autosort with radices 4 and 2 as register butterflies and every odd prime factor as a
+// direct (output-oriented) pass; every pass reads all its inputs into registers,
+// synchronises, then writes in place.  Twiddles come from the plan's per-length table e^{iπt/n}, t < 2n.
+#include "akra_internal.cuh"
+
+namespace akra {
+
+constexpr int FFT_NT = 512;
+constexpr int FFT_NMAX = 4 * kMaxNside;
+
+template <typename T>
+__device__ __forceinline__ cx_t<T> cmul(cx_t<T> a, cx_t<T> b)
+{
+    return cx_t<T>{fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x)};
+}
+
+template <typename T, int DIR>
+__device__ __forceinline__ cx_t<T> twid(const cx_t<T> *__restrict__ tw, int t)
+{
+    cx_t<T> w = tw[t];
+    if (DIR < 0) w.y = -w.y;
+    return w;
+}
+
+// R-point DFT in registers (R = 2, 4): out[r] = Σ_q v[q] e^{DIR 2πi qr/R}
+template <typename T, int R, int DIR>
+__device__ __forceinline__ void dft_small(cx_t<T> (&v)[R])
+{
+    using C2 = cx_t<T>;
+    if constexpr (R == 2) {
+        const C2 a = v[0], b = v[1];
+        v[0] = C2{a.x + b.x, a.y + b.y};
+        v[1] = C2{a.x - b.x, a.y - b.y};
+    } else if constexpr (R == 4) {
+        const C2 t0{v[0].x + v[2].x, v[0].y + v[2].y};
+        const C2 t1{v[0].x - v[2].x, v[0].y - v[2].y};
+        const C2 t2{v[1].x + v[3].x, v[1].y + v[3].y};
+        const C2 d{v[1].x - v[3].x, v[1].y - v[3].y};
+        const C2 t3 = DIR > 0 ? C2{-d.y, d.x} : C2{d.y, -d.x};   // DIR·i·d
+        v[0] = C2{t0.x + t2.x, t0.y + t2.y};
+        v[2] = C2{t0.x - t2.x, t0.y - t2.y};
+        v[1] = C2{t1.x + t3.x, t1.y + t3.y};
+        v[3] = C2{t1.x - t3.x, t1.y - t3.y};
+    }
+}
+
+template <typename T, int R, int DIR>
+__device__ void pass_small(cx_t<T> *data, int n, int Ns, const cx_t<T> *__restrict__ tw)
+{
+    constexpr int MB = (FFT_NMAX / R + FFT_NT - 1) / FFT_NT;
+    cx_t<T> v[MB][R];
+    const int nb = n / R;
+    const int twstep = (2 * n) / (Ns * R);
+#pragma unroll
+    for (int b = 0; b < MB; b++) {
+        const int j = threadIdx.x + b * FFT_NT;
+        if (j < nb) {
+            const int k = j % Ns;
+#pragma unroll
+            for (int q = 0; q < R; q++) v[b][q] = data[j + q * nb];
+            if (Ns > 1) {
+#pragma unroll
+                for (int q = 1; q < R; q++) v[b][q] = cmul<T>(v[b][q], twid<T, DIR>(tw, twstep * q * k));
+            }
+            dft_small<T, R, DIR>(v[b]);
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int b = 0; b < MB; b++) {
+        const int j = threadIdx.x + b * FFT_NT;
+        if (j < nb) {
+            const int k = j % Ns;
+            const int base = (j / Ns) * Ns * R + k;
+#pragma unroll
+            for (int q = 0; q < R; q++) data[base + q * Ns] = v[b][q];
+        }
+    }
+    __syncthreads();
+}
+
+// direct pass for an odd prime radix p (3, 5, 7 and larger): y[(j/Ns)Ns p + k + r Ns] = Σ_q x[j + q n/p] w_{Ns p}^{q(k + Ns r)}
+template <typename T, int DIR>
+__device__ void pass_generic(cx_t<T> *data, int n, int Ns, int p, const cx_t<T> *__restrict__ tw)
+{
+    constexpr int MO = (FFT_NMAX + FFT_NT - 1) / FFT_NT;
+    cx_t<T> out[MO];
+    const int NsP = Ns * p, nb = n / p, twstep = (2 * n) / NsP;
+#pragma unroll
+    for (int b = 0; b < MO; b++) {
+        const int o = threadIdx.x + b * FFT_NT;
+        if (o < n) {
+            const int g = o / NsP, rem = o - g * NsP, rr = rem / Ns, k = rem - rr * Ns;
+            const int j = g * Ns + k, step = k + Ns * rr;
+            cx_t<T> acc{0, 0};
+            int ex = 0;
+            for (int q = 0; q < p; q++) {
+                const cx_t<T> t = cmul<T>(data[j + q * nb], twid<T, DIR>(tw, twstep * ex));
+                acc.x += t.x;
+                acc.y += t.y;
+                ex += step;
+                if (ex >= NsP) ex -= NsP;
+            }
+            out[b] = acc;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int b = 0; b < MO; b++) {
+        const int o = threadIdx.x + b * FFT_NT;
+        if (o < n) data[o] = out[b];
+    }
+    __syncthreads();
+}
+
+template <typename T, int DIR>
+__device__ void fft_inplace(cx_t<T> *data, int n, const FftFactors &fac,
+                            const cx_t<T> *__restrict__ tw)
+{
+    int Ns = 1;
+    for (int i = 0; i < fac.nf; i++) {
+        const int R = fac.f[i];
+        switch (R) {
+        case 4: pass_small<T, 4, DIR>(data, n, Ns, tw); break;
+        case 2: pass_small<T, 2, DIR>(data, n, Ns, tw); break;
+        default: pass_generic<T, DIR>(data, n, Ns, R, tw); break;
+        }
+        Ns *= R;
+    }
+}
+
+__device__ __forceinline__ int floordiv(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
+
+template <typename T, int MODE>
+__global__ void __launch_bounds__(FFT_NT)
+k_ring_fft(int L, int nring, long long npix, int nmax, const int *__restrict__ rings,
+           const RingInfo *__restrict__ rinfo, const FftFactors *__restrict__ factors,
+           const cx_t<T> *__restrict__ tw_all, const T *__restrict__ W, int weighted,
+           cx_t<T> *__restrict__ phi, const T *__restrict__ map_in, T *__restrict__ map_out,
+           const int *__restrict__ skip)
+{
+    using C2 = cx_t<T>;
+    if (skip && *skip) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C2 *data = reinterpret_cast<C2 *>(smem_raw);
+    C2 *red = data + nmax;
+    const int ring = rings ? rings[blockIdx.x] : (int)blockIdx.x;
+    const int r = blockIdx.y;
+    const int tid = threadIdx.x;
+    const RingInfo ri = rinfo[ring];
+    const int n = ri.nphi, sigma = ri.sigma;
+    const long long first = ri.first;
+    const FftFactors fac = factors[ri.ilen];
+    const C2 *tw = tw_all + ri.tw_off;
+    C2 *prow = phi + ((size_t)r * nring + ring) * (2 * (size_t)L + 1) + L;   // prow[m], |m| <= L
+
+    if (MODE != (int)FftMode::Adjoint) {
+        // fold Φ(m) into n bins
+        if (n >= FFT_NT) {
+            for (int k = tid; k < n; k += FFT_NT) {
+                const int qlo = -((L + k) / n), qhi = floordiv(L - k, n);
+                C2 acc{0, 0};
+                for (int q = qlo; q <= qhi; q++) {
+                    const C2 v = prow[k + n * q];
+                    if (sigma && (q & 1)) { acc.x -= v.x; acc.y -= v.y; }
+                    else { acc.x += v.x; acc.y += v.y; }
+                }
+                data[k] = sigma ? cmul<T>(acc, tw[k]) : acc;
+            }
+        } else {
+            const int G = FFT_NT / n, g = tid / n, k = tid - g * n;
+            if (g < G) {
+                const int qlo = -((L + k) / n), qhi = floordiv(L - k, n);
+                C2 acc{0, 0};
+                for (int q = qlo + g; q <= qhi; q += G) {
+                    const C2 v = prow[k + n * q];
+                    if (sigma && (q & 1)) { acc.x -= v.x; acc.y -= v.y; }
+                    else { acc.x += v.x; acc.y += v.y; }
+                }
+                red[g * n + k] = acc;
+            }
+            __syncthreads();
+            for (int kk = tid; kk < n; kk += FFT_NT) {
+                C2 acc{0, 0};
+                for (int gg = 0; gg < G; gg++) {
+                    acc.x += red[gg * n + kk].x;
+                    acc.y += red[gg * n + kk].y;
+                }
+                data[kk] = sigma ? cmul<T>(acc, tw[kk]) : acc;
+            }
+        }
+        __syncthreads();
+        fft_inplace<T, +1>(data, n, fac, tw);
+        if (MODE == (int)FftMode::Synth) {
+            T *o1 = map_out + ((size_t)r * 2 + 0) * npix + first;
+            T *o2 = map_out + ((size_t)r * 2 + 1) * npix + first;
+            for (int j = tid; j < n; j += FFT_NT) {
+                C2 v = data[j];
+                if (weighted) {
+                    const T wj = W[first + j];
+                    v.x *= wj;
+                    v.y *= wj;
+                }
+                o1[j] = v.x;
+                o2[j] = v.y;
+            }
+            return;
+        }
+        for (int j = tid; j < n; j += FFT_NT) {
+            const T wj = W[first + j];
+            data[j].x *= wj;
+            data[j].y *= wj;
+        }
+        __syncthreads();
+    } else {
+        const T *u1 = map_in + ((size_t)r * 2 + 0) * npix + first;
+        const T *u2 = map_in + ((size_t)r * 2 + 1) * npix + first;
+        for (int j = tid; j < n; j += FFT_NT) {
+            C2 v{u1[j], u2[j]};
+            if (weighted) {
+                const T wj = W[first + j];
+                v.x *= wj;
+                v.y *= wj;
+            }
+            data[j] = v;
+        }
+        __syncthreads();
+    }
+    fft_inplace<T, -1>(data, n, fac, tw);
+    // unfold: Φ'(m) = e^{-iπσk/n} (-1)^{σq} Ŵ[k],  m = k + nq
+    for (int mm = tid; mm < 2 * L + 1; mm += FFT_NT) {
+        const int m = mm - L;
+        const int q = floordiv(m, n), k = m - q * n;
+        C2 v = data[k];
+        if (sigma) {
+            v = cmul<T>(v, twid<T, -1>(tw, k));
+            if (q & 1) { v.x = -v.x; v.y = -v.y; }
+        }
+        prow[m] = v;
+    }
+}
+
+template <typename T> const cx_t<T> *tw_ptr(akra_plan p);
+template <> const float2 *tw_ptr<float>(akra_plan p) { return p->d_tw32; }
+template <> const double2 *tw_ptr<double>(akra_plan p) { return p->d_tw64; }
+template <typename T> const T *W_ptr(akra_plan p);
+template <> const float *W_ptr<float>(akra_plan p) { return p->d_W32; }
+template <> const double *W_ptr<double>(akra_plan p) { return p->d_W64; }
+
+template <typename T, int MODE>
+static akra_status launch_fft(akra_plan p, void *phi, const void *map_in, void *map_out,
+                              bool weighted, int R, const int *rings, int nrings, cudaStream_t st)
+{
+    const int nmax = 4 * p->nside;
+    const size_t smem = (size_t)(nmax + FFT_NT) * sizeof(cx_t<T>);
+    auto kern = k_ring_fft<T, MODE>;
+    dim3 grid(nrings, R);
+    kern<<<grid, FFT_NT, smem, st>>>(p->lmax, p->nring, p->npix, nmax, rings, p->d_rings,
+                                     p->d_factors, tw_ptr<T>(p), W_ptr<T>(p), weighted ? 1 : 0,
+                                     (cx_t<T> *)phi, (const T *)map_in, (T *)map_out, p->cur_skip);
+    AKRA_CUDA_TRY(cudaGetLastError());
+    p->launches++;
+    return AKRA_OK;
+}
+
+template <typename T>
+akra_status ring_fft(akra_plan p, FftMode mode, void *phi, const void *map_in, void *map_out,
+                     bool weighted, int R, const int *rings, int nrings, cudaStream_t st)
+{
+    if (nrings <= 0) return AKRA_OK;
+    switch (mode) {
+    case FftMode::Synth:
+        return launch_fft<T, 0>(p, phi, map_in, map_out, weighted, R, rings, nrings, st);
+    case FftMode::Adjoint:
+        return launch_fft<T, 1>(p, phi, map_in, map_out, weighted, R, rings, nrings, st);
+    default:
+        return launch_fft<T, 2>(p, phi, map_in, map_out, weighted, R, rings, nrings, st);
+    }
+}
+
+// raise the dynamic shared-memory limit of every ring-FFT kernel once (at plan creation,
+// never inside a stream capture)
+akra_status ring_fft_prepare(akra_plan p)
+{
+    const int nmax = 4 * p->nside;
+    const int s32 = (nmax + FFT_NT) * (int)sizeof(float2);
+    const int s64 = (nmax + FFT_NT) * (int)sizeof(double2);
+    AKRA_CUDA_TRY(cudaFuncSetAttribute(k_ring_fft<float, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, s32));
+    AKRA_CUDA_TRY(cudaFuncSetAttribute(k_ring_fft<float, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, s32));
+    AKRA_CUDA_TRY(cudaFuncSetAttribute(k_ring_fft<float, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, s32));
+    AKRA_CUDA_TRY(cudaFuncSetAttribute(k_ring_fft<double, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, s64));
+    AKRA_CUDA_TRY(cudaFuncSetAttribute(k_ring_fft<double, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, s64));
+    AKRA_CUDA_TRY(cudaFuncSetAttribute(k_ring_fft<double, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, s64));
+    return AKRA_OK;
+}
+
+template akra_status ring_fft<float>(akra_plan, FftMode, void *, const void *, void *, bool, int,
+                                     const int *, int, cudaStream_t);
+template akra_status ring_fft<double>(akra_plan, FftMode, void *, const void *, void *, bool, int,
+                                      const int *, int, cudaStream_t);
+
+}  // namespace akra

@@ -1,0 +1,268 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle.
+
+Tolerances: FP64 operators and FP64 solves at rel. L2 1e-10; FP32 operators at
+tol32(L) = 4 ε32 L (FP32 rounding of the l-recurrence grows linearly in the number of steps);
+mixed-precision solves at 1e-6 on the solved alm against the oracle solved to 1e-12.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+import synthetic as S
+from paper_2606_06175_gb300 import akra as A
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+TOL64 = 1e-10
+
+
+def tol32(lmax):
+    # the three-term recurrence is neutrally stable on the oscillatory side, so FP32 rounding
+    # grows linearly with the number of l-steps: rel. error ~ ε32 L / 2 (measured); bound 4 ε32 L
+    return 4 * 2.0 ** -24 * max(lmax, 16)
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+def alm_dev(pairs, prec=A.F64):
+    arr = np.stack([np.stack(p) for p in pairs])
+    return torch.from_numpy(arr).to(DEV, torch.complex128 if prec == A.F64 else torch.complex64)
+
+
+def map_dev(maps, prec=A.F64):
+    arr = np.stack([np.stack(m) for m in maps])
+    return torch.from_numpy(arr).to(DEV, torch.float64 if prec == A.F64 else torch.float32)
+
+
+_plans = {}
+
+
+def plan(N, L):
+    if (N, L) not in _plans:
+        _plans[(N, L)] = A.akra_plan_create(N, L)
+    return _plans[(N, L)]
+
+
+SIZES = [(1, 2), (2, 5), (4, 8), (8, 31), (16, 40), (32, 64), (64, 150), (256, 300)]
+
+
+@pytest.mark.parametrize("N,L", SIZES)
+@pytest.mark.parametrize("prec", [A.F64, A.F32])
+def test_synthesis_matches_oracle(N, L, prec):
+    rng = np.random.default_rng(N * 1000 + L)
+    aE, aB = S.random_alm(L, rng), S.random_alm(L, rng)
+    g = A.akra_synth_spin2(plan(N, L), prec, alm_dev([(aE, aB)], prec))[0].cpu().numpy()
+    ref = np.stack(O.synth_spin2(N, L, aE, aB))
+    err = rel(g, ref)
+    assert err < (TOL64 if prec == A.F64 else tol32(L)), err
+
+
+@pytest.mark.parametrize("N,L", SIZES)
+@pytest.mark.parametrize("prec", [A.F64, A.F32])
+def test_adjoint_matches_oracle(N, L, prec):
+    rng = np.random.default_rng(N * 1000 + L + 1)
+    u = rng.normal(size=(2, 12 * N * N))
+    a = A.akra_adjoint_synth_spin2(plan(N, L), prec, map_dev([u], prec))[0].cpu().numpy()
+    ref = np.stack(O.adjoint_synth_spin2(N, L, u[0], u[1]))
+    err = rel(a, ref)
+    assert err < (TOL64 if prec == A.F64 else tol32(L)), err
+    ls, ms = O.lm_arrays(L)
+    assert np.all(a[:, ms == 0].imag == 0)
+
+
+def _mask_weights(N, seed, cap=1.0):
+    rng = np.random.default_rng(seed)
+    th, ph = O.pixel_angles(N)
+    ninv = np.where((th > cap) & (np.sin(3 * ph) > -0.7), rng.poisson(20, 12 * N * N) / 0.26 ** 2, 0.0)
+    return ninv
+
+
+@pytest.mark.parametrize("N,L", [(4, 8), (8, 31), (16, 40), (32, 64), (256, 300)])
+@pytest.mark.parametrize("prec", [A.F64, A.F32])
+def test_H_matches_oracle(N, L, prec):
+    ninv = _mask_weights(N, N + L)
+    p = A.akra_plan_create(N, L)
+    A.akra_plan_set_weights(p, torch.from_numpy(ninv).to(DEV), 1e-3)
+    w = O.Weights(N, ninv, 1e-3)
+    d = A.akra_plan_describe(p)
+    assert abs(d["lambda_eff"] - w.lam_eff) <= 1e-12 * w.lam_eff
+    assert abs(d["precond"] - w.precond) <= 1e-12 * w.precond
+    rng = np.random.default_rng(L)
+    xE, xB = S.random_alm(L, rng), S.random_alm(L, rng)
+    h = A.akra_apply_H(p, prec, alm_dev([(xE, xB)], prec))[0].cpu().numpy()
+    ref = np.stack(O.apply_H(N, L, w, xE, xB))
+    err = rel(h, ref)
+    assert err < (TOL64 if prec == A.F64 else tol32(L)), err
+
+
+@pytest.mark.parametrize("prec", [A.F64, A.F32])
+def test_apply_A_and_At_match_oracle(prec):
+    N, L = 16, 40
+    ninv = _mask_weights(N, 3)
+    p = A.akra_plan_create(N, L)
+    A.akra_plan_set_weights(p, torch.from_numpy(ninv).to(DEV), 1e-3)
+    w = O.Weights(N, ninv, 1e-3)
+    rng = np.random.default_rng(11)
+    xE, xB = S.random_alm(L, rng), S.random_alm(L, rng)
+    tol = TOL64 if prec == A.F64 else tol32(L)
+    y = A.akra_apply_A(p, prec, alm_dev([(xE, xB)], prec))[0].cpu().numpy()
+    assert rel(y, np.stack(O.forward_A(N, L, xE, xB))) < tol
+    yw = A.akra_apply_A(p, prec, alm_dev([(xE, xB)], prec), weighted=True)[0].cpu().numpy()
+    assert rel(yw, w.W * np.stack(O.forward_A(N, L, xE, xB))) < tol
+    u = rng.normal(size=(2, 12 * N * N))
+    b = A.akra_apply_At(p, prec, map_dev([u], prec), weighted=True)[0].cpu().numpy()
+    assert rel(b, np.stack(O.rhs_b(N, L, w, u[0], u[1]))) < tol
+
+
+@pytest.mark.parametrize("prec", [A.F64, A.F32])
+def test_batched_rhs_match_oracle(prec):
+    """R = 3 right-hand sides in one launch (a ragged RHS group for the 2- and 4-wide tiles)."""
+    N, L = 16, 40
+    R = 3
+    rng = np.random.default_rng(5)
+    pairs = [(S.random_alm(L, rng), S.random_alm(L, rng)) for _ in range(R)]
+    p = plan(N, L)
+    g = A.akra_synth_spin2(p, prec, alm_dev(pairs, prec)).cpu().numpy()
+    tol = TOL64 if prec == A.F64 else tol32(L)
+    for r in range(R):
+        assert rel(g[r], np.stack(O.synth_spin2(N, L, *pairs[r]))) < tol
+    us = [rng.normal(size=(2, 12 * N * N)) for _ in range(R)]
+    a = A.akra_adjoint_synth_spin2(p, prec, map_dev(us, prec)).cpu().numpy()
+    for r in range(R):
+        assert rel(a[r], np.stack(O.adjoint_synth_spin2(N, L, us[r][0], us[r][1]))) < tol
+
+
+def test_adjoint_identity_gpu_512():
+    """<A x, u> = <x, A^T u> to 1e-12 on the GPU at Nside 512, lmax 1024 (FP64)."""
+    N, L = 512, 1024
+    p = plan(N, L)
+    rng = np.random.default_rng(9)
+    x = alm_dev([(S.random_alm(L, rng), S.random_alm(L, rng))])
+    u = torch.randn((1, 2, 12 * N * N), dtype=torch.float64, device=DEV)
+    g = A.akra_synth_spin2(p, A.F64, x)
+    a = A.akra_adjoint_synth_spin2(p, A.F64, u)
+    lhs = float((g * u).sum())
+    ls, ms = O.lm_arrays(L)
+    w = torch.from_numpy(np.where(ms == 0, 1.0, 2.0)).to(DEV)
+    xr, ar = x[0].real, a[0].real
+    xi = torch.where(torch.from_numpy(ms == 0).to(DEV), 0.0, x[0].imag)
+    rhs = float((w * (xr * ar + xi * a[0].imag)).sum())
+    assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
+
+
+# ---------------------------------------------------------------------------
+# CG
+# ---------------------------------------------------------------------------
+def _cap32():
+    wl = S.workload("cap32")
+    N, L = wl["nside"], wl["lmax"]
+    y = np.stack(O.forward_A(N, L, *wl["x_true"])) + wl["noise"]
+    y = np.where(wl["ninv"] > 0, y, 0.0)
+    return wl, N, L, y
+
+
+@pytest.fixture(scope="module")
+def cap32_ref():
+    wl, N, L, y = _cap32()
+    w = O.Weights(N, wl["ninv"], 1e-3)
+    (xE, xB), it, rr, hist = O.cg_solve(N, L, w, y[0], y[1], tol=1e-12, maxiter=3000)
+    return wl, N, L, y, np.stack([xE, xB]), it, hist
+
+
+def test_cg_fp64_cap32_matches_oracle(cap32_ref):
+    wl, N, L, y, xref, it_ref, _ = cap32_ref
+    p = A.akra_plan_create(N, L)
+    A.akra_plan_set_weights(p, torch.from_numpy(wl["ninv"]).to(DEV), 1e-3)
+    x, info = A.akra_cg_solve(p, A.F64, torch.from_numpy(y[None]).to(DEV), tol=1e-12, maxiter=3000)
+    assert info["status"] == 0 and info["relres"] < 1e-11
+    assert rel(x[0].cpu().numpy(), xref) < TOL64
+    # iteration count at the same tolerance equals the oracle's up to rounding
+    assert abs(info["iters"] - it_ref) <= 2
+    # the workload's own tolerance (1e-8): recursive and true FP64 residuals below it
+    x8, info8 = A.akra_cg_solve(p, A.F64, torch.from_numpy(y[None]).to(DEV), tol=1e-8, maxiter=3000)
+    assert info8["status"] == 0 and info8["relres"] < 1e-8
+
+
+def test_cg_mixed_cap32_matches_oracle(cap32_ref):
+    wl, N, L, y, xref, _, _ = cap32_ref
+    p = A.akra_plan_create(N, L)
+    A.akra_plan_set_weights(p, torch.from_numpy(wl["ninv"]).to(DEV), 1e-3)
+    x, info = A.akra_cg_solve(p, A.MIXED, torch.from_numpy(y[None]).to(DEV), tol=1e-9, maxiter=3000)
+    assert info["status"] == 0 and info["relres"] < 1e-9
+    assert info["outer"] >= 1 and info["h_applies_f32"] > 0
+    assert rel(x[0].cpu().numpy(), xref) < 1e-6
+
+
+def test_cg_fp32_cap32_close_to_oracle(cap32_ref):
+    wl, N, L, y, xref, _, _ = cap32_ref
+    p = A.akra_plan_create(N, L)
+    A.akra_plan_set_weights(p, torch.from_numpy(wl["ninv"]).to(DEV), 1e-3)
+    x, info = A.akra_cg_solve(p, A.F32, torch.from_numpy(y[None]).to(DEV, torch.float32), tol=1e-5,
+                              maxiter=3000)
+    assert info["status"] == 0
+    assert rel(x[0].cpu().numpy(), xref) < 1e-3
+
+
+def test_cg_multi_rhs_matches_single(cap32_ref):
+    wl, N, L, y, xref, _, _ = cap32_ref
+    p = A.akra_plan_create(N, L)
+    A.akra_plan_set_weights(p, torch.from_numpy(wl["ninv"]).to(DEV), 1e-3)
+    ys = np.stack([y, 0.5 * y, -y])
+    x, info = A.akra_cg_solve(p, A.F64, torch.from_numpy(ys).to(DEV), tol=1e-12, maxiter=3000)
+    assert info["status"] == 0
+    xs = x.cpu().numpy()
+    assert rel(xs[0], xref) < TOL64
+    assert rel(xs[1], 0.5 * xref) < TOL64
+    assert rel(xs[2], -xref) < TOL64
+
+
+def test_cg_solve_b_equals_cg_solve(cap32_ref):
+    wl, N, L, y, xref, _, _ = cap32_ref
+    p = A.akra_plan_create(N, L)
+    A.akra_plan_set_weights(p, torch.from_numpy(wl["ninv"]).to(DEV), 1e-3)
+    b = A.akra_apply_At(p, A.F64, torch.from_numpy(y[None]).to(DEV), weighted=True)
+    x, info = A.akra_cg_solve_b(p, A.F64, b, tol=1e-12, maxiter=3000)
+    assert rel(x[0].cpu().numpy(), xref) < TOL64
+
+
+# ---------------------------------------------------------------------------
+# error statuses (faults injected on the host; nothing faults the GPU)
+# ---------------------------------------------------------------------------
+def test_error_statuses():
+    N, L = 8, 12
+    p = A.akra_plan_create(N, L)
+    x = torch.zeros((1, 2, p.ntri), dtype=torch.complex128, device=DEV)
+    with pytest.raises(A.AkraError) as ei:
+        A.akra_apply_H(p, A.F64, x)
+    assert ei.value.status == 7   # ENOWEIGHTS
+    bad = torch.full((p.npix,), -1.0, dtype=torch.float64, device=DEV)
+    with pytest.raises(A.AkraError) as ei:
+        A.akra_plan_set_weights(p, bad, 1e-3)
+    assert ei.value.status == 1
+    nan = torch.full((p.npix,), float("nan"), dtype=torch.float64, device=DEV)
+    with pytest.raises(A.AkraError):
+        A.akra_plan_set_weights(p, nan, 1e-3)
+    A.akra_plan_set_weights(p, torch.full((p.npix,), 100.0, dtype=torch.float64, device=DEV), 1e-3)
+    y = torch.randn((1, 2, p.npix), dtype=torch.float64, device=DEV)
+    _, info = A.akra_cg_solve(p, A.F64, y, tol=1e-14, maxiter=1)
+    assert info["status"] == 4 and info["iters"] == 1          # ENOCONV after maxiter
+    A.akra_set_timeout(1e-9)
+    try:
+        with pytest.raises(A.AkraError) as ei:
+            A.akra_cg_solve(p, A.F64, y, tol=1e-14, maxiter=100000)
+        assert ei.value.status == 6                               # ETIMEOUT
+    finally:
+        A.akra_set_timeout(3600.0)
+        torch.cuda.synchronize()
+    # the plan and context are still usable after the timeout
+    _, info = A.akra_cg_solve(p, A.F64, y, tol=1e-8, maxiter=500)
+    assert info["status"] == 0
+    yn = y.clone()
+    yn[0, 0, 0] = float("nan")
+    _, info = A.akra_cg_solve(p, A.F64, yn, tol=1e-8, maxiter=50)
+    assert info["status"] == 5                                    # ENUMERIC
