@@ -1,0 +1,341 @@
+#!/usr/bin/env python
+"""Benchmark of the AKRA 3.0 hot path on GB300.
+
+One step = one mixed-precision PCG solve (FP32 inner CG, FP64 outer refinement) of the
+regularised normal equations at Nside 2048, lmax 4096 on a synthetic DES-like footprint, to
+relative residual 1e-6 -- every H application inside it runs the full chain (KS,
+spin-2 synthesis, ring FFT x W x FFT, exact adjoint, epilogue) in libakra.so.
+
+Metric (as named): "H-applies/s and CG solve time at Nside=2048 (mixed vs FP64, rel.res 1e-6)";
+`value` = H applications (FP32 inner + FP64 outer + the FP64 A^T of b) per second over the
+timed solves, whole job (summed over ranks); ms_per_step = the CG solve time.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun each rank solves its own replica (independent noise realisation): weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "H-applies/s and CG solve time at Nside=2048 (mixed vs FP64, rel.res 1e-6)"
+UNIT = "H-applies/s"
+NSIDE, LMAX, TOL = 2048, 4096, 1e-6
+SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+
+
+def fp32_peak_tflops(mhz=SM_MAX_MHZ):
+    # 152 SMs x 128 FP32 lanes x 2 flops (FMA) x clock
+    return SM_COUNT * FP32_LANES * 2 * mhz * 1e6 / 1e12
+
+
+class ClockSampler:
+    """nvidia-smi samples (SM clock, throttle reasons) while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            for k, nm in enumerate(names):
+                if len(r) > 5 + k and r[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.rows)}
+
+
+def make_inputs(rank, dev):
+    """des2048 workload (seeded), shear y = M (A x_true + n) formed with our FP64 forward operator."""
+    import torch
+
+    import synthetic as S
+    from paper_2606_06175_gb300 import akra as A
+
+    wl = S.workload("des2048")
+    plan = A.akra_plan_create(NSIDE, LMAX)
+    ninv = torch.from_numpy(wl["ninv"]).to(dev)
+    A.akra_plan_set_weights(plan, ninv, 1e-3)
+    x_true = torch.from_numpy(np.stack(wl["x_true"])[None]).to(dev)
+    y = A.akra_apply_A(plan, A.F64, x_true)
+    noise = wl["noise"]
+    if rank:
+        noise = S.shape_noise(wl["ninv"], np.random.default_rng(10_000 + rank))[0]
+    y += torch.from_numpy(noise[None]).to(dev)
+    y *= (ninv > 0).to(y.dtype)
+    torch.cuda.synchronize()
+    return plan, y, wl
+
+
+def legendre_flops(desc, R=1):
+    """Algorithmic FP32 work of one Legendre launch over the active ring pairs: every
+    (l >= 2, m, pair) step does two spin recurrences (6 flops-as-FMA ops) and 8 FMA of
+    contraction per RHS; flops = 2 x FMA-ops."""
+    steps = desc["n_active_units"] * (desc["ntri"] - 3)
+    return steps * (6 + 8 * R) * 2, steps
+
+
+def cpu_oracle_H_estimate(nside, lmax, target_s=15.0):
+    """Time the FP64 CPU oracle on a bounded sample of one full H application at (nside, lmax)
+    and extrapolate: Legendre synthesis on a sample of rings, the adjoint on a sample of m
+    columns, numpy ring DFTs on a sample of rings."""
+    from oracle import oracle as O
+
+    O.build()
+    th = O.num_threads()
+    nring = 4 * nside - 1
+    rng = np.random.default_rng(0)
+    nt = O.ntri(lmax)
+    aE = rng.normal(size=nt) + 1j * rng.normal(size=nt)
+    aB = rng.normal(size=nt) + 1j * rng.normal(size=nt)
+    nr = max(2 * th, 8)
+    rings = np.linspace(1, nring, nr).astype(np.int32)
+    t0 = time.perf_counter()
+    F = O.legendre_synth(nside, lmax, aE, aB, rings)
+    t_syn = time.perf_counter() - t0
+    # per-ring phase sums (numpy) on a sample of ring lengths
+    t0 = time.perf_counter()
+    nfft = 0
+    for k, r in enumerate(rings):
+        ct, st, n, sg, first = O.ring_info(nside, int(r))
+        f = O.ring_phase_sum(F[k], lmax, n, sg)
+        O.ring_phase_adjoint(f, lmax, sg)
+        nfft += 1
+    t_fft = (time.perf_counter() - t0) / nfft
+    # adjoint Legendre on a sample of m columns (cost ∝ lmax - m + 1)
+    nm = max(th, 4)
+    ms = np.linspace(0, lmax, nm).astype(np.int32)
+    G = np.ascontiguousarray(np.repeat(F[:1], nring, axis=0))
+    g = np.zeros(nt, np.complex128)
+    h = np.zeros(nt, np.complex128)
+    t0 = time.perf_counter()
+    O._lib().orc_legendre_adjoint(nside, lmax, O._dptr(G.view(np.float64)), len(ms), O._iptr(ms),
+                                  O._dptr(g.view(np.float64)), O._dptr(h.view(np.float64)))
+    t_adj = time.perf_counter() - t0
+    t_H = t_syn * nring / nr + t_adj * (lmax + 1) / nm + t_fft * nring
+    sample = ("FP64 oracle on %d of %d rings (Legendre synthesis), %d of %d m-columns "
+              "(adjoint), %d ring DFT pairs; extrapolated to one H application at Nside %d, "
+              "lmax %d (the oracle transforms every ring)" % (nr, nring, nm, lmax + 1, nfft, nside, lmax))
+    return t_H, th, sample, t_syn + t_adj + t_fft * nfft
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    vals = []
+    t_total = 0.0
+    for _ in range(args.warmup):
+        cpu_oracle_H_estimate(NSIDE, LMAX)
+    for _ in range(args.steps):
+        t_H, th, sample, spent = cpu_oracle_H_estimate(NSIDE, LMAX)
+        vals.append(1.0 / t_H)
+        t_total += spent
+    v = statistics.median(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / v,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "des2048: Nside 2048, lmax 4096, DES-like 4123 deg2 footprint, "
+                                   "one H application (the oracle is FP64 only)"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": th, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--fp64-solve", action="store_true", help="also run one full FP64 CG solve")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    import torch.distributed as dist
+
+    from paper_2606_06175_gb300 import akra as A
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    plan, y, wl = make_inputs(rank, dev)
+    A.akra_autotune(plan, A.MIXED, 1)
+    desc = A.akra_plan_describe(plan)
+    x = torch.empty((1, 2, plan.ntri), dtype=torch.complex128, device=dev)
+    for _ in range(args.warmup):
+        A.akra_cg_solve(plan, A.MIXED, y, x, tol=TOL, maxiter=2000)
+    torch.cuda.synchronize()
+
+    # ---- timed region: K mixed-precision solves, inputs resident in HBM ----
+    infos = []
+    barrier()
+    torch.cuda.synchronize()
+    launches0 = A.akra_plan_describe(plan)["kernel_launches"]
+    print("timed region starts after %d libakra kernel launches" % launches0, file=sys.stderr, flush=True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        ev0.record()
+        for _ in range(args.steps):
+            _, info = A.akra_cg_solve(plan, A.MIXED, y, x, tol=TOL, maxiter=2000)
+            infos.append(info)
+        ev1.record()
+        torch.cuda.synchronize()
+    barrier()
+    launches = A.akra_plan_describe(plan)["kernel_launches"] - launches0
+    elapsed = ev0.elapsed_time(ev1) / 1e3
+    t_max = elapsed
+    applies = sum(i["h_applies_f32"] + i["h_applies_f64"] for i in infos)
+    if world > 1:
+        tt = torch.tensor([elapsed], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt)
+        aa = torch.tensor([float(applies)], device=dev)
+        dist.all_reduce(aa)
+        applies_all = float(aa)
+    else:
+        applies_all = float(applies)
+    value = applies_all / t_max
+    ms_per_step = 1e3 * t_max / args.steps
+
+    # ---- per-stage kernel timing (CUDA events on this stream, kernels timed alone) ----
+    st32 = A.akra_time_H_stages(plan, A.F32, 1, 5)
+    st64 = A.akra_time_H_stages(plan, A.F64, 1, 2)
+    flops, steps = legendre_flops(desc)
+    dom = "legendre_adjoint" if st32["legendre_adjoint"] >= st32["legendre_synth"] else "legendre_synth"
+    achieved = flops / (st32[dom] * 1e-3) / 1e12
+    peak = fp32_peak_tflops()
+    roofline = {"bound": "alu", "kernel": "k_leg_adjoint<float>" if dom == "legendre_adjoint" else "k_leg_synth<float>",
+                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None,
+                "peak_basis": "152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz (unit counts and maximum clock)",
+                "flops_per_launch": flops, "lm_pair_steps_per_launch": steps,
+                "stage_ms_fp32": st32, "stage_ms_fp64": st64}
+
+    # ---- FP64 comparison (the plain FP64 GPU path) ----
+    t_h64 = st64["total"] * 1e-3
+    inner = infos[-1]["iters"]
+    fp64 = {"h_applies_per_s": 1.0 / t_h64, "h_apply_ms": st64["total"],
+            "fp32_h_apply_ms": st32["total"]}
+    if args.fp64_solve:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, info64 = A.akra_cg_solve(plan, A.F64, y, x, tol=TOL, maxiter=3000)
+        torch.cuda.synchronize()
+        fp64.update({"cg_solve_s": time.perf_counter() - t0, "cg_iters": info64["iters"],
+                     "relres": info64["relres"]})
+    else:
+        # FP64 CG needs about as many iterations as the FP32 inner CG took to reach the same
+        # residual; this is labelled as an extrapolation
+        fp64["cg_solve_s_extrapolated"] = (inner + 1) * t_h64
+        fp64["extrapolation"] = "FP64 H time x (mixed inner iterations + 1)"
+
+    # ---- end to end through the C ABI with host buffers ----
+    y_host = y.cpu().pin_memory()
+    x_host = torch.empty(x.shape, dtype=x.dtype).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    y_dev = y_host.to(dev, non_blocking=True)
+    _, info_e = A.akra_cg_solve(plan, A.MIXED, y_dev, x, tol=TOL, maxiter=2000)
+    x_host.copy_(x, non_blocking=True)
+    torch.cuda.synchronize()
+    t_e2e = time.perf_counter() - t0
+    e2e_applies = info_e["h_applies_f32"] + info_e["h_applies_f64"]
+    e2e = {"value": e2e_applies / t_e2e, "unit": UNIT, "h2d_bytes_per_step": y_host.numel() * 8,
+           "d2h_bytes_per_step": x_host.numel() * 16, "solve_s": t_e2e}
+
+    if rank != 0:
+        return
+    cpu = None
+    if not args.no_cpu_baseline:
+        t_H, th, sample, _ = cpu_oracle_H_estimate(NSIDE, LMAX)
+        cpu = {"value": 1.0 / t_H, "unit": UNIT, "cores": th, "kind": "oracle", "sample": sample,
+               "h_apply_s_extrapolated": t_H}
+    last = infos[-1]
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": "des2048: Nside 2048, lmax 4096, DES-like footprint %.0f deg2, "
+                               "mixed FP32-inner/FP64-refinement PCG to rel.res 1e-6"
+                               % (float(np.mean(wl["mask"])) * 41252.96),
+                   "nside": NSIDE, "lmax": LMAX, "tol": TOL, "rhs": 1,
+                   "active_rings": desc["n_active_rings"], "active_ring_pairs": desc["n_active_units"],
+                   "l2": "inputs larger than L2 (FP64 shear maps 805 MB, phase array 0.5-1.1 GB per H)"},
+        "cg": {"solve_s": ms_per_step / 1e3, "inner_iters": last["iters"], "outer": last["outer"],
+               "h_applies_f32": last["h_applies_f32"], "h_applies_f64": last["h_applies_f64"],
+               "relres": last["relres"], "per_inner_iter_ms": st32["total"]},
+        "fp64": fp64,
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+        "gpu_launches": launches, "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -74,6 +74,7 @@ typedef struct {
     long long npix, ntri;
     int has_weights;
     int n_active_rings;               /* rings with any N^-1 > 0 */
+    int n_active_units;               /* ring pairs with an active ring (the units H transforms) */
     double lambda, lambda_eff;        /* λ and λ_eff = λ <N^-1>_M  (Eq. 14) */
     double precond;                   /* scalar P of Eq. 15 */
     double omega;                     /* pixel area 4π/npix folded into W = ω M N^-1 */

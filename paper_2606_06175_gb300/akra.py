@@ -39,6 +39,7 @@ class PlanDesc(ctypes.Structure):
     _fields_ = [("nside", ctypes.c_int), ("lmax", ctypes.c_int), ("nring", ctypes.c_int),
                 ("nunit", ctypes.c_int), ("npix", ctypes.c_longlong), ("ntri", ctypes.c_longlong),
                 ("has_weights", ctypes.c_int), ("n_active_rings", ctypes.c_int),
+                ("n_active_units", ctypes.c_int),
                 ("lambda_", ctypes.c_double), ("lambda_eff", ctypes.c_double),
                 ("precond", ctypes.c_double), ("omega", ctypes.c_double),
                 ("device_bytes", ctypes.c_size_t), ("kernel_launches", ctypes.c_longlong)]

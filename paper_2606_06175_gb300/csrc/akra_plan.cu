@@ -431,6 +431,7 @@ extern "C" akra_status akra_plan_describe(akra_plan p, akra_plan_desc *out)
     out->ntri = p->ntri;
     out->has_weights = p->has_weights ? 1 : 0;
     out->n_active_rings = p->n_active_rings;
+    out->n_active_units = p->n_active_units;
     out->lambda = p->lambda;
     out->lambda_eff = p->lambda_eff;
     out->precond = p->precond;
