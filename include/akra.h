@@ -117,6 +117,23 @@ akra_status akra_plan_set_weights(akra_plan plan, const double *d_ninv, double l
 akra_status akra_synth_spin2(akra_plan plan, akra_prec prec, const void *d_alm, void *d_map,
                              int R, void *stream);
 
+/* akra_synth_spin2 without any device allocation.  The paper has no counterpart: this is
+ * for callers that cannot allocate at the point of the call -- inside a stream capture, under
+ * a memory pool or budget that forbids new allocations, or in a loop where the implicit
+ * synchronisation of cudaMalloc is not acceptable.  Same arguments, layouts and result as
+ * akra_synth_spin2 (the same kernels run); the phase-array scratch is a fixed 32 MiB
+ * device array inside the library (held by every GPU that loads the library until the
+ * process exits) instead of a plan workspace.  The plan itself must already exist.
+ * Limit: R * (4 nside - 1) * (2 lmax + 1) * sizeof(complex) <= 32 MiB (for R = 1: FP64 up to
+ * about nside 256 / lmax 512, FP32 up to nside 512 / lmax 1024); larger sizes return
+ * EINVAL with a message.  The first call on each device looks up the scratch address
+ * (cudaGetSymbolAddress): make that first call before any stream capture.  All calls share
+ * the one scratch array, so calls whose kernels overlap on the GPU (different streams, or
+ * several threads) race and corrupt each other's results; serialise them.  Nothing in the
+ * scratch needs clearing: each call writes every entry before reading it. */
+akra_status akra_synth_spin2_static(akra_plan plan, akra_prec prec, const void *d_alm,
+                                    void *d_map, int R, void *stream);
+
 /* Exact transpose of akra_synth_spin2 in the real-dof inner product:
  * (a_E, a_B) = (-(g+h)/2, (i/2)(g-h)) with g_lm = Σ_p (u1+iu2)_p 2Y*_lm(p) and
  * h_lm = Σ_p (u1-iu2)_p (-2)Y*_lm(p).  d_map [R][2][npix] -> d_alm [R][2][ntri].

@@ -49,7 +49,7 @@ EXPORTS = ["akra_plan_create", "akra_plan_destroy", "akra_last_error", "akra_ver
            "akra_plan_describe", "akra_plan_set_weights", "akra_synth_spin2",
            "akra_adjoint_synth_spin2", "akra_apply_A", "akra_apply_At", "akra_apply_H",
            "akra_cg_solve", "akra_cg_solve_b", "akra_set_timeout", "akra_autotune",
-           "akra_time_H_stages"]
+           "akra_time_H_stages", "akra_synth_spin2_static"]
 
 _lib_handle = None
 
@@ -87,6 +87,7 @@ def load(build_if_missing: bool = False):
         "akra_set_timeout": ([d], i),
         "akra_autotune": ([vp, i, i, vp], i),
         "akra_time_H_stages": ([vp, i, i, i, vp, ctypes.POINTER(ctypes.c_double)], i),
+        "akra_synth_spin2_static": ([vp, i, vp, vp, i, vp], i),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -179,6 +180,17 @@ def akra_synth_spin2(plan: Plan, prec: int, alm: torch.Tensor, out: torch.Tensor
         out = torch.empty((R, 2, plan.npix), dtype=_rdtype(prec), device=alm.device)
     _need(out, (R, 2, plan.npix), _rdtype(prec), "out")
     _check(load().akra_synth_spin2(plan.handle, prec, _ptr(alm), _ptr(out), R, _stream(stream)))
+    return out
+
+
+def akra_synth_spin2_static(plan: Plan, prec: int, alm: torch.Tensor, out: torch.Tensor, stream=None):
+    """akra_synth_spin2 that allocates no device memory (the caller passes `out`; the
+    library's fixed 32 MiB scratch holds the phase array).  For callers that cannot allocate
+    at the point of the call, e.g. inside a stream capture or under an allocation budget."""
+    R = alm.shape[0]
+    _need(alm, (R, 2, plan.ntri), _cdtype(prec), "alm")
+    _need(out, (R, 2, plan.npix), _rdtype(prec), "out")
+    _check(load().akra_synth_spin2_static(plan.handle, prec, _ptr(alm), _ptr(out), R, _stream(stream)))
     return out
 
 
