@@ -117,10 +117,17 @@ struct akra_plan_s {
     double4_32a *d_coef64 = nullptr;            // [ntri] {A, A B, A 2m/(l(l+1)), 0}
     float4 *d_coef32 = nullptr;
     double *d_seedC = nullptr;               // [lmax + 1] log2 seed prefactor per m
+    float4 *d_seed32 = nullptr;              // [(lmax+1) nunit] {2λ_l0, (-2)λ_l0, e bits, 0} (FP64-computed)
+    double4_32a *d_seed64 = nullptr;         // [(lmax+1) nunit] {2λ_l0, (-2)λ_l0, e, 0}
     double *d_D64 = nullptr;                 // [lmax + 1] KS kernel D_l
     float *d_D32 = nullptr;
     double2 *d_tw64 = nullptr;               // ring twiddles e^{iπ t/n}
     float2 *d_tw32 = nullptr;
+    int fft32_mmax = 0;                      // FP32 ring FFT: largest convolution length
+    int *d_fft32_M = nullptr;                // [nside + 1] per ring length index: M (== n if 2^k)
+    long long *d_fft32_off = nullptr;        // [nside + 1] offset of the chirp spectrum
+    float2 *d_fft32_tw2 = nullptr;           // e^{-2πi t/MMAX}
+    float2 *d_fft32_bhat = nullptr;          // chirp spectra (DIF output order)
     int *d_all_rings = nullptr;              // [nring] 0..nring-1
     int *d_all_units = nullptr;              // [nunit] 0..nunit-1
 
@@ -179,6 +186,10 @@ enum class FftMode { Synth = 0, Adjoint = 1, Happly = 2 };
 template <typename T>
 akra_status ring_fft(akra_plan p, FftMode mode, void *phi, const void *map_in, void *map_out,
                      bool weighted, int R, const int *rings, int nrings, cudaStream_t st);
+// FP32 ring FFT with Bluestein for non-power-of-two rings (akra_ringfft32.cu)
+akra_status ring_fft32_build(akra_plan p);
+akra_status ring_fft32(akra_plan p, FftMode mode, void *phi, const void *map_in, void *map_out,
+                       bool weighted, int R, const int *rings, int nrings, cudaStream_t st);
 
 // whole operators
 template <typename T>

@@ -17,24 +17,23 @@ namespace akra {
 
 constexpr int TL = 64;  // l-steps staged in shared memory per tile (even)
 
-// seeds 2λ_{l0 m} (vp) and (-2)λ_{l0 m} (vm) with a shared exponent index e
-template <typename T>
-__device__ __forceinline__ void seed_pair(int m, double Cm, double ls, double lc, T &vp, T &vm,
-                                          int &e)
+// seeds 2λ_{l0 m} (vp) and (-2)λ_{l0 m} (vm) with their shared exponent index e, from the
+// plan's table (computed in FP64 at plan creation)
+__device__ __forceinline__ void load_seed(const float4 *__restrict__ t, size_t i, float &vp,
+                                          float &vm, int &e)
 {
-    constexpr int Q = Scale<T>::Q;
-    const int a = m + 2, b = m >= 2 ? m - 2 : 2 - m;
-    const double Lp = Cm + a * ls + b * lc;   // log2 |2λ_{l0 m}|
-    const double Lm = Cm + b * ls + a * lc;   // log2 |(-2)λ_{l0 m}|
-    const double sp = (m & 1) ? -1.0 : 1.0;
-    const double sm = (m >= 2) ? sp : 1.0;
-    int ee = (int)floor((fmax(Lp, Lm) + 0.5 * Q) / Q);
-    if (ee > 0) ee = 0;
-    const double vplus = sp * exp2(Lp - (double)Q * ee);
-    const double vminus = sm * exp2(Lm - (double)Q * ee);
-    vp = (T)vplus;
-    vm = (T)vminus;
-    e = ee;
+    const float4 s = t[i];
+    vp = s.x;
+    vm = s.y;
+    e = __float_as_int(s.z);
+}
+__device__ __forceinline__ void load_seed(const double4_32a *__restrict__ t, size_t i, double &vp,
+                                          double &vm, int &e)
+{
+    const double4_32a s = t[i];
+    vp = s.x;
+    vm = s.y;
+    e = (int)s.z;
 }
 
 // ---------------------------------------------------------------------------
@@ -44,7 +43,7 @@ template <typename T, int P, int RG, int NT>
 __global__ void __launch_bounds__(NT)
 k_leg_synth(int L, int nring, long long ntri, int nchunks, int nunits,
             const int *__restrict__ units, const UnitInfo *__restrict__ uinfo,
-            const v4_t<T> *__restrict__ coef, const double *__restrict__ seedC,
+            const v4_t<T> *__restrict__ coef, const v4_t<T> *__restrict__ seeds, int nunit_all,
             const T *__restrict__ fl, const cx_t<T> *__restrict__ alm, int R,
             cx_t<T> *__restrict__ phi, const unsigned char *__restrict__ ring_active,
             const int *__restrict__ skip)
@@ -73,9 +72,8 @@ k_leg_synth(int L, int nring, long long ntri, int nchunks, int nunits,
         vp[k] = vm[k] = 0;
         e[k] = 0;
         if (uid[k] >= 0) {
-            const UnitInfo ui = uinfo[uid[k]];
-            x[k] = (T)ui.x;
-            seed_pair<T>(m, seedC[m], ui.ls, ui.lc, vp[k], vm[k], e[k]);
+            x[k] = (T)uinfo[uid[k]].x;
+            load_seed(seeds, (size_t)m * nunit_all + uid[k], vp[k], vm[k], e[k]);
         }
         vpo[k] = vmo[k] = 0;
 #pragma unroll
@@ -219,17 +217,17 @@ k_leg_synth(int L, int nring, long long ntri, int nchunks, int nunits,
 //     (l+m) even: E += 2λ U1 + (-2)λ U2,  B += 2λ U3 + (-2)λ U4
 //     (l+m) odd : E += 2λ U3 - (-2)λ U4,  B += 2λ U1 - (-2)λ U2
 // ---------------------------------------------------------------------------
-template <typename T>
-__device__ __forceinline__ T shfl_x(T v, int off)
-{
-    return __shfl_xor_sync(0xffffffffu, v, off);
-}
+// row stride (in elements) of the per-warp transpose buffer: conflict-free scalar stores of
+// one value per lane and 16-byte row loads (36 floats, 34 doubles)
+template <typename T> struct TrStride;
+template <> struct TrStride<float> { static constexpr int v = 36; };
+template <> struct TrStride<double> { static constexpr int v = 34; };
 
 template <typename T, int P, int RG, int NT>
 __global__ void __launch_bounds__(NT)
 k_leg_adjoint(int L, int nring, long long ntri, int nchunks, int nunits,
               const int *__restrict__ units, const UnitInfo *__restrict__ uinfo,
-              const v4_t<T> *__restrict__ coef, const double *__restrict__ seedC,
+              const v4_t<T> *__restrict__ coef, const v4_t<T> *__restrict__ seeds, int nunit_all,
               const cx_t<T> *__restrict__ phi, int R, T *__restrict__ partial,
               const unsigned char *__restrict__ ring_active, const int *__restrict__ skip)
 {
@@ -237,10 +235,14 @@ k_leg_adjoint(int L, int nring, long long ntri, int nchunks, int nunits,
     using C2 = cx_t<T>;
     using V4 = v4_t<T>;
     constexpr int NW = NT / 32;
-    constexpr int K = 8 / RG;   // l-steps per transpose-reduce block: K * 4 * RG = 32 values
+    constexpr int K = 8 / RG;   // l-steps per reduction block: K * 4 * RG = 32 values per lane
+    constexpr int S = TrStride<T>::v;
     static_assert(K >= 2 && K * 4 * RG == 32, "RG must be 1, 2 or 4");
-    __shared__ V4 s_coef[TL];
-    __shared__ T s_red[NW][TL][RG][4];
+    // l-tile: 64 steps, shorter for FP64 with several RHS to stay within 48 KB of static smem
+    constexpr int TLA = sizeof(T) == 8 ? 64 / RG : TL;
+    __shared__ V4 s_coef[TLA];
+    __shared__ T s_red[NW][TLA][RG][4];
+    __shared__ __align__(16) T s_tr[NW][32][S];
 
     const int m = blockIdx.x / nchunks;
     const int chunk = blockIdx.x - m * nchunks;
@@ -269,7 +271,7 @@ k_leg_adjoint(int L, int nring, long long ntri, int nchunks, int nunits,
         if (u >= 0) {
             ui = uinfo[u];
             x[k] = (T)ui.x;
-            seed_pair<T>(m, seedC[m], ui.ls, ui.lc, vp[k], vm[k], e[k]);
+            load_seed(seeds, (size_t)m * nunit_all + u, vp[k], vm[k], e[k]);
         }
 #pragma unroll
         for (int rr = 0; rr < RG; rr++) {
@@ -298,113 +300,106 @@ k_leg_adjoint(int L, int nring, long long ntri, int nchunks, int nunits,
         }
     }
 
-    for (int lt = l0; lt <= L; lt += TL) {
+    T (*tr)[S] = s_tr[warp];
+    for (int lt = l0; lt <= L; lt += TLA) {
         __syncthreads();
-        for (int i = tid; i < TL; i += NT) {
+        for (int i = tid; i < TLA; i += NT) {
             const int l = lt + i;
             s_coef[i] = (l <= L) ? coef[mbase + l] : V4{0, 0, 0, 0};
         }
         __syncthreads();
-        const int nl = min(TL, L - lt + 1);
+        const int nl = min(TLA, L - lt + 1);
         bool live = true;
 #pragma unroll
         for (int k = 0; k < P; k++) live &= (e[k] == 0);
         const bool all_live = __all_sync(0xffffffffu, live);
         const int nkb = (nl + K - 1) / K;
 
-        for (int kb = 0; kb < nkb; kb++) {
-            T ta[K][RG][4];
-#pragma unroll
-            for (int kk = 0; kk < K; kk++)
-#pragma unroll
-                for (int rr = 0; rr < RG; rr++)
-#pragma unroll
-                    for (int q = 0; q < 4; q++) ta[kk][rr][q] = 0;
-#pragma unroll
-            for (int kk = 0; kk < K; kk++) {
-                const int i = kb * K + kk;
-                const V4 c = s_coef[i];
-                const bool slotA = (kk & 1) == 0;
-                bool any = true;
-                if (!all_live) {
-                    bool a_ = false;
-#pragma unroll
-                    for (int k = 0; k < P; k++) a_ |= (e[k] == 0);
-                    any = __any_sync(0xffffffffu, a_);
-                }
-                if (any) {
-#pragma unroll
-                    for (int k = 0; k < P; k++) {
-                        const T lp = (!all_live && e[k] != 0) ? T(0) : vp[k];
-                        const T lm0 = (!all_live && e[k] != 0) ? T(0) : vm[k];
-                        const T lm = slotA ? lm0 : -lm0;
-#pragma unroll
-                        for (int rr = 0; rr < RG; rr++) {
-                            const C2 eP = slotA ? X1[k][rr] : X3[k][rr];
-                            const C2 eM = slotA ? X2[k][rr] : X4[k][rr];
-                            const C2 bP = slotA ? X3[k][rr] : X1[k][rr];
-                            const C2 bM = slotA ? X4[k][rr] : X2[k][rr];
-                            T *t = ta[kk][rr];
-                            t[0] = fma(lp, eP.x, fma(lm, eM.x, t[0]));
-                            t[1] = fma(lp, eP.y, fma(lm, eM.y, t[1]));
-                            t[2] = fma(lp, bP.x, fma(lm, bM.x, t[2]));
-                            t[3] = fma(lp, bP.y, fma(lm, bM.y, t[3]));
-                        }
-                    }
-                }
-#pragma unroll
-                for (int k = 0; k < P; k++) {
-                    const T t1 = fma(c.x, x[k], c.z);
-                    const T t2 = fma(c.x, x[k], -c.z);
-                    const T np = fma(t1, vp[k], -c.y * vpo[k]);
-                    const T nm = fma(t2, vm[k], -c.y * vmo[k]);
-                    vpo[k] = vp[k];
-                    vmo[k] = vm[k];
-                    vp[k] = np;
-                    vm[k] = nm;
-                    if (!all_live && e[k] < 0 &&
-                        (fabs(vp[k]) > Scale<T>::hi() || fabs(vm[k]) > Scale<T>::hi())) {
-                        vp[k] *= Scale<T>::inv();
-                        vm[k] *= Scale<T>::inv();
-                        vpo[k] *= Scale<T>::inv();
-                        vmo[k] *= Scale<T>::inv();
-                        e[k]++;
-                    }
-                }
-            }
-            // warp transpose-reduce: 32 values per lane -> lane j holds the warp sum of value j
-            T v[32];
-#pragma unroll
-            for (int kk = 0; kk < K; kk++)
-#pragma unroll
-                for (int rr = 0; rr < RG; rr++)
-#pragma unroll
-                    for (int q = 0; q < 4; q++) v[(kk * RG + rr) * 4 + q] = ta[kk][rr][q];
-#pragma unroll
-            for (int off = 16; off >= 1; off >>= 1) {
-                const bool upper = (lane & off) != 0;
-#pragma unroll
-                for (int i = 0; i < off; i++) {
-                    const T send = upper ? v[i] : v[i + off];
-                    const T keep = upper ? v[i + off] : v[i];
-                    v[i] = keep + shfl_x(send, off);
-                }
-            }
-            {
-                const int kk = lane / (4 * RG), rr = (lane / 4) % RG, q = lane & 3;
-                s_red[warp][kb * K + kk][rr][q] = v[0];
-            }
+        // K l-steps into ta[K][RG][4] (slot of step kk = parity of kk), then recur
+#define AKRA_ADJ_KBLOCK(GATED)                                                                  \
+    for (int kb = 0; kb < nkb; kb++) {                                                          \
+        T ta[K][RG][4];                                                                         \
+        _Pragma("unroll") for (int kk = 0; kk < K; kk++)                                        \
+            _Pragma("unroll") for (int rr = 0; rr < RG; rr++)                                   \
+                _Pragma("unroll") for (int q = 0; q < 4; q++) ta[kk][rr][q] = 0;                \
+        _Pragma("unroll") for (int kk = 0; kk < K; kk++) {                                      \
+            const V4 c = s_coef[kb * K + kk];                                                   \
+            const bool slotA = (kk & 1) == 0;                                                   \
+            bool any = true;                                                                    \
+            if (GATED) {                                                                        \
+                bool a_ = false;                                                                \
+                _Pragma("unroll") for (int k = 0; k < P; k++) a_ |= (e[k] == 0);                \
+                any = __any_sync(0xffffffffu, a_);                                              \
+            }                                                                                   \
+            if (any) {                                                                          \
+                _Pragma("unroll") for (int k = 0; k < P; k++) {                                 \
+                    const T lp = (GATED && e[k] != 0) ? T(0) : vp[k];                           \
+                    const T lm0 = (GATED && e[k] != 0) ? T(0) : vm[k];                          \
+                    const T lm = slotA ? lm0 : -lm0;                                            \
+                    _Pragma("unroll") for (int rr = 0; rr < RG; rr++) {                         \
+                        const C2 eP = slotA ? X1[k][rr] : X3[k][rr];                            \
+                        const C2 eM = slotA ? X2[k][rr] : X4[k][rr];                            \
+                        const C2 bP = slotA ? X3[k][rr] : X1[k][rr];                            \
+                        const C2 bM = slotA ? X4[k][rr] : X2[k][rr];                            \
+                        T *t = ta[kk][rr];                                                      \
+                        t[0] = fma(lp, eP.x, fma(lm, eM.x, t[0]));                              \
+                        t[1] = fma(lp, eP.y, fma(lm, eM.y, t[1]));                              \
+                        t[2] = fma(lp, bP.x, fma(lm, bM.x, t[2]));                              \
+                        t[3] = fma(lp, bP.y, fma(lm, bM.y, t[3]));                              \
+                    }                                                                           \
+                }                                                                               \
+            }                                                                                   \
+            _Pragma("unroll") for (int k = 0; k < P; k++) {                                     \
+                const T t1 = fma(c.x, x[k], c.z);                                               \
+                const T t2 = fma(c.x, x[k], -c.z);                                              \
+                const T np = fma(t1, vp[k], -c.y * vpo[k]);                                     \
+                const T nm = fma(t2, vm[k], -c.y * vmo[k]);                                     \
+                vpo[k] = vp[k];                                                                 \
+                vmo[k] = vm[k];                                                                 \
+                vp[k] = np;                                                                     \
+                vm[k] = nm;                                                                     \
+                if (GATED && e[k] < 0 &&                                                        \
+                    (fabs(vp[k]) > Scale<T>::hi() || fabs(vm[k]) > Scale<T>::hi())) {           \
+                    vp[k] *= Scale<T>::inv();                                                   \
+                    vm[k] *= Scale<T>::inv();                                                   \
+                    vpo[k] *= Scale<T>::inv();                                                  \
+                    vmo[k] *= Scale<T>::inv();                                                  \
+                    e[k]++;                                                                     \
+                }                                                                               \
+            }                                                                                   \
+        }                                                                                       \
+        /* warp transpose through shared memory: lane L's value i goes to tr[i][L]; lane j */  \
+        /* then sums row j, i.e. value j over all lanes */                                       \
+        _Pragma("unroll") for (int kk = 0; kk < K; kk++)                                        \
+            _Pragma("unroll") for (int rr = 0; rr < RG; rr++)                                   \
+                _Pragma("unroll") for (int q = 0; q < 4; q++)                                   \
+                    tr[(kk * RG + rr) * 4 + q][lane] = ta[kk][rr][q];                           \
+        __syncwarp();                                                                           \
+        T sum = 0;                                                                              \
+        _Pragma("unroll") for (int i = 0; i < 32; i++) sum += tr[lane][i];                      \
+        __syncwarp();                                                                           \
+        {                                                                                       \
+            const int kk = lane / (4 * RG), rr = (lane / 4) % RG, q = lane & 3;                 \
+            s_red[warp][kb * K + kk][rr][q] = sum;                                              \
+        }                                                                                       \
+    }
+
+        if (all_live) {
+            AKRA_ADJ_KBLOCK(false)
+        } else {
+            AKRA_ADJ_KBLOCK(true)
         }
+#undef AKRA_ADJ_KBLOCK
         __syncthreads();
         // sum the warps and write this chunk's partial sums for the tile
         for (int i = tid; i < nl * RG * 4; i += NT) {
             const int step = i / (RG * 4), rem = i - step * RG * 4, rr = rem >> 2, q = rem & 3;
             const int r = r0 + rr;
             if (r >= R) continue;
-            T s = 0;
+            T sv = 0;
 #pragma unroll
-            for (int w = 0; w < NW; w++) s += s_red[w][step][rr][q];
-            partial[(((size_t)chunk * R + r) * ntri + mbase + lt + step) * 4 + q] = s;
+            for (int w = 0; w < NW; w++) sv += s_red[w][step][rr][q];
+            partial[(((size_t)chunk * R + r) * ntri + mbase + lt + step) * 4 + q] = sv;
         }
     }
 }
@@ -458,6 +453,9 @@ __global__ void k_adj_epilogue(int L, long long ntri, int nchunks, int R,
 template <typename T> const v4_t<T> *coef_ptr(akra_plan p);
 template <> const float4 *coef_ptr<float>(akra_plan p) { return p->d_coef32; }
 template <> const double4_32a *coef_ptr<double>(akra_plan p) { return p->d_coef64; }
+template <typename T> const v4_t<T> *seed_ptr(akra_plan p);
+template <> const float4 *seed_ptr<float>(akra_plan p) { return p->d_seed32; }
+template <> const double4_32a *seed_ptr<double>(akra_plan p) { return p->d_seed64; }
 template <typename T> const T *D_ptr(akra_plan p);
 template <> const float *D_ptr<float>(akra_plan p) { return p->d_D32; }
 template <> const double *D_ptr<double>(akra_plan p) { return p->d_D64; }
@@ -470,7 +468,7 @@ static void launch_synth(akra_plan p, LegMode mode, const void *alm, void *phi, 
     dim3 grid((unsigned)(p->lmax + 1) * nchunks, (R + RG - 1) / RG);
     k_leg_synth<T, P, RG, NT><<<grid, NT, 0, st>>>(
         p->lmax, p->nring, p->ntri, nchunks, nunits, units, p->d_units, coef_ptr<T>(p),
-        p->d_seedC, mode == LegMode::KS ? D_ptr<T>(p) : nullptr, (const cx_t<T> *)alm, R,
+        seed_ptr<T>(p), p->nunit, mode == LegMode::KS ? D_ptr<T>(p) : nullptr, (const cx_t<T> *)alm, R,
         (cx_t<T> *)phi, units == p->d_all_units ? nullptr : p->d_ring_active, p->cur_skip);
 }
 
@@ -482,7 +480,7 @@ static int launch_adjoint(akra_plan p, const void *phi, void *partial, int R, co
     dim3 grid((unsigned)(p->lmax + 1) * nchunks, (R + RG - 1) / RG);
     k_leg_adjoint<T, P, RG, NT><<<grid, NT, 0, st>>>(
         p->lmax, p->nring, p->ntri, nchunks, nunits, units, p->d_units, coef_ptr<T>(p),
-        p->d_seedC, (const cx_t<T> *)phi, R, (T *)partial,
+        seed_ptr<T>(p), p->nunit, (const cx_t<T> *)phi, R, (T *)partial,
         units == p->d_all_units ? nullptr : p->d_ring_active, p->cur_skip);
     return nchunks;
 }

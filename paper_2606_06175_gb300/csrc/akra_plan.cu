@@ -119,6 +119,41 @@ __global__ void k_seed(int L, double *seedC, double *D64, float *D32)
     D32[m] = (float)D;
 }
 
+// Seeds of the two spin recurrences at l0 = max(m, 2) for every (m, ring pair), in FP64:
+//   log2|2λ| = C_m + a log2 sin(θ/2) + b log2 cos(θ/2), (a, b) = (m+2, |m-2|), sign (-1)^m,
+//   log2|(-2)λ| with (a, b) swapped, sign (-1)^m for m >= 2 and +1 below,
+// scaled by 2^(-Q e) with one exponent index e <= 0 per pair (Q = 64 for the FP32 table,
+// 600 for FP64) so that the larger one lies in [2^(-Q/2), 2^(Q/2)).
+__device__ void seed_values(int m, double Cm, double ls, double lc, int Q, double &vp, double &vm,
+                            int &e)
+{
+    const int a = m + 2, b = m >= 2 ? m - 2 : 2 - m;
+    const double Lp = Cm + a * ls + b * lc;
+    const double Lm = Cm + b * ls + a * lc;
+    const double sp = (m & 1) ? -1.0 : 1.0;
+    const double sm = (m >= 2) ? sp : 1.0;
+    int ee = (int)floor((fmax(Lp, Lm) + 0.5 * Q) / Q);
+    if (ee > 0) ee = 0;
+    vp = sp * exp2(Lp - (double)Q * ee);
+    vm = sm * exp2(Lm - (double)Q * ee);
+    e = ee;
+}
+
+__global__ void k_seeds(int L, int nunit, const double *seedC, const UnitInfo *units, float4 *s32,
+                        double4_32a *s64)
+{
+    const int m = blockIdx.x;
+    for (int u = threadIdx.x; u < nunit; u += blockDim.x) {
+        const UnitInfo ui = units[u];
+        double vp, vm;
+        int e;
+        seed_values(m, seedC[m], ui.ls, ui.lc, Scale<float>::Q, vp, vm, e);
+        s32[(size_t)m * nunit + u] = make_float4((float)vp, (float)vm, __int_as_float(e), 0.f);
+        seed_values(m, seedC[m], ui.ls, ui.lc, Scale<double>::Q, vp, vm, e);
+        s64[(size_t)m * nunit + u] = make_double4_32a(vp, vm, (double)e, 0.0);
+    }
+}
+
 // e^{iπ t/n} for every ring length n = 4i (i = 1..N), t in [0, 2n), at offset 4i(i-1)
 __global__ void k_twiddles(int N, double2 *tw64, float2 *tw32)
 {
@@ -324,6 +359,8 @@ static akra_status plan_build(akra_plan p)
     AKRA_TRY(dev_alloc(p, &p->d_coef32, sizeof(float4) * p->ntri));
     AKRA_TRY(dev_alloc(p, &p->d_seedC, sizeof(double) * (L + 1)));
     AKRA_TRY(dev_alloc(p, &p->d_D64, sizeof(double) * (L + 1)));
+    AKRA_TRY(dev_alloc(p, &p->d_seed32, sizeof(float4) * (size_t)(L + 1) * p->nunit));
+    AKRA_TRY(dev_alloc(p, &p->d_seed64, sizeof(double4_32a) * (size_t)(L + 1) * p->nunit));
     AKRA_TRY(dev_alloc(p, &p->d_D32, sizeof(float) * (L + 1)));
     const size_t ntw = 4ull * N * (N + 1);
     AKRA_TRY(dev_alloc(p, &p->d_tw64, sizeof(double2) * ntw));
@@ -347,6 +384,8 @@ static akra_status plan_build(akra_plan p)
     AKRA_CUDA_TRY(cudaGetLastError());
     k_seed<<<(L + 1 + 127) / 128, 128>>>(L, p->d_seedC, p->d_D64, p->d_D32);
     AKRA_CUDA_TRY(cudaGetLastError());
+    k_seeds<<<L + 1, 256>>>(L, p->nunit, p->d_seedC, p->d_units, p->d_seed32, p->d_seed64);
+    AKRA_CUDA_TRY(cudaGetLastError());
     k_twiddles<<<dim3(4, N), 256>>>(N, p->d_tw64, p->d_tw32);
     AKRA_CUDA_TRY(cudaGetLastError());
     k_iota<<<(p->nring + 255) / 256, 256>>>(p->nring, p->d_all_rings);
@@ -354,6 +393,7 @@ static akra_status plan_build(akra_plan p)
     AKRA_CUDA_TRY(cudaGetLastError());
     AKRA_CUDA_TRY(cudaMemset(p->d_ring_active, 1, p->nring));
     AKRA_TRY(ring_fft_prepare(p));
+    AKRA_TRY(ring_fft32_build(p));
     AKRA_CUDA_TRY(cudaStreamCreateWithFlags(&p->stream, cudaStreamNonBlocking));
     AKRA_CUDA_TRY(cudaEventCreateWithFlags(&p->ev_a, cudaEventDisableTiming));
     AKRA_CUDA_TRY(cudaEventCreateWithFlags(&p->ev_b, cudaEventDisableTiming));
@@ -408,7 +448,8 @@ extern "C" void akra_plan_destroy(akra_plan p)
     void *ptrs[] = {p->d_rings, p->d_units, p->d_factors, p->d_coef64, p->d_coef32, p->d_seedC,
                     p->d_D64, p->d_D32, p->d_tw64, p->d_tw32, p->d_all_rings, p->d_all_units,
                     p->d_active_rings, p->d_active_units, p->d_ring_active, p->d_W64, p->d_W32,
-                    p->phi.ptr, p->partial.ptr, p->cg.ptr, p->red.ptr};
+                    p->phi.ptr, p->partial.ptr, p->cg.ptr, p->red.ptr, p->d_fft32_M,
+                    p->d_fft32_off, p->d_fft32_tw2, p->d_fft32_bhat, p->d_seed32, p->d_seed64};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     if (p->stream) cudaStreamDestroy(p->stream);

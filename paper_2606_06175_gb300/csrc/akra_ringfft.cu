@@ -2,6 +2,7 @@
 // (the φ half of SHT^-1 / SHT in Sec. II B), fused with the pixel-space diagonal
 // W = ω M N^-1 (Sec. II B, "Pixel space (diagonal)").
 //
+// (This Stockham form serves the FP64 path; FP32 uses akra_ringfft32.cu.)
 // Ring with n pixels at φ_j = π(2j+σ)/n.  Synthesis direction:
 //   f_j = Σ_{m=-L}^{L} Φ(m) e^{imφ_j} = Σ_k e^{2πijk/n} F[k],
 //   F[k] = e^{iπσk/n} Σ_{q: |k+nq|<=L} (-1)^{σq} Φ(k+nq)          (fold)
@@ -278,6 +279,8 @@ akra_status ring_fft(akra_plan p, FftMode mode, void *phi, const void *map_in, v
                      bool weighted, int R, const int *rings, int nrings, cudaStream_t st)
 {
     if (nrings <= 0) return AKRA_OK;
+    if constexpr (sizeof(T) == sizeof(float))   // FP32: O(n log n) for every ring length
+        return ring_fft32(p, mode, phi, map_in, map_out, weighted, R, rings, nrings, st);
     switch (mode) {
     case FftMode::Synth:
         return launch_fft<T, 0>(p, phi, map_in, map_out, weighted, R, rings, nrings, st);
