@@ -174,6 +174,56 @@ akra_status akra_cg_solve(akra_plan plan, akra_prec prec, const void *d_shear, v
 akra_status akra_cg_solve_b(akra_plan plan, akra_prec prec, const void *d_b, void *d_x,
                             int R, double tol, int maxiter, akra_cg_info *info, void *stream);
 
+/* Implicit adjoint solve for gradients through akra_cg_solve: given d_g [R][2][ntri], the
+ * gradient of a loss w.r.t. the stored (re, im) components of the solution x̂, solve
+ * H u = G^{-1} g (G: the real-dof metric, 1 at m = 0 real parts, 2 at m > 0; the ignored
+ * imaginary parts at m = 0 get 0) into d_u.  Then dL/dy = W A u (akra_apply_A with
+ * weighted = 1) and dL/dN^-1 follows from akra_weight_grad.  Same precisions, tolerances,
+ * blocking behaviour and errors as akra_cg_solve_b (the differentiation form of the north
+ * star; Eq. 14's estimator differentiated with λ_eff held fixed). */
+akra_status akra_cg_solve_adjoint(akra_plan plan, akra_prec prec, const void *d_g, void *d_u,
+                                  int R, double tol, int maxiter, akra_cg_info *info,
+                                  void *stream);
+
+/* d_grad[p] = ω M_p Σ_r Σ_c Au[r][c][p] (y[r][c][p] - Ax[r][c][p])  for p < npix:
+ * the gradient of the loss w.r.t. N^-1_p when Au = A u (u from akra_cg_solve_adjoint) and
+ * Ax = A x̂ (both unweighted maps [R][2][npix]), y the shear.  Maps and d_grad in the
+ * precision's real type (F64: double, F32: float).  Errors: EINVAL, ENOWEIGHTS, ECUDA. */
+akra_status akra_weight_grad(akra_plan plan, akra_prec prec, const void *d_Au, const void *d_y,
+                             const void *d_Ax, void *d_grad, int R, void *stream);
+
+/* ---- several instances (uneven nside / lmax, several RHS each) solved together ----------
+ * Motivated by the paper's noise realisations and tomographic bins (Sec. III); the batched
+ * form is not in the paper.  Each FP32 H application of the inner CG runs as one persistent
+ * Legendre-synthesis launch over the work items of all instances (a queue of
+ * (instance, m, ring-pair chunk, RHS group) items, heaviest first), one ring-FFT launch over
+ * all instances' rings and one persistent Legendre-adjoint launch. */
+typedef struct akra_batch_s *akra_batch;
+
+/* Group ninst plans (each with weights set; no plan twice) with R[i] RHS each (1..64).
+ * The plans must outlive the batch.  Blocking.  Errors: EINVAL, ENOWEIGHTS, ENOMEM. */
+akra_status akra_batch_create(int ninst, const akra_plan *plans, const int *R, akra_batch *out);
+void akra_batch_destroy(akra_batch batch);
+
+/* Choose the batch's Legendre tile shape by timing the batched FP32 H (blocking). */
+akra_status akra_batch_autotune(akra_batch batch, void *stream);
+
+/* d_y[i] = H_i d_x[i] in FP32 for every instance (complex float [R_i][2][ntri_i]) in one
+ * batched pass.  Asynchronous on stream after a blocking upload of the launch arguments. */
+akra_status akra_batch_apply_H(akra_batch batch, const void *const *d_x, void *const *d_y,
+                               void *stream);
+
+/* Solve every instance: d_shear[i] [R_i][2][npix_i] -> d_x[i] [R_i][2][ntri_i].
+ * AKRA_MIXED: FP64 in/out, FP64 b and outer residuals per instance, batched FP32 inner CG;
+ * AKRA_F32: FP32 in/out.  info: host array [ninst] (may be NULL).  Blocking; returns the worst
+ * status over all instances and RHS. */
+akra_status akra_batch_cg_solve(akra_batch batch, akra_prec prec, const void *const *d_shear,
+                                void *const *d_x, double tol, int maxiter, akra_cg_info *info,
+                                void *stream);
+
+/* Current tile shape (ring pairs per thread, RHS per block) and batched launches so far. */
+akra_status akra_batch_describe(akra_batch batch, int *P, int *RG, long long *launches);
+
 /* Host-side wall-clock budget (seconds, > 0) for blocking solves; default 3600. */
 akra_status akra_set_timeout(double seconds);
 

@@ -491,3 +491,48 @@ def band_power_loss(lmax: int, kE, edges) -> float:
         if sel.any():
             tot += cl[sel].mean()
     return float(tot)
+
+
+def band_power_grad(lmax: int, kE, edges):
+    """Gradient of band_power_loss w.r.t. the stored components of κ_E, packed as
+    dL/dRe + i dL/dIm (m = 0 imaginary parts do not enter the loss)."""
+    ls, ms = lm_arrays(lmax)
+    kE = np.asarray(kE)
+    ell = np.arange(lmax + 1)
+    coef = np.zeros(lmax + 1)
+    for b in range(len(edges) - 1):
+        sel = (ell > edges[b]) & (ell <= edges[b + 1])
+        if sel.any():
+            coef[sel] += 1.0 / sel.sum()
+    c = coef[ls] / (2 * ls + 1)
+    w = np.where(ms == 0, 2.0, 4.0)        # d(x^2)/dx = 2x, doubled for m > 0
+    g = c * w * kE.real + 1j * np.where(ms == 0, 0.0, c * 4.0 * kE.imag)
+    return g
+
+
+def solve_grad(nside: int, lmax: int, ninv, y, lam: float, gfun, tol: float = 1e-13,
+               maxiter: int = 5000):
+    """x̂ = H^{-1} A^T W y and the gradient of L(x̂) w.r.t. y and N^-1 (λ_eff held fixed).
+
+    gfun(x̂) returns dL/dx̂ on the stored components (dL/dRe + i dL/dIm, for (κ_E, κ_B)).
+    With G the real-dof metric (H is self-adjoint in it): u = H^{-1} G^{-1} g,
+    dL/dy = W A u, dL/dN^-1_p = ω M_p <(A u)_p, y_p - (A x̂)_p>.
+    """
+    wts = Weights(nside, ninv, lam)
+    y = np.asarray(y, np.float64)
+    (xE, xB), _, _, _ = cg_solve(nside, lmax, wts, y[0], y[1], tol=tol, maxiter=maxiter)
+    gE, gB = gfun((xE, xB))
+    _, ms = lm_arrays(lmax)
+
+    def ginv(v):
+        v = np.asarray(v, np.complex128)
+        return np.where(ms == 0, v.real + 0j, 0.5 * v)
+
+    (uE, uB), _, _, _ = pcg(lambda e, b: apply_H(nside, lmax, wts, e, b), (ginv(gE), ginv(gB)),
+                            wts.precond, lmax, tol, maxiter)
+    Au = np.stack(forward_A(nside, lmax, uE, uB))
+    Ax = np.stack(forward_A(nside, lmax, xE, xB))
+    dy = wts.W * Au
+    mask = np.asarray(ninv) > 0
+    dninv = np.where(mask, wts.omega * np.sum(Au * (y - Ax), axis=0), 0.0)
+    return (xE, xB), dy, dninv

@@ -49,7 +49,9 @@ EXPORTS = ["akra_plan_create", "akra_plan_destroy", "akra_last_error", "akra_ver
            "akra_plan_describe", "akra_plan_set_weights", "akra_synth_spin2",
            "akra_adjoint_synth_spin2", "akra_apply_A", "akra_apply_At", "akra_apply_H",
            "akra_cg_solve", "akra_cg_solve_b", "akra_set_timeout", "akra_autotune",
-           "akra_time_H_stages", "akra_synth_spin2_static"]
+           "akra_time_H_stages", "akra_synth_spin2_static", "akra_cg_solve_adjoint",
+           "akra_weight_grad", "akra_batch_create", "akra_batch_destroy", "akra_batch_autotune",
+           "akra_batch_apply_H", "akra_batch_cg_solve", "akra_batch_describe"]
 
 _lib_handle = None
 
@@ -88,6 +90,15 @@ def load(build_if_missing: bool = False):
         "akra_autotune": ([vp, i, i, vp], i),
         "akra_time_H_stages": ([vp, i, i, i, vp, ctypes.POINTER(ctypes.c_double)], i),
         "akra_synth_spin2_static": ([vp, i, vp, vp, i, vp], i),
+        "akra_cg_solve_adjoint": ([vp, i, vp, vp, i, d, i, ctypes.POINTER(CgInfo), vp], i),
+        "akra_weight_grad": ([vp, i, vp, vp, vp, vp, i, vp], i),
+        "akra_batch_create": ([i, ctypes.POINTER(vp), ctypes.POINTER(i), ctypes.POINTER(vp)], i),
+        "akra_batch_destroy": ([vp], None),
+        "akra_batch_autotune": ([vp, vp], i),
+        "akra_batch_apply_H": ([vp, ctypes.POINTER(vp), ctypes.POINTER(vp), vp], i),
+        "akra_batch_cg_solve": ([vp, i, ctypes.POINTER(vp), ctypes.POINTER(vp), d, i,
+                                 ctypes.POINTER(CgInfo), vp], i),
+        "akra_batch_describe": ([vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(ctypes.c_longlong)], i),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -269,6 +280,28 @@ def akra_cg_solve_b(plan: Plan, prec: int, b: torch.Tensor, out=None, tol: float
     return _solve(load().akra_cg_solve_b, plan, prec, b, out, R, tol, maxiter, stream, raise_on_noconv)
 
 
+def akra_cg_solve_adjoint(plan: Plan, prec: int, g: torch.Tensor, out=None, tol: float = 1e-6,
+                          maxiter: int = 1000, stream=None, raise_on_noconv: bool = False):
+    R = g.shape[0]
+    _need(g, (R, 2, plan.ntri), _cdtype(F64 if prec == MIXED else prec), "g")
+    return _solve(load().akra_cg_solve_adjoint, plan, prec, g, out, R, tol, maxiter, stream,
+                  raise_on_noconv)
+
+
+def akra_weight_grad(plan: Plan, prec: int, Au: torch.Tensor, y: torch.Tensor, Ax: torch.Tensor,
+                     out: torch.Tensor = None, stream=None):
+    R = Au.shape[0]
+    dt = _rdtype(prec)
+    for t, nm in ((Au, "Au"), (y, "y"), (Ax, "Ax")):
+        _need(t, (R, 2, plan.npix), dt, nm)
+    if out is None:
+        out = torch.empty((plan.npix,), dtype=dt, device=Au.device)
+    _need(out, (plan.npix,), dt, "out")
+    _check(load().akra_weight_grad(plan.handle, prec, _ptr(Au), _ptr(y), _ptr(Ax), _ptr(out), R,
+                                   _stream(stream)))
+    return out
+
+
 def akra_set_timeout(seconds: float):
     _check(load().akra_set_timeout(float(seconds)))
 
@@ -283,3 +316,87 @@ def akra_time_H_stages(plan: Plan, prec: int, R: int = 1, reps: int = 3, stream=
     _check(load().akra_time_H_stages(plan.handle, prec, R, reps, _stream(stream), ms))
     return {"legendre_synth": ms[0], "ring_fft": ms[1], "legendre_adjoint": ms[2],
             "epilogue": ms[3], "total": ms[4]}
+
+
+class Batch:
+    """Owning handle of an akra_batch over several plans (kept alive with it)."""
+
+    def __init__(self, handle, plans, R):
+        self.handle, self.plans, self.R = handle, list(plans), list(R)
+
+    def close(self):
+        if self.handle:
+            load().akra_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def akra_batch_create(plans, R) -> Batch:
+    n = len(plans)
+    arr = (ctypes.c_void_p * n)(*[p.handle for p in plans])
+    rr = (ctypes.c_int * n)(*R)
+    h = ctypes.c_void_p()
+    _check(load().akra_batch_create(n, arr, rr, ctypes.byref(h)))
+    return Batch(h, plans, R)
+
+
+def akra_batch_destroy(batch: Batch):
+    batch.close()
+
+
+def akra_batch_autotune(batch: Batch, stream=None):
+    _check(load().akra_batch_autotune(batch.handle, _stream(stream)))
+
+
+def akra_batch_describe(batch: Batch) -> dict:
+    P, RG, nl = ctypes.c_int(), ctypes.c_int(), ctypes.c_longlong()
+    _check(load().akra_batch_describe(batch.handle, ctypes.byref(P), ctypes.byref(RG), ctypes.byref(nl)))
+    return {"P": P.value, "RG": RG.value, "launches": nl.value}
+
+
+def akra_batch_apply_H(batch: Batch, xs, out=None, stream=None):
+    n = len(batch.plans)
+    if out is None:
+        out = [torch.empty_like(x) for x in xs]
+    for p, R, x, y in zip(batch.plans, batch.R, xs, out):
+        _need(x, (R, 2, p.ntri), torch.complex64, "x")
+        _need(y, (R, 2, p.ntri), torch.complex64, "out")
+    xa = (ctypes.c_void_p * n)(*[x.data_ptr() for x in xs])
+    ya = (ctypes.c_void_p * n)(*[y.data_ptr() for y in out])
+    _check(load().akra_batch_apply_H(batch.handle, xa, ya, _stream(stream)))
+    return out
+
+
+def akra_batch_cg_solve(batch: Batch, prec: int, shears, out=None, tol: float = 1e-6,
+                        maxiter: int = 2000, stream=None, raise_on_noconv: bool = False):
+    n = len(batch.plans)
+    rdt = torch.float32 if prec == F32 else torch.float64
+    cdt = torch.complex64 if prec == F32 else torch.complex128
+    if out is None:
+        out = [torch.empty((R, 2, p.ntri), dtype=cdt, device=s.device)
+               for p, R, s in zip(batch.plans, batch.R, shears)]
+    for p, R, y, x in zip(batch.plans, batch.R, shears, out):
+        _need(y, (R, 2, p.npix), rdt, "shear")
+        _need(x, (R, 2, p.ntri), cdt, "out")
+    infos = (CgInfo * n)()
+    keep = []
+    for k in range(n):
+        rel = (ctypes.c_double * batch.R[k])()
+        its = (ctypes.c_int * batch.R[k])()
+        keep.append((rel, its))
+        infos[k].relres_rhs = rel
+        infos[k].iters_rhs = its
+    ya = (ctypes.c_void_p * n)(*[y.data_ptr() for y in shears])
+    xa = (ctypes.c_void_p * n)(*[x.data_ptr() for x in out])
+    st = load().akra_batch_cg_solve(batch.handle, prec, ya, xa, float(tol), int(maxiter), infos, _stream(stream))
+    if st != 0 and (raise_on_noconv or st not in (4, 5)):
+        _check(st)
+    res = [{"iters": infos[k].iters, "outer": infos[k].outer, "h_applies_f64": infos[k].h_applies_f64,
+            "h_applies_f32": infos[k].h_applies_f32, "relres": infos[k].relres, "status": infos[k].status,
+            "relres_rhs": list(keep[k][0]), "iters_rhs": list(keep[k][1])} for k in range(n)]
+    return out, res

@@ -14,30 +14,9 @@
 #include <chrono>
 #include <thread>
 
-#include "akra_internal.cuh"
+#include "akra_cg_impl.cuh"
 
 namespace akra {
-
-struct CgState {          // one per RHS (device)
-    double rz, pq, alpha, beta, rr, bnorm2, relres, tol;
-    int done, iters, status, pad;
-};
-
-struct CgCtl {            // one per solver precision (device)
-    int all_done;         // read by every iteration kernel
-    int counter;          // last-block ticket
-    int maxiter;
-    int R;
-    double precond;
-};
-
-constexpr int RED_NB = 296;    // reduction blocks (2 per SM on 148+ SMs)
-constexpr int RED_NT = 256;
-
-struct CgGraph {
-    cudaGraphExec_t exec = nullptr;
-    unsigned gen = 0;
-};
 
 // ---------------------------------------------------------------------------
 // vector kernels
@@ -308,23 +287,7 @@ __global__ void k_axpy_mixed(long long n, int R, const float2 *d32, const double
     }
 }
 
-// ---------------------------------------------------------------------------
-// workspace layout (plan->cg): FP64 region of 5 vectors, FP32 region of 5 vectors
-//   F64 CG:  b x r p q in the FP64 region
-//   F32 CG and the MIXED inner CG: b x r p q in the FP32 region
-//   MIXED outer: b64 x64 r64 t64 in the FP64 region (slots 0..3)
-// plan->red: [CgState R] x 2 precisions, CgCtl x 2, scratch doubles, residual doubles
-// ---------------------------------------------------------------------------
-struct CgBufs {
-    void *v64[5];
-    void *v32[5];
-    CgState *st[2];
-    CgCtl *ctl[2];
-    double *scratch;
-    double *res;
-};
-
-static akra_status cg_reserve(akra_plan p, int R, CgBufs &b)
+akra_status cg_reserve(akra_plan p, int R, CgBufs &b)
 {
     if (R > kMaxRhsLocal) {
         set_error("CG: at most %d right-hand sides per solve", kMaxRhsLocal);
@@ -358,12 +321,6 @@ static akra_status cg_reserve(akra_plan p, int R, CgBufs &b)
     return AKRA_OK;
 }
 
-template <typename T> struct PrecIdx;
-template <> struct PrecIdx<double> { static constexpr int v = 0; };
-template <> struct PrecIdx<float> { static constexpr int v = 1; };
-
-template <typename T>
-static void **vecs(CgBufs &b) { return PrecIdx<T>::v == 0 ? b.v64 : b.v32; }
 
 // capture (or reuse) the graph of one CG iteration for precision T and R RHS
 template <typename T>
@@ -421,10 +378,10 @@ static akra_status cg_graph(akra_plan p, int R, CgBufs &b, cudaGraphExec_t *out)
     return AKRA_OK;
 }
 
-static double g_timeout_s = 3600.0;
+double g_timeout_s = 3600.0;
 
 // wait for the event with a wall-clock budget (no unbounded device wait)
-static akra_status bounded_wait(cudaEvent_t ev, std::chrono::steady_clock::time_point deadline)
+akra_status bounded_wait(cudaEvent_t ev, std::chrono::steady_clock::time_point deadline)
 {
     for (;;) {
         const cudaError_t e = cudaEventQuery(ev);
@@ -639,6 +596,76 @@ static akra_status solve_b(akra_plan p, akra_prec prec, const void *bsrc, void *
     return (akra_status)worst;
 }
 
+template <typename T>
+akra_status cg_launch_init(akra_plan p, int R, CgBufs &b, double tol, int maxiter, cudaStream_t cs)
+{
+    void **v = vecs<T>(b);
+    CgState *st = b.st[PrecIdx<T>::v];
+    CgCtl *ctl = b.ctl[PrecIdx<T>::v];
+    CgCtl hctl{};
+    hctl.R = R;
+    hctl.precond = p->precond;
+    hctl.maxiter = maxiter;
+    // pageable-to-device copies are staged and ordered on the stream
+    AKRA_CUDA_TRY(cudaMemcpyAsync(ctl, &hctl, sizeof(CgCtl), cudaMemcpyHostToDevice, cs));
+    k_cg_init<T><<<RED_NB, RED_NT, 0, cs>>>(p->lmax, p->ntri, (const cx_t<T> *)v[0], (cx_t<T> *)v[1],
+                                            (cx_t<T> *)v[2], (cx_t<T> *)v[3], st, ctl, b.scratch, tol,
+                                            maxiter);
+    AKRA_CUDA_TRY(cudaGetLastError());
+    p->launches++;
+    return AKRA_OK;
+}
+
+template <typename T>
+akra_status cg_launch_tail(akra_plan p, CgBufs &b, cudaStream_t cs)
+{
+    void **v = vecs<T>(b);
+    CgState *st = b.st[PrecIdx<T>::v];
+    CgCtl *ctl = b.ctl[PrecIdx<T>::v];
+    k_cg_dot_pq<T><<<RED_NB, RED_NT, 0, cs>>>(p->lmax, p->ntri, (const cx_t<T> *)v[3],
+                                              (const cx_t<T> *)v[4], st, ctl, b.scratch);
+    k_cg_update_xr<T><<<RED_NB, RED_NT, 0, cs>>>(p->lmax, p->ntri, (const cx_t<T> *)v[3],
+                                                 (const cx_t<T> *)v[4], (cx_t<T> *)v[1],
+                                                 (cx_t<T> *)v[2], st, ctl, b.scratch);
+    k_cg_update_p<T><<<RED_NB, RED_NT, 0, cs>>>(p->ntri, (const cx_t<T> *)v[2], (cx_t<T> *)v[3], st, ctl);
+    AKRA_CUDA_TRY(cudaGetLastError());
+    return AKRA_OK;
+}
+
+akra_status launch_residual64(akra_plan p, int R, CgBufs &b, const void *bv, const void *hv, void *out,
+                              cudaStream_t cs)
+{
+    k_residual<double><<<RED_NB, RED_NT, 0, cs>>>(p->lmax, p->ntri, R, (const double2 *)bv,
+                                                 (const double2 *)hv, (double2 *)out, b.res, b.ctl[0],
+                                                 b.scratch);
+    AKRA_CUDA_TRY(cudaGetLastError());
+    p->launches++;
+    return AKRA_OK;
+}
+
+akra_status launch_cast_scaled(akra_plan p, int R, CgBufs &b, cudaStream_t cs)
+{
+    k_cast_scaled<<<RED_NB, RED_NT, 0, cs>>>(2 * p->ntri, R, (const double2 *)b.v64[2], b.res,
+                                             (float2 *)b.v32[0]);
+    AKRA_CUDA_TRY(cudaGetLastError());
+    p->launches++;
+    return AKRA_OK;
+}
+
+akra_status launch_axpy_mixed(akra_plan p, int R, CgBufs &b, cudaStream_t cs)
+{
+    k_axpy_mixed<<<RED_NB, RED_NT, 0, cs>>>(2 * p->ntri, R, (const float2 *)b.v32[1], b.res,
+                                            (double2 *)b.v64[1]);
+    AKRA_CUDA_TRY(cudaGetLastError());
+    p->launches++;
+    return AKRA_OK;
+}
+
+template akra_status cg_launch_init<float>(akra_plan, int, CgBufs &, double, int, cudaStream_t);
+template akra_status cg_launch_init<double>(akra_plan, int, CgBufs &, double, int, cudaStream_t);
+template akra_status cg_launch_tail<float>(akra_plan, CgBufs &, cudaStream_t);
+template akra_status cg_launch_tail<double>(akra_plan, CgBufs &, cudaStream_t);
+
 void cg_release_graphs(akra_plan p)
 {
     for (auto &kv : p->graphs) {
@@ -738,4 +765,18 @@ extern "C" akra_status akra_cg_solve(akra_plan p, akra_prec prec, const void *d_
     // the adjoint may have grown a workspace; refresh the buffer pointers
     AKRA_TRY(cg_reserve(p, R, b));
     return solve_b(p, prec, nullptr, d_x, R, tol, maxiter, info, user, true, b, h64);
+}
+
+extern "C" akra_status akra_cg_solve_adjoint(akra_plan p, akra_prec prec, const void *d_g, void *d_u, int R,
+                                             double tol, int maxiter, akra_cg_info *info, void *stream)
+{
+    AKRA_TRY(check_cg(p, prec, d_g, d_u, R, tol, maxiter, "akra_cg_solve_adjoint"));
+    cudaStream_t user = (cudaStream_t)stream;
+    CgBufs b;
+    AKRA_TRY(cg_reserve(p, R, b));
+    AKRA_TRY(join_user(p, user, b));
+    // right-hand side G^{-1} g in the solve's own precision region
+    const bool dbl = prec != AKRA_F32;
+    AKRA_TRY(metric_inverse(p, dbl, d_g, dbl ? b.v64[0] : b.v32[0], R, p->stream));
+    return solve_b(p, prec, nullptr, d_u, R, tol, maxiter, info, user, true, b, 0);
 }

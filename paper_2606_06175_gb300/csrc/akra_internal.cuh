@@ -96,6 +96,43 @@ struct LegShape {
     int RG;                // RHS handled together by one block
 };
 
+// arguments of one Legendre kernel instance (one plan; the batched launches hold an array)
+template <typename T>
+struct LegArgs {
+    int L, nring, nchunks, nunits, nunit_all, R;
+    long long ntri;
+    const int *units;                 // ring pairs to process
+    const UnitInfo *uinfo;
+    const v4_t<T> *coef;              // recurrence coefficients
+    const v4_t<T> *seeds;             // seeds per (m, ring pair)
+    const T *fl;                      // synthesis: per-l factor (nullptr = -1)
+    const cx_t<T> *alm;               // synthesis input  [R][2][ntri]
+    cx_t<T> *phi;                     // synthesis output [R][nring][2L+1]
+    const cx_t<T> *phi_in;            // adjoint input    [R][nring][2L+1]
+    T *partial;                       // adjoint output   [nchunks][R][ntri][4]
+    const unsigned char *ring_active; // nullptr = all rings
+    const int *skip;                  // device flag: return at once if set
+};
+
+// arguments of one FP32 ring-FFT instance
+struct Fft32Args {
+    int L, nring, mmax;
+    long long npix;
+    const int *rings;                 // ring list (nullptr = all rings by block index)
+    const RingInfo *rinfo;
+    const int *fftM;
+    const long long *bhat_off;
+    const float2 *bhat_all;
+    const float2 *tw2;
+    const float2 *tw_all;
+    const float *W;
+    int weighted;
+    float2 *phi;
+    const float *map_in;
+    float *map_out;
+    const int *skip;
+};
+
 struct Workspace {
     void *ptr = nullptr;
     size_t bytes = 0;
@@ -167,6 +204,11 @@ enum class LegMode { Synth, KS };   // per-l factor f_l = -1 (pure spin-2 SHT) o
 LegShape leg_shape(akra_plan p, akra_prec prec, int R);
 int legendre_chunks(int nunits, const LegShape &s);
 void cg_release_graphs(akra_plan p);   // akra_cg.cu
+akra_status metric_inverse(akra_plan p, bool dbl, const void *in, void *out, int R, cudaStream_t st);
+
+// the LegArgs of plan p for precision T (pointers for data are filled by the caller)
+template <typename T>
+LegArgs<T> leg_args(akra_plan p, const LegShape &s, LegMode mode, const int *units, int nunits, int R);
 
 // alm [R][2][ntri] -> Φ [R][nring][2L+1] on the listed units
 template <typename T>
@@ -188,6 +230,7 @@ akra_status ring_fft(akra_plan p, FftMode mode, void *phi, const void *map_in, v
                      bool weighted, int R, const int *rings, int nrings, cudaStream_t st);
 // FP32 ring FFT with Bluestein for non-power-of-two rings (akra_ringfft32.cu)
 akra_status ring_fft32_build(akra_plan p);
+Fft32Args fft32_args(akra_plan p, bool weighted, const int *rings);
 akra_status ring_fft32(akra_plan p, FftMode mode, void *phi, const void *map_in, void *map_out,
                        bool weighted, int R, const int *rings, int nrings, cudaStream_t st);
 

@@ -11,398 +11,9 @@
 // rings through even/odd (l+m) accumulators.  Seeds at l0 = max(m,2) are formed in FP64 in
 // log2 form; the recurrence carries a per-unit exponent index e (value = v 2^(Q e)) and
 // contributes only once e == 0.
-#include "akra_internal.cuh"
+#include "akra_legendre_impl.cuh"
 
 namespace akra {
-
-constexpr int TL = 64;  // l-steps staged in shared memory per tile (even)
-
-// seeds 2λ_{l0 m} (vp) and (-2)λ_{l0 m} (vm) with their shared exponent index e, from the
-// plan's table (computed in FP64 at plan creation)
-__device__ __forceinline__ void load_seed(const float4 *__restrict__ t, size_t i, float &vp,
-                                          float &vm, int &e)
-{
-    const float4 s = t[i];
-    vp = s.x;
-    vm = s.y;
-    e = __float_as_int(s.z);
-}
-__device__ __forceinline__ void load_seed(const double4_32a *__restrict__ t, size_t i, double &vp,
-                                          double &vm, int &e)
-{
-    const double4_32a s = t[i];
-    vp = s.x;
-    vm = s.y;
-    e = (int)s.z;
-}
-
-// ---------------------------------------------------------------------------
-// synthesis: Φ(ring, ±m) for every ring of the listed units
-// ---------------------------------------------------------------------------
-template <typename T, int P, int RG, int NT>
-__global__ void __launch_bounds__(NT)
-k_leg_synth(int L, int nring, long long ntri, int nchunks, int nunits,
-            const int *__restrict__ units, const UnitInfo *__restrict__ uinfo,
-            const v4_t<T> *__restrict__ coef, const v4_t<T> *__restrict__ seeds, int nunit_all,
-            const T *__restrict__ fl, const cx_t<T> *__restrict__ alm, int R,
-            cx_t<T> *__restrict__ phi, const unsigned char *__restrict__ ring_active,
-            const int *__restrict__ skip)
-{
-    using C2 = cx_t<T>;
-    using V4 = v4_t<T>;
-    __shared__ V4 s_coef[TL];
-    __shared__ V4 s_alm[TL][RG];
-    if (skip && *skip) return;
-
-    const int m = blockIdx.x / nchunks;
-    const int chunk = blockIdx.x - m * nchunks;
-    const int r0 = blockIdx.y * RG;
-    const int l0 = m > 2 ? m : 2;
-    const int tid = threadIdx.x;
-    const long long mbase = (long long)m * (2 * L + 1 - m) / 2;
-
-    T x[P], vp[P], vm[P], vpo[P], vmo[P];
-    int e[P], uid[P];
-    T acc[P][RG][16];
-#pragma unroll
-    for (int k = 0; k < P; k++) {
-        const int iu = (chunk * P + k) * NT + tid;
-        uid[k] = iu < nunits ? (units ? units[iu] : iu) : -1;
-        x[k] = 0;
-        vp[k] = vm[k] = 0;
-        e[k] = 0;
-        if (uid[k] >= 0) {
-            x[k] = (T)uinfo[uid[k]].x;
-            load_seed(seeds, (size_t)m * nunit_all + uid[k], vp[k], vm[k], e[k]);
-        }
-        vpo[k] = vmo[k] = 0;
-#pragma unroll
-        for (int r = 0; r < RG; r++)
-#pragma unroll
-            for (int j = 0; j < 16; j++) acc[k][r][j] = 0;
-    }
-
-    for (int lt = l0; lt <= L; lt += TL) {
-        __syncthreads();
-        for (int i = tid; i < TL; i += NT) {
-            const int l = lt + i;
-            s_coef[i] = (l <= L) ? coef[mbase + l] : V4{0, 0, 0, 0};
-        }
-        for (int i = tid; i < TL * RG; i += NT) {
-            const int li = i / RG, rr = i - li * RG;
-            const int l = lt + li, r = r0 + rr;
-            V4 v{0, 0, 0, 0};
-            if (l <= L && r < R) {
-                C2 E = alm[((size_t)r * 2 + 0) * ntri + mbase + l];
-                C2 B = alm[((size_t)r * 2 + 1) * ntri + mbase + l];
-                const T f = fl ? fl[l] : T(-1);
-                if (m == 0) E.y = B.y = 0;
-                // c = f (E + iB), d = f (E - iB)
-                v = V4{f * (E.x - B.y), f * (E.y + B.x), f * (E.x + B.y), f * (E.y - B.x)};
-            }
-            s_alm[li][rr] = v;
-        }
-        __syncthreads();
-        const int nl = min(TL, L - lt + 1);
-        bool live = true;
-#pragma unroll
-        for (int k = 0; k < P; k++) live &= (e[k] == 0);
-        const bool all_live = __all_sync(0xffffffffu, live);
-
-        // one l-step: contract at l (slot S = parity of l - l0), then recur to l+1.
-        // vp = 2λ, vm = (-2)λ; accumulators per slot: P1 = Σ c 2λ, P2 = Σ d (-2)λ,
-        // P3 = Σ c (-2)λ, P4 = Σ d 2λ (complex)
-#define AKRA_SYNTH_STEP(I, S, GATED)                                                        \
-    {                                                                                       \
-        const V4 c = s_coef[I];                                                             \
-        bool any = true;                                                                    \
-        if (GATED) {                                                                        \
-            bool a_ = false;                                                                \
-            _Pragma("unroll") for (int k = 0; k < P; k++) a_ |= (e[k] == 0);                \
-            any = __any_sync(0xffffffffu, a_);                                              \
-        }                                                                                   \
-        if (any) {                                                                          \
-            _Pragma("unroll") for (int k = 0; k < P; k++) {                                 \
-                const T lp = (GATED && e[k] != 0) ? T(0) : vp[k];                           \
-                const T lm = (GATED && e[k] != 0) ? T(0) : vm[k];                           \
-                _Pragma("unroll") for (int r = 0; r < RG; r++) {                            \
-                    const V4 a = s_alm[I][r];                                               \
-                    T *ac = &acc[k][r][(S) * 8];                                            \
-                    ac[0] = fma(a.x, lp, ac[0]);                                            \
-                    ac[1] = fma(a.y, lp, ac[1]);                                            \
-                    ac[2] = fma(a.z, lm, ac[2]);                                            \
-                    ac[3] = fma(a.w, lm, ac[3]);                                            \
-                    ac[4] = fma(a.x, lm, ac[4]);                                            \
-                    ac[5] = fma(a.y, lm, ac[5]);                                            \
-                    ac[6] = fma(a.z, lp, ac[6]);                                            \
-                    ac[7] = fma(a.w, lp, ac[7]);                                            \
-                }                                                                           \
-            }                                                                               \
-        }                                                                                   \
-        _Pragma("unroll") for (int k = 0; k < P; k++) {                                     \
-            const T t1 = fma(c.x, x[k], c.z);                                               \
-            const T t2 = fma(c.x, x[k], -c.z);                                              \
-            const T np = fma(t1, vp[k], -c.y * vpo[k]);                                     \
-            const T nm = fma(t2, vm[k], -c.y * vmo[k]);                                     \
-            vpo[k] = vp[k];                                                                 \
-            vmo[k] = vm[k];                                                                 \
-            vp[k] = np;                                                                     \
-            vm[k] = nm;                                                                     \
-            if (GATED && e[k] < 0 &&                                                        \
-                (fabs(vp[k]) > Scale<T>::hi() || fabs(vm[k]) > Scale<T>::hi())) {           \
-                vp[k] *= Scale<T>::inv();                                                   \
-                vm[k] *= Scale<T>::inv();                                                   \
-                vpo[k] *= Scale<T>::inv();                                                  \
-                vmo[k] *= Scale<T>::inv();                                                  \
-                e[k]++;                                                                     \
-            }                                                                               \
-        }                                                                                   \
-    }
-
-        if (all_live) {
-            for (int i = 0; i < nl; i += 2) {
-                AKRA_SYNTH_STEP(i, 0, false)
-                AKRA_SYNTH_STEP(i + 1, 1, false)
-            }
-        } else {
-            for (int i = 0; i < nl; i += 2) {
-                AKRA_SYNTH_STEP(i, 0, true)
-                AKRA_SYNTH_STEP(i + 1, 1, true)
-            }
-        }
-#undef AKRA_SYNTH_STEP
-    }
-
-    // combine parities into the north and south rings and write Φ(±m)
-    const bool swap = ((l0 + m) & 1) != 0;   // slot A holds odd (l+m) when l0+m is odd
-    const size_t row = 2 * (size_t)L + 1;
-#pragma unroll
-    for (int k = 0; k < P; k++) {
-        if (uid[k] < 0) continue;
-        const UnitInfo ui = uinfo[uid[k]];
-#pragma unroll
-        for (int rr = 0; rr < RG; rr++) {
-            const int r = r0 + rr;
-            if (r >= R) continue;
-            T se[8], so[8];
-#pragma unroll
-            for (int j = 0; j < 8; j++) {
-                se[j] = swap ? acc[k][rr][8 + j] : acc[k][rr][j];
-                so[j] = swap ? acc[k][rr][j] : acc[k][rr][8 + j];
-            }
-            // north: Φ(m) = P1,  conj Φ(-m) = P2        (even + odd)
-            // south: Φ(m) = P3,  conj Φ(-m) = P4        (even - odd)
-#pragma unroll
-            for (int side = 0; side < 2; side++) {
-                const int ring = side == 0 ? ui.ring_n : ui.ring_s;
-                if (ring < 0) continue;
-                if (ring_active && !ring_active[ring]) continue;
-                const int o = side == 0 ? 0 : 4;
-                const T sg = side == 0 ? T(1) : T(-1);
-                const T fr = se[o + 0] + sg * so[o + 0], fi = se[o + 1] + sg * so[o + 1];
-                const T gr = se[o + 2] + sg * so[o + 2], gi = se[o + 3] + sg * so[o + 3];
-                C2 *prow = phi + ((size_t)r * nring + ring) * row + L;
-                prow[m] = C2{fr, fi};
-                if (m > 0) prow[-m] = C2{gr, -gi};
-            }
-        }
-    }
-}
-
-// ---------------------------------------------------------------------------
-// adjoint: partial[chunk][r][idx(l,m)] = Σ_{units in chunk} (E-part, B-part) at each l
-//   E-part = Σ_rings [2λ P + (-2)λ Q],  B-part = Σ_rings [2λ P - (-2)λ Q]
-//   with P = G(m), Q = conj(G(-m)) of the ring's Φ' row.  With the mirror relation and
-//   U1 = P_N + Q_S, U2 = Q_N + P_S, U3 = P_N - Q_S, U4 = P_S - Q_N:
-//     (l+m) even: E += 2λ U1 + (-2)λ U2,  B += 2λ U3 + (-2)λ U4
-//     (l+m) odd : E += 2λ U3 - (-2)λ U4,  B += 2λ U1 - (-2)λ U2
-// ---------------------------------------------------------------------------
-// row stride (in elements) of the per-warp transpose buffer: conflict-free scalar stores of
-// one value per lane and 16-byte row loads (36 floats, 34 doubles)
-template <typename T> struct TrStride;
-template <> struct TrStride<float> { static constexpr int v = 36; };
-template <> struct TrStride<double> { static constexpr int v = 34; };
-
-template <typename T, int P, int RG, int NT>
-__global__ void __launch_bounds__(NT)
-k_leg_adjoint(int L, int nring, long long ntri, int nchunks, int nunits,
-              const int *__restrict__ units, const UnitInfo *__restrict__ uinfo,
-              const v4_t<T> *__restrict__ coef, const v4_t<T> *__restrict__ seeds, int nunit_all,
-              const cx_t<T> *__restrict__ phi, int R, T *__restrict__ partial,
-              const unsigned char *__restrict__ ring_active, const int *__restrict__ skip)
-{
-    if (skip && *skip) return;
-    using C2 = cx_t<T>;
-    using V4 = v4_t<T>;
-    constexpr int NW = NT / 32;
-    constexpr int K = 8 / RG;   // l-steps per reduction block: K * 4 * RG = 32 values per lane
-    constexpr int S = TrStride<T>::v;
-    static_assert(K >= 2 && K * 4 * RG == 32, "RG must be 1, 2 or 4");
-    // l-tile: 64 steps, shorter for FP64 with several RHS to stay within 48 KB of static smem
-    constexpr int TLA = sizeof(T) == 8 ? 64 / RG : TL;
-    __shared__ V4 s_coef[TLA];
-    __shared__ T s_red[NW][TLA][RG][4];
-    __shared__ __align__(16) T s_tr[NW][32][S];
-
-    const int m = blockIdx.x / nchunks;
-    const int chunk = blockIdx.x - m * nchunks;
-    const int r0 = blockIdx.y * RG;
-    const int l0 = m > 2 ? m : 2;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const long long mbase = (long long)m * (2 * L + 1 - m) / 2;
-    const size_t row = 2 * (size_t)L + 1;
-    const bool swap = ((l0 + m) & 1) != 0;
-
-    T x[P], vp[P], vm[P], vpo[P], vmo[P];
-    int e[P];
-    // per unit and RHS, the partners of 2λ and (-2)λ in slot A (l - l0 even):
-    //   E += 2λ X1 + (-2)λ X2,  B += 2λ X3 + (-2)λ X4;   slot B: E += 2λ X3 - (-2)λ X4,
-    //   B += 2λ X1 - (-2)λ X2   (X = U1..U4, or U3, -U4, U1, -U2 when l0+m is odd)
-    C2 X1[P][RG], X2[P][RG], X3[P][RG], X4[P][RG];
-#pragma unroll
-    for (int k = 0; k < P; k++) {
-        const int iu = (chunk * P + k) * NT + tid;
-        const int u = iu < nunits ? (units ? units[iu] : iu) : -1;
-        x[k] = 0;
-        vp[k] = vm[k] = vpo[k] = vmo[k] = 0;
-        e[k] = 0;
-        UnitInfo ui;
-        ui.ring_n = ui.ring_s = -1;
-        if (u >= 0) {
-            ui = uinfo[u];
-            x[k] = (T)ui.x;
-            load_seed(seeds, (size_t)m * nunit_all + u, vp[k], vm[k], e[k]);
-        }
-#pragma unroll
-        for (int rr = 0; rr < RG; rr++) {
-            const int r = r0 + rr;
-            C2 Pv[2], Qv[2];
-#pragma unroll
-            for (int side = 0; side < 2; side++) {
-                const int ring = side == 0 ? ui.ring_n : ui.ring_s;
-                Pv[side] = C2{0, 0};
-                Qv[side] = C2{0, 0};
-                if (ring < 0 || r >= R) continue;
-                if (ring_active && !ring_active[ring]) continue;
-                const C2 *prow = phi + ((size_t)r * nring + ring) * row + L;
-                const C2 g = prow[m], gm = prow[-m];
-                Pv[side] = g;
-                Qv[side] = C2{gm.x, -gm.y};
-            }
-            const C2 u1{Pv[0].x + Qv[1].x, Pv[0].y + Qv[1].y};
-            const C2 u2{Qv[0].x + Pv[1].x, Qv[0].y + Pv[1].y};
-            const C2 u3{Pv[0].x - Qv[1].x, Pv[0].y - Qv[1].y};
-            const C2 u4{Pv[1].x - Qv[0].x, Pv[1].y - Qv[0].y};
-            X1[k][rr] = swap ? u3 : u1;
-            X2[k][rr] = swap ? C2{-u4.x, -u4.y} : u2;
-            X3[k][rr] = swap ? u1 : u3;
-            X4[k][rr] = swap ? C2{-u2.x, -u2.y} : u4;
-        }
-    }
-
-    T (*tr)[S] = s_tr[warp];
-    for (int lt = l0; lt <= L; lt += TLA) {
-        __syncthreads();
-        for (int i = tid; i < TLA; i += NT) {
-            const int l = lt + i;
-            s_coef[i] = (l <= L) ? coef[mbase + l] : V4{0, 0, 0, 0};
-        }
-        __syncthreads();
-        const int nl = min(TLA, L - lt + 1);
-        bool live = true;
-#pragma unroll
-        for (int k = 0; k < P; k++) live &= (e[k] == 0);
-        const bool all_live = __all_sync(0xffffffffu, live);
-        const int nkb = (nl + K - 1) / K;
-
-        // K l-steps into ta[K][RG][4] (slot of step kk = parity of kk), then recur
-#define AKRA_ADJ_KBLOCK(GATED)                                                                  \
-    for (int kb = 0; kb < nkb; kb++) {                                                          \
-        T ta[K][RG][4];                                                                         \
-        _Pragma("unroll") for (int kk = 0; kk < K; kk++)                                        \
-            _Pragma("unroll") for (int rr = 0; rr < RG; rr++)                                   \
-                _Pragma("unroll") for (int q = 0; q < 4; q++) ta[kk][rr][q] = 0;                \
-        _Pragma("unroll") for (int kk = 0; kk < K; kk++) {                                      \
-            const V4 c = s_coef[kb * K + kk];                                                   \
-            const bool slotA = (kk & 1) == 0;                                                   \
-            bool any = true;                                                                    \
-            if (GATED) {                                                                        \
-                bool a_ = false;                                                                \
-                _Pragma("unroll") for (int k = 0; k < P; k++) a_ |= (e[k] == 0);                \
-                any = __any_sync(0xffffffffu, a_);                                              \
-            }                                                                                   \
-            if (any) {                                                                          \
-                _Pragma("unroll") for (int k = 0; k < P; k++) {                                 \
-                    const T lp = (GATED && e[k] != 0) ? T(0) : vp[k];                           \
-                    const T lm0 = (GATED && e[k] != 0) ? T(0) : vm[k];                          \
-                    const T lm = slotA ? lm0 : -lm0;                                            \
-                    _Pragma("unroll") for (int rr = 0; rr < RG; rr++) {                         \
-                        const C2 eP = slotA ? X1[k][rr] : X3[k][rr];                            \
-                        const C2 eM = slotA ? X2[k][rr] : X4[k][rr];                            \
-                        const C2 bP = slotA ? X3[k][rr] : X1[k][rr];                            \
-                        const C2 bM = slotA ? X4[k][rr] : X2[k][rr];                            \
-                        T *t = ta[kk][rr];                                                      \
-                        t[0] = fma(lp, eP.x, fma(lm, eM.x, t[0]));                              \
-                        t[1] = fma(lp, eP.y, fma(lm, eM.y, t[1]));                              \
-                        t[2] = fma(lp, bP.x, fma(lm, bM.x, t[2]));                              \
-                        t[3] = fma(lp, bP.y, fma(lm, bM.y, t[3]));                              \
-                    }                                                                           \
-                }                                                                               \
-            }                                                                                   \
-            _Pragma("unroll") for (int k = 0; k < P; k++) {                                     \
-                const T t1 = fma(c.x, x[k], c.z);                                               \
-                const T t2 = fma(c.x, x[k], -c.z);                                              \
-                const T np = fma(t1, vp[k], -c.y * vpo[k]);                                     \
-                const T nm = fma(t2, vm[k], -c.y * vmo[k]);                                     \
-                vpo[k] = vp[k];                                                                 \
-                vmo[k] = vm[k];                                                                 \
-                vp[k] = np;                                                                     \
-                vm[k] = nm;                                                                     \
-                if (GATED && e[k] < 0 &&                                                        \
-                    (fabs(vp[k]) > Scale<T>::hi() || fabs(vm[k]) > Scale<T>::hi())) {           \
-                    vp[k] *= Scale<T>::inv();                                                   \
-                    vm[k] *= Scale<T>::inv();                                                   \
-                    vpo[k] *= Scale<T>::inv();                                                  \
-                    vmo[k] *= Scale<T>::inv();                                                  \
-                    e[k]++;                                                                     \
-                }                                                                               \
-            }                                                                                   \
-        }                                                                                       \
-        /* warp transpose through shared memory: lane L's value i goes to tr[i][L]; lane j */  \
-        /* then sums row j, i.e. value j over all lanes */                                       \
-        _Pragma("unroll") for (int kk = 0; kk < K; kk++)                                        \
-            _Pragma("unroll") for (int rr = 0; rr < RG; rr++)                                   \
-                _Pragma("unroll") for (int q = 0; q < 4; q++)                                   \
-                    tr[(kk * RG + rr) * 4 + q][lane] = ta[kk][rr][q];                           \
-        __syncwarp();                                                                           \
-        T sum = 0;                                                                              \
-        _Pragma("unroll") for (int i = 0; i < 32; i++) sum += tr[lane][i];                      \
-        __syncwarp();                                                                           \
-        {                                                                                       \
-            const int kk = lane / (4 * RG), rr = (lane / 4) % RG, q = lane & 3;                 \
-            s_red[warp][kb * K + kk][rr][q] = sum;                                              \
-        }                                                                                       \
-    }
-
-        if (all_live) {
-            AKRA_ADJ_KBLOCK(false)
-        } else {
-            AKRA_ADJ_KBLOCK(true)
-        }
-#undef AKRA_ADJ_KBLOCK
-        __syncthreads();
-        // sum the warps and write this chunk's partial sums for the tile
-        for (int i = tid; i < nl * RG * 4; i += NT) {
-            const int step = i / (RG * 4), rem = i - step * RG * 4, rr = rem >> 2, q = rem & 3;
-            const int r = r0 + rr;
-            if (r >= R) continue;
-            T sv = 0;
-#pragma unroll
-            for (int w = 0; w < NW; w++) sv += s_red[w][step][rr][q];
-            partial[(((size_t)chunk * R + r) * ntri + mbase + lt + step) * 4 + q] = sv;
-        }
-    }
-}
 
 // ---------------------------------------------------------------------------
 // epilogue: sum chunk partials, apply f_l/2 and the spin ±2 -> E/B recombination
@@ -460,29 +71,48 @@ template <typename T> const T *D_ptr(akra_plan p);
 template <> const float *D_ptr<float>(akra_plan p) { return p->d_D32; }
 template <> const double *D_ptr<double>(akra_plan p) { return p->d_D64; }
 
+template <typename T>
+LegArgs<T> leg_args(akra_plan p, const LegShape &s, LegMode mode, const int *units, int nunits, int R)
+{
+    LegArgs<T> a{};
+    a.L = p->lmax;
+    a.nring = p->nring;
+    a.nchunks = (nunits + s.NT * s.P - 1) / (s.NT * s.P);
+    a.nunits = nunits;
+    a.nunit_all = p->nunit;
+    a.R = R;
+    a.ntri = p->ntri;
+    a.units = units;
+    a.uinfo = p->d_units;
+    a.coef = coef_ptr<T>(p);
+    a.seeds = seed_ptr<T>(p);
+    a.fl = mode == LegMode::KS ? D_ptr<T>(p) : nullptr;
+    a.ring_active = units == p->d_all_units ? nullptr : p->d_ring_active;
+    a.skip = p->cur_skip;
+    return a;
+}
+
 template <typename T, int P, int RG, int NT>
 static void launch_synth(akra_plan p, LegMode mode, const void *alm, void *phi, int R,
                          const int *units, int nunits, cudaStream_t st)
 {
-    const int nchunks = (nunits + NT * P - 1) / (NT * P);
-    dim3 grid((unsigned)(p->lmax + 1) * nchunks, (R + RG - 1) / RG);
-    k_leg_synth<T, P, RG, NT><<<grid, NT, 0, st>>>(
-        p->lmax, p->nring, p->ntri, nchunks, nunits, units, p->d_units, coef_ptr<T>(p),
-        seed_ptr<T>(p), p->nunit, mode == LegMode::KS ? D_ptr<T>(p) : nullptr, (const cx_t<T> *)alm, R,
-        (cx_t<T> *)phi, units == p->d_all_units ? nullptr : p->d_ring_active, p->cur_skip);
+    LegArgs<T> a = leg_args<T>(p, LegShape{P, NT, RG}, mode, units, nunits, R);
+    a.alm = (const cx_t<T> *)alm;
+    a.phi = (cx_t<T> *)phi;
+    dim3 grid((unsigned)(p->lmax + 1) * a.nchunks, (R + RG - 1) / RG);
+    k_leg_synth<T, P, RG, NT><<<grid, NT, 0, st>>>(a);
 }
 
 template <typename T, int P, int RG, int NT>
 static int launch_adjoint(akra_plan p, const void *phi, void *partial, int R, const int *units,
                           int nunits, cudaStream_t st)
 {
-    const int nchunks = (nunits + NT * P - 1) / (NT * P);
-    dim3 grid((unsigned)(p->lmax + 1) * nchunks, (R + RG - 1) / RG);
-    k_leg_adjoint<T, P, RG, NT><<<grid, NT, 0, st>>>(
-        p->lmax, p->nring, p->ntri, nchunks, nunits, units, p->d_units, coef_ptr<T>(p),
-        seed_ptr<T>(p), p->nunit, (const cx_t<T> *)phi, R, (T *)partial,
-        units == p->d_all_units ? nullptr : p->d_ring_active, p->cur_skip);
-    return nchunks;
+    LegArgs<T> a = leg_args<T>(p, LegShape{P, NT, RG}, LegMode::Synth, units, nunits, R);
+    a.phi_in = (const cx_t<T> *)phi;
+    a.partial = (T *)partial;
+    dim3 grid((unsigned)(p->lmax + 1) * a.nchunks, (R + RG - 1) / RG);
+    k_leg_adjoint<T, P, RG, NT><<<grid, NT, 0, st>>>(a);
+    return a.nchunks;
 }
 
 // shape dispatch: (P, RG) combinations compiled for each precision, NT = 128
@@ -540,6 +170,8 @@ akra_status adjoint_epilogue(akra_plan p, LegMode mode, const void *partial, int
 
 int legendre_chunks(int nunits, const LegShape &s) { return (nunits + s.NT * s.P - 1) / (s.NT * s.P); }
 
+template LegArgs<float> leg_args<float>(akra_plan, const LegShape &, LegMode, const int *, int, int);
+template LegArgs<double> leg_args<double>(akra_plan, const LegShape &, LegMode, const int *, int, int);
 template akra_status legendre_synth<float>(akra_plan, const LegShape &, LegMode, const void *, void *,
                                            int, const int *, int, cudaStream_t);
 template akra_status legendre_synth<double>(akra_plan, const LegShape &, LegMode, const void *,

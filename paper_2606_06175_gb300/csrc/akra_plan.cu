@@ -290,14 +290,18 @@ akra_status op_adjoint(akra_plan p, LegMode mode, const void *map, void *alm, bo
                        cudaStream_t st)
 {
     const LegShape s = leg_shape(p, prec_of<T>(), R);
+    // with weights, rings where W = 0 contribute exactly nothing: transform the active ones only
+    const bool act = weighted && p->has_weights;
+    const int *units = act ? p->d_active_units : p->d_all_units;
+    const int nunits = act ? p->n_active_units : p->nunit;
+    const int *rings = act ? p->d_active_rings : p->d_all_rings;
+    const int nrings = act ? p->n_active_rings : p->nring;
     AKRA_TRY(ws_reserve(p, p->phi, phi_bytes(p, sizeof(cx_t<T>), R)));
-    AKRA_TRY(ws_reserve(p, p->partial, (size_t)legendre_chunks(p->nunit, s) * R * p->ntri * 4 *
+    AKRA_TRY(ws_reserve(p, p->partial, (size_t)legendre_chunks(nunits, s) * R * p->ntri * 4 *
                                            sizeof(T)));
-    AKRA_TRY(ring_fft<T>(p, FftMode::Adjoint, p->phi.ptr, map, nullptr, weighted, R,
-                         p->d_all_rings, p->nring, st));
+    AKRA_TRY(ring_fft<T>(p, FftMode::Adjoint, p->phi.ptr, map, nullptr, weighted, R, rings, nrings, st));
     int nch = 0;
-    AKRA_TRY(legendre_adjoint<T>(p, s, p->phi.ptr, p->partial.ptr, R, p->d_all_units, p->nunit,
-                                 &nch, st));
+    AKRA_TRY(legendre_adjoint<T>(p, s, p->phi.ptr, p->partial.ptr, R, units, nunits, &nch, st));
     return adjoint_epilogue<T>(p, mode, p->partial.ptr, nch, nullptr, 0.0, alm, R, st);
 }
 

@@ -295,7 +295,9 @@ akra_status ring_fft(akra_plan p, FftMode mode, void *phi, const void *map_in, v
 // never inside a stream capture)
 akra_status ring_fft_prepare(akra_plan p)
 {
-    const int nmax = 4 * p->nside;
+    // the attribute is per kernel, shared by every plan: clear the largest supported ring
+    (void)p;
+    const int nmax = FFT_NMAX;
     const int s32 = (nmax + FFT_NT) * (int)sizeof(float2);
     const int s64 = (nmax + FFT_NT) * (int)sizeof(double2);
     AKRA_CUDA_TRY(cudaFuncSetAttribute(k_ring_fft<float, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, s32));

@@ -1,0 +1,283 @@
+// akra_ringfft32_impl.cuh -- FP32 ring FFT bodies (see akra_ringfft32.cu for the method),
+// shared by the per-plan launches and the multi-instance launches (akra_batch.cu).
+#pragma once
+#include "akra_internal.cuh"
+
+namespace akra {
+
+constexpr int F32_NT = 1024;
+constexpr int F32_MMAX = 8 * kMaxNside;   // largest convolution length (n <= 4 nside - 4)
+
+__device__ __forceinline__ float2 cm(float2 a, float2 b)
+{
+    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ float2 cmc(float2 a, float2 b)   // a * conj(b)
+{
+    return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.y, b.x, -a.x * b.y));
+}
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+// multiply by s·i (s = ±1)
+template <int S> __device__ __forceinline__ float2 mul_si(float2 a)
+{
+    return S > 0 ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+}
+
+// e^{S 2πi t/L} from the table e^{-2πi u/MMAX}
+template <int S>
+__device__ __forceinline__ float2 w_pow2(const float2 *__restrict__ tw2, int t, int L)
+{
+    float2 w = tw2[t * (F32_MMAX / L)];
+    if (S > 0) w.y = -w.y;
+    return w;
+}
+
+// in-place DIF with DFT sign S: natural order in, bit-reversed out
+template <int S>
+__device__ void dif(float2 *x, int M, int logM, const float2 *__restrict__ tw2)
+{
+    int L = M;
+    if (logM & 1) {
+        const int h = M >> 1;
+        for (int i = threadIdx.x; i < h; i += blockDim.x) {
+            const float2 a = x[i], b = x[i + h];
+            x[i] = cadd(a, b);
+            x[i + h] = cm(csub(a, b), w_pow2<S>(tw2, i, M));
+        }
+        __syncthreads();
+        L = h;
+    }
+    for (; L >= 4; L >>= 2) {
+        const int q = L >> 2;
+        for (int b = threadIdx.x; b < (M >> 2); b += blockDim.x) {
+            const int blk = b / q, i = b - blk * q;
+            float2 *p = x + blk * L + i;
+            const float2 a0 = p[0], a1 = p[q], a2 = p[2 * q], a3 = p[3 * q];
+            const float2 w1 = w_pow2<S>(tw2, i, L), w2 = w_pow2<S>(tw2, 2 * i, L),
+                         w3 = w_pow2<S>(tw2, 3 * i, L);
+            const float2 u0 = cadd(a0, a2), u1 = cadd(a1, a3), d0 = csub(a0, a2);
+            const float2 d1 = mul_si<S>(csub(a1, a3));
+            p[0] = cadd(u0, u1);
+            p[q] = cm(csub(u0, u1), w2);
+            p[2 * q] = cm(cadd(d0, d1), w1);
+            p[3 * q] = cm(csub(d0, d1), w3);
+        }
+        __syncthreads();
+    }
+}
+
+// in-place DIT with DFT sign S: bit-reversed order in, natural out (DIT<-S>(DIF<S>(x)) = M x)
+template <int S>
+__device__ void dit(float2 *x, int M, int logM, const float2 *__restrict__ tw2)
+{
+    const int Lmax = (logM & 1) ? (M >> 1) : M;
+    for (int L = 4; L <= Lmax; L <<= 2) {
+        const int q = L >> 2;
+        for (int b = threadIdx.x; b < (M >> 2); b += blockDim.x) {
+            const int blk = b / q, i = b - blk * q;
+            float2 *p = x + blk * L + i;
+            const float2 p0 = p[0], p1 = p[q], p2 = p[2 * q], p3 = p[3 * q];
+            const float2 w1 = w_pow2<S>(tw2, i, L), w2 = w_pow2<S>(tw2, 2 * i, L);
+            float2 t = cm(p1, w2);
+            const float2 u0 = cadd(p0, t), u1 = csub(p0, t);
+            t = cm(p3, w2);
+            const float2 u2 = cadd(p2, t), u3 = csub(p2, t);
+            const float2 v2 = cm(u2, w1), v3 = mul_si<S>(cm(u3, w1));
+            p[0] = cadd(u0, v2);
+            p[2 * q] = csub(u0, v2);
+            p[q] = cadd(u1, v3);
+            p[3 * q] = csub(u1, v3);
+        }
+        __syncthreads();
+    }
+    if (logM & 1) {
+        const int h = M >> 1;
+        for (int i = threadIdx.x; i < h; i += blockDim.x) {
+            const float2 a = x[i], b = cm(x[i + h], w_pow2<S>(tw2, i, M));
+            x[i] = cadd(a, b);
+            x[i + h] = csub(a, b);
+        }
+        __syncthreads();
+    }
+}
+
+// Bluestein DFT of x[0..n) in place (natural order in and out), sign S.
+// chirp c_j = tw_ring[j^2 mod 2n] = e^{iπ j²/n}; bhat = DIF<-1> of the chirp filter.
+template <int S>
+__device__ void bluestein(float2 *x, int n, int M, int logM, const float2 *__restrict__ tw_ring,
+                          const float2 *__restrict__ bhat, const float2 *__restrict__ tw2)
+{
+    const int n2 = 2 * n;
+    for (int j = threadIdx.x; j < M; j += blockDim.x) {
+        if (j < n) {
+            const float2 c = tw_ring[(int)(((long long)j * j) % n2)];
+            const float2 v = x[j];
+            // forward: x conj(c);  backward: conj(x c) (conjugation trick)
+            x[j] = S < 0 ? cmc(v, c) : make_float2(v.x * c.x - v.y * c.y, -(v.x * c.y + v.y * c.x));
+        } else {
+            x[j] = make_float2(0.f, 0.f);
+        }
+    }
+    __syncthreads();
+    dif<-1>(x, M, logM, tw2);
+    for (int k = threadIdx.x; k < M; k += blockDim.x) x[k] = cm(x[k], bhat[k]);
+    __syncthreads();
+    dit<+1>(x, M, logM, tw2);
+    const float inv = 1.0f / (float)M;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        const float2 c = tw_ring[(int)(((long long)k * k) % n2)];
+        const float2 y = x[k];
+        // forward: conj(c) y / M;  backward: c conj(y) / M
+        const float2 r = S < 0 ? cmc(y, c) : cmc(c, y);
+        x[k] = make_float2(r.x * inv, r.y * inv);
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ int fdiv(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
+
+template <int MODE>
+__device__ __forceinline__ void ring_fft32_item(const Fft32Args &a, const int ring, const int r,
+                                                float2 *buf, float2 *red)
+{
+    const int L = a.L, nring = a.nring;
+    const long long npix = a.npix;
+    const RingInfo *__restrict__ rinfo = a.rinfo;
+    const int *__restrict__ fftM = a.fftM;
+    const long long *__restrict__ bhat_off = a.bhat_off;
+    const float2 *__restrict__ bhat_all = a.bhat_all;
+    const float2 *__restrict__ tw2 = a.tw2;
+    const float2 *__restrict__ tw_all = a.tw_all;
+    const float *__restrict__ W = a.W;
+    const int weighted = a.weighted;
+    float2 *__restrict__ phi = a.phi;
+    const float *__restrict__ map_in = a.map_in;
+    float *__restrict__ map_out = a.map_out;
+    const int tid = threadIdx.x;
+    const RingInfo ri = rinfo[ring];
+    const int n = ri.nphi, sigma = ri.sigma;
+    const long long first = ri.first;
+    const float2 *tw = tw_all + ri.tw_off;         // e^{iπ t/n}, t < 2n
+    const int M = fftM[ri.ilen];
+    const bool pow2 = (M == n);
+    const int logM = 31 - __clz(M), logn = 31 - __clz(n);
+    const float2 *bhat = pow2 ? nullptr : bhat_all + bhat_off[ri.ilen];
+    float2 *prow = phi + ((size_t)r * nring + ring) * (2 * (size_t)L + 1) + L;
+
+    if (MODE != (int)FftMode::Adjoint) {
+        // fold Φ(m) into n bins: F[k] = e^{iπσk/n} Σ_q (-1)^{σq} Φ(k + nq)
+        if (n >= F32_NT) {
+            for (int k = tid; k < n; k += F32_NT) {
+                const int qlo = -((L + k) / n), qhi = fdiv(L - k, n);
+                float2 acc = make_float2(0.f, 0.f);
+                for (int q = qlo; q <= qhi; q++) {
+                    const float2 v = prow[k + n * q];
+                    if (sigma && (q & 1)) acc = csub(acc, v);
+                    else acc = cadd(acc, v);
+                }
+                buf[k] = sigma ? cm(acc, tw[k]) : acc;
+            }
+        } else {
+            const int G = F32_NT / n, g = tid / n, k = tid - g * n;
+            if (g < G) {
+                const int qlo = -((L + k) / n), qhi = fdiv(L - k, n);
+                float2 acc = make_float2(0.f, 0.f);
+                for (int q = qlo + g; q <= qhi; q += G) {
+                    const float2 v = prow[k + n * q];
+                    if (sigma && (q & 1)) acc = csub(acc, v);
+                    else acc = cadd(acc, v);
+                }
+                red[g * n + k] = acc;
+            }
+            __syncthreads();
+            for (int kk = tid; kk < n; kk += F32_NT) {
+                float2 acc = make_float2(0.f, 0.f);
+                for (int gg = 0; gg < G; gg++) acc = cadd(acc, red[gg * n + kk]);
+                buf[kk] = sigma ? cm(acc, tw[kk]) : acc;
+            }
+        }
+        __syncthreads();
+        // backward DFT: pixel values (bit-reversed order for power-of-two rings)
+        if (pow2) dif<+1>(buf, n, logn, tw2);
+        else bluestein<+1>(buf, n, M, logM, tw, bhat, tw2);
+        if (MODE == (int)FftMode::Synth) {
+            float *o1 = map_out + ((size_t)r * 2 + 0) * npix + first;
+            float *o2 = map_out + ((size_t)r * 2 + 1) * npix + first;
+            for (int k = tid; k < n; k += F32_NT) {
+                const int j = pow2 ? (int)(__brev((unsigned)k) >> (32 - logn)) : k;
+                float2 v = buf[k];
+                if (weighted) {
+                    const float wj = W[first + j];
+                    v.x *= wj;
+                    v.y *= wj;
+                }
+                o1[j] = v.x;
+                o2[j] = v.y;
+            }
+            return;
+        }
+        for (int k = tid; k < n; k += F32_NT) {
+            const int j = pow2 ? (int)(__brev((unsigned)k) >> (32 - logn)) : k;
+            const float wj = W[first + j];
+            buf[k].x *= wj;
+            buf[k].y *= wj;
+        }
+        __syncthreads();
+    } else {
+        const float *u1 = map_in + ((size_t)r * 2 + 0) * npix + first;
+        const float *u2 = map_in + ((size_t)r * 2 + 1) * npix + first;
+        for (int k = tid; k < n; k += F32_NT) {
+            const int j = pow2 ? (int)(__brev((unsigned)k) >> (32 - logn)) : k;
+            float2 v = make_float2(u1[j], u2[j]);
+            if (weighted) {
+                const float wj = W[first + j];
+                v.x *= wj;
+                v.y *= wj;
+            }
+            buf[k] = v;
+        }
+        __syncthreads();
+    }
+    // forward DFT back to bins (natural order)
+    if (pow2) dit<-1>(buf, n, logn, tw2);
+    else bluestein<-1>(buf, n, M, logM, tw, bhat, tw2);
+    // unfold: Φ'(m) = e^{-iπσk/n} (-1)^{σq} Ŵ[k],  m = k + nq
+    for (int mm = tid; mm < 2 * L + 1; mm += F32_NT) {
+        const int m = mm - L;
+        const int q = fdiv(m, n), k = m - q * n;
+        float2 v = buf[k];
+        if (sigma) {
+            v = cmc(v, tw[k]);
+            if (q & 1) v = make_float2(-v.x, -v.y);
+        }
+        prow[m] = v;
+    }
+}
+
+
+template <int MODE>
+__global__ void __launch_bounds__(F32_NT) k_ring_fft32(Fft32Args a)
+{
+    if (a.skip && *a.skip) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2 *buf = reinterpret_cast<float2 *>(smem_raw);
+    const int ring = a.rings ? a.rings[blockIdx.x] : (int)blockIdx.x;
+    ring_fft32_item<MODE>(a, ring, blockIdx.y, buf, buf + a.mmax);
+}
+
+// batched form over several plans: item = {instance, index into its ring list, RHS, 0}
+template <int MODE>
+__global__ void __launch_bounds__(F32_NT)
+k_ring_fft32_batch(const Fft32Args *__restrict__ insts, const int4 *__restrict__ items, int mmax)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2 *buf = reinterpret_cast<float2 *>(smem_raw);
+    const int4 w = items[blockIdx.x];
+    const Fft32Args a = insts[w.x];
+    if (a.skip && *a.skip) return;
+    const int ring = a.rings ? a.rings[w.y] : w.y;
+    ring_fft32_item<MODE>(a, ring, w.z, buf, buf + mmax);
+}
+
+}  // namespace akra

@@ -1,0 +1,121 @@
+"""Parity at the full benchmark size (Nside 2048, lmax 4096), in the autotuned launch
+configuration the benchmark uses: the oracle computes sampled outputs one by one (whole
+rings of the synthesis, whole m-columns of the adjoint), and H is checked through properties
+that hold at any size (symmetry in the real-dof metric; FP32 against FP64).
+
+FP32 near the poles: the l-recurrence at small θ amplifies each step's rounding by up to
+~1/θ, so the rings closest to the poles carry relative errors up to ~ε32 sqrt(L)/θ
+(a few 1e-2 for the first rings at Nside 2048); they are bounded separately.  Weighted
+operators on the DES-like footprint (|dec| <= 60 deg, no polar rings) meet tol32(L)."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+import synthetic as S
+from paper_2606_06175_gb300 import akra as A
+
+pytestmark = pytest.mark.gpu
+N, L = 2048, 4096
+DEV = "cuda:0"
+RINGS = [1, 2, 37, 600, 2047, 2048, 3000, 4096, 5000, 6143, 6144, 8000, 8190, 8191]
+MS = [0, 1, 2, 3, 257, 2048, 4000, 4096]
+
+
+def tol32(lmax):
+    return 4 * 2.0 ** -24 * max(lmax, 16)
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.fixture(scope="module")
+def plan():
+    p = A.akra_plan_create(N, L)
+    sv = S.survey(N, "des", S.SEEDS["des2048"])
+    A.akra_plan_set_weights(p, torch.from_numpy(sv["ninv"]).to(DEV), 1e-3)
+    A.akra_autotune(p, A.MIXED, 1)
+    return p
+
+
+@pytest.fixture(scope="module")
+def alm():
+    rng = np.random.default_rng(2048)
+    return S.random_alm(L, rng), S.random_alm(L, rng)
+
+
+@pytest.mark.parametrize("prec", [A.F64, A.F32])
+def test_fullsize_synthesis_sampled_rings(plan, alm, prec):
+    aE, aB = alm
+    x = torch.from_numpy(np.stack([aE, aB])[None]).to(DEV, torch.complex128 if prec == A.F64 else torch.complex64)
+    g = A.akra_synth_spin2(plan, prec, x)[0]
+    F = O.legendre_synth(N, L, aE, aB, np.array(RINGS, np.int32))
+    num = den = 0.0
+    for k, r in enumerate(RINGS):
+        ct, st, n, sg, first = O.ring_info(N, r)
+        ref = O.ring_phase_sum(F[k], L, n, sg)
+        got = g[:, first:first + n].double().cpu().numpy()
+        d = np.abs(got[0] + 1j * got[1] - ref)
+        ring_err = math.sqrt(float((d ** 2).sum()) / float((np.abs(ref) ** 2).sum()))
+        if prec == A.F64:
+            num += float((d ** 2).sum())
+            den += float((np.abs(ref) ** 2).sum())
+        elif abs(ct) < 0.99:
+            assert ring_err < tol32(L), (r, ring_err)
+        else:
+            assert ring_err < 0.25, (r, ring_err)   # polar amplification, see module docstring
+    if prec == A.F64:
+        assert math.sqrt(num / den) < 1e-10
+
+
+@pytest.mark.parametrize("prec", [A.F64, A.F32])
+def test_fullsize_adjoint_sampled_m(plan, prec):
+    torch.manual_seed(7)
+    u = torch.randn((1, 2, 12 * N * N), dtype=torch.float64, device=DEV)
+    a = A.akra_adjoint_synth_spin2(plan, prec, u if prec == A.F64 else u.float())[0].cpu().numpy()
+    un = u[0].cpu().numpy()
+    if prec == A.F32:
+        un = un.astype(np.float32).astype(np.float64)
+    rE, rB = O.adjoint_synth_spin2(N, L, un[0], un[1], m_list=np.array(MS, np.int32))
+    sel = np.concatenate([np.arange(O.tri_index(L, m, m), O.tri_index(L, m, m) + L + 1 - m) for m in MS])
+    got = a[:, sel]
+    ref = np.stack([rE[sel], rB[sel]])
+    err = rel(got, ref)
+    # FP32 full sky: the polar rings' amplified error reaches every coefficient (module docstring)
+    assert err < (1e-10 if prec == A.F64 else 4 * tol32(L)), err
+
+
+def test_fullsize_weighted_adjoint_fp32(plan):
+    """A^T W u on the DES-like footprint (no polar rings): FP32 within tol32(L) of FP64."""
+    torch.manual_seed(8)
+    u = torch.randn((1, 2, 12 * N * N), dtype=torch.float64, device=DEV)
+    a64 = A.akra_apply_At(plan, A.F64, u, weighted=True)
+    a32 = A.akra_apply_At(plan, A.F32, u.float(), weighted=True).to(torch.complex128)
+    err = float(torch.linalg.vector_norm(a32 - a64) / torch.linalg.vector_norm(a64))
+    assert err < tol32(L), err
+
+
+def test_fullsize_H_symmetric_and_fp32_close(plan):
+    rng = np.random.default_rng(11)
+    x = torch.from_numpy(np.stack([S.random_alm(L, rng), S.random_alm(L, rng)])[None]).to(DEV)
+    z = torch.from_numpy(np.stack([S.random_alm(L, rng), S.random_alm(L, rng)])[None]).to(DEV)
+    hx = A.akra_apply_H(plan, A.F64, x)
+    hz = A.akra_apply_H(plan, A.F64, z)
+    ls, ms = O.lm_arrays(L)
+    w = torch.from_numpy(np.where(ms == 0, 1.0, 2.0)).to(DEV)
+    m0 = torch.from_numpy(ms == 0).to(DEV)
+
+    def dot(a, b):
+        ai = torch.where(m0, 0.0, a.imag)
+        bi = torch.where(m0, 0.0, b.imag)
+        return float((w * (a.real * b.real + ai * bi)).sum())
+
+    lhs = dot(hx[0, 0], z[0, 0]) + dot(hx[0, 1], z[0, 1])
+    rhs = dot(x[0, 0], hz[0, 0]) + dot(x[0, 1], hz[0, 1])
+    assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
+    h32 = A.akra_apply_H(plan, A.F32, x.to(torch.complex64)).to(torch.complex128)
+    err = float(torch.linalg.vector_norm(h32 - hx) / torch.linalg.vector_norm(hx))
+    assert err < tol32(L), err
