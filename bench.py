@@ -116,10 +116,10 @@ def make_inputs(rank, dev):
 
 def legendre_flops(desc, R=1):
     """Algorithmic FP32 work of one Legendre launch over the active ring pairs: every
-    (l >= 2, m, pair) step does two spin recurrences (6 flops-as-FMA ops) and 8 FMA of
-    contraction per RHS; flops = 2 x FMA-ops."""
+    (l >= 2, m, pair) step does two monic spin recurrences (4 FMA) and 8 FMA of contraction
+    per RHS; flops = 2 x FMA."""
     steps = desc["n_active_units"] * (desc["ntri"] - 3)
-    return steps * (6 + 8 * R) * 2, steps
+    return steps * (4 + 8 * R) * 2, steps
 
 
 def cpu_oracle_H_estimate(nside, lmax, target_s=15.0):

@@ -4,7 +4,10 @@
 // Work unit: one m and one ring pair (north ring θ, south ring π-θ; the equator ring alone).
 // Two recurrences run in ℓ, one per spin s = ±2 (x = cos θ, A_l, B_l the normalised
 // Wigner-d coefficients):
-//     sλ_{l+1} = (A_l x + s A_l m/(l(l+1))) sλ_l - A_l B_l sλ_{l-1}
+//     sλ_{l+1} = (A_l x + s A_l m/(l(l+1))) sλ_l - A_l B_l sλ_{l-1},
+// carried in monic form μ_l = sλ_l / σ_l (σ from the plan's table, between 0.17 and 1), so a
+// step is μ_{l+1} = (A'_l x ± c'_l) μ_l - μ_{l-1}: 2 FMA per spin; σ_l is folded into the staged
+// alm (synthesis) and into the per-l partial sums (adjoint).
 // (kept separate: near the poles one spin is O(1) and the other tiny, and any mixed
 // combination would leak the large one's rounding into the small one).  The mirror ring
 // follows from  sλ_lm(π-θ) = (-1)^{l+m} (-s)λ_lm(θ), so one pair of recurrences feeds both

@@ -84,7 +84,8 @@ __device__ __forceinline__ void leg_synth_item(const LegArgs<T> &a, const int m,
             if (l <= L && r < R) {
                 C2 E = alm[((size_t)r * 2 + 0) * ntri + mbase + l];
                 C2 B = alm[((size_t)r * 2 + 1) * ntri + mbase + l];
-                const T f = fl ? fl[l] : T(-1);
+                // KS (or -1) factor times the monic scale σ_l: λ_l = σ_l μ_l
+                const T f = (fl ? fl[l] : T(-1)) * coef[mbase + l].z;
                 if (m == 0) E.y = B.y = 0;
                 // c = f (E + iB), d = f (E - iB)
                 v = V4{f * (E.x - B.y), f * (E.y + B.x), f * (E.x + B.y), f * (E.y - B.x)};
@@ -129,10 +130,10 @@ __device__ __forceinline__ void leg_synth_item(const LegArgs<T> &a, const int m,
             }                                                                               \
         }                                                                                   \
         _Pragma("unroll") for (int k = 0; k < P; k++) {                                     \
-            const T t1 = fma(c.x, x[k], c.z);                                               \
-            const T t2 = fma(c.x, x[k], -c.z);                                              \
-            const T np = fma(t1, vp[k], -c.y * vpo[k]);                                     \
-            const T nm = fma(t2, vm[k], -c.y * vmo[k]);                                     \
+            const T t1 = fma(c.x, x[k], c.y);                                               \
+            const T t2 = fma(c.x, x[k], -c.y);                                              \
+            const T np = fma(t1, vp[k], -vpo[k]);                                           \
+            const T nm = fma(t2, vm[k], -vmo[k]);                                           \
             vpo[k] = vp[k];                                                                 \
             vmo[k] = vm[k];                                                                 \
             vp[k] = np;                                                                     \
@@ -372,10 +373,10 @@ __device__ __forceinline__ void leg_adjoint_item(
                 }                                                                               \
             }                                                                                   \
             _Pragma("unroll") for (int k = 0; k < P; k++) {                                     \
-                const T t1 = fma(c.x, x[k], c.z);                                               \
-                const T t2 = fma(c.x, x[k], -c.z);                                              \
-                const T np = fma(t1, vp[k], -c.y * vpo[k]);                                     \
-                const T nm = fma(t2, vm[k], -c.y * vmo[k]);                                     \
+                const T t1 = fma(c.x, x[k], c.y);                                               \
+                const T t2 = fma(c.x, x[k], -c.y);                                              \
+                const T np = fma(t1, vp[k], -vpo[k]);                                           \
+                const T nm = fma(t2, vm[k], -vmo[k]);                                           \
                 vpo[k] = vp[k];                                                                 \
                 vmo[k] = vm[k];                                                                 \
                 vp[k] = np;                                                                     \
@@ -421,7 +422,8 @@ __device__ __forceinline__ void leg_adjoint_item(
             T sv = 0;
 #pragma unroll
             for (int w = 0; w < NW; w++) sv += s_red[w][step][rr][q];
-            partial[(((size_t)chunk * R + r) * ntri + mbase + lt + step) * 4 + q] = sv;
+            // the recurrence ran on μ_l = λ_l / σ_l
+            partial[(((size_t)chunk * R + r) * ntri + mbase + lt + step) * 4 + q] = sv * s_coef[step].z;
         }
     }
 }

@@ -77,29 +77,39 @@ __global__ void k_geometry(int N, RingInfo *rings, UnitInfo *units)
     }
 }
 
-// Recurrence coefficients per (l, m) for the λp/λm recurrence (Wigner-d, normalised, s = 2):
+// Recurrence coefficients per (l, m), s = ±2 (Wigner-d, normalised):
+//   sλ_{l+1} = (A_l x + s A_l m/(l(l+1))) sλ_l - A_l B_l sλ_{l-1}
 //   A_l = sqrt((2l+3)/(2l+1)) (l+1)(2l+1) / sqrt(((l+1)^2-m^2)((l+1)^2-4))
 //   B_l = sqrt((l^2-m^2)(l^2-4))/(l(2l+1)) sqrt((2l+1)/(2l-1))   (0 at l = l0)
-//   entry {A_l, A_l B_l, A_l 2m/(l(l+1)), 0}
+// stored in monic form: with sλ_l = σ_l μ_l, σ_{l0} = σ_{l0+1} = 1, σ_{l+1} = A_l B_l σ_{l-1},
+//   μ_{l+1} = (A'_l x ± c'_l) μ_l - μ_{l-1},  A'_l = A_l σ_l/σ_{l+1},  c'_l = A_l (2m/(l(l+1))) σ_l/σ_{l+1}
+// (σ stays within [0.17, 1] up to lmax 4096).  Entry {A', c', σ_l, 0}.  One thread per m.
 __global__ void k_coef(int L, double4_32a *c64, float4 *c32)
 {
-    const int m = blockIdx.x;
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m > L) return;
     const long long mbase = (long long)m * (2 * L + 1 - m) / 2;
     const int l0 = m > 2 ? m : 2;
-    for (int l = m + threadIdx.x; l <= L; l += blockDim.x) {
-        double a = 0, b = 0, c = 0;
-        if (l >= l0) {
-            const double dl = l, mm = (double)m * m, lp1 = l + 1.0;
-            a = sqrt((2 * dl + 3) / (2 * dl + 1)) * lp1 * (2 * dl + 1) /
-                sqrt((lp1 * lp1 - mm) * (lp1 * lp1 - 4.0));
-            const double B = (l == l0) ? 0.0
-                                       : sqrt((dl * dl - mm) * (dl * dl - 4.0)) / (dl * (2 * dl + 1)) *
-                                             sqrt((2 * dl + 1) / (2 * dl - 1));
-            b = a * B;
-            c = a * 2.0 * m / (dl * (dl + 1));
-        }
-        c64[mbase + l] = make_double4_32a(a, b, c, 0.0);
-        c32[mbase + l] = make_float4((float)a, (float)b, (float)c, 0.f);
+    for (int l = m; l < l0 && l <= L; l++) {
+        c64[mbase + l] = make_double4_32a(0.0, 0.0, 0.0, 0.0);
+        c32[mbase + l] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    double sig_prev = 1.0, sig = 1.0;   // σ_{l-1}, σ_l
+    const double mm = (double)m * m;
+    for (int l = l0; l <= L; l++) {
+        const double dl = l, lp1 = l + 1.0;
+        const double A = sqrt((2 * dl + 3) / (2 * dl + 1)) * lp1 * (2 * dl + 1) /
+                         sqrt((lp1 * lp1 - mm) * (lp1 * lp1 - 4.0));
+        const double B = (l == l0) ? 0.0
+                                   : sqrt((dl * dl - mm) * (dl * dl - 4.0)) / (dl * (2 * dl + 1)) *
+                                         sqrt((2 * dl + 1) / (2 * dl - 1));
+        const double sig_next = (l == l0) ? 1.0 : A * B * sig_prev;
+        const double r = sig / sig_next;
+        const double a = A * r, c = A * 2.0 * m / (dl * (dl + 1)) * r;
+        c64[mbase + l] = make_double4_32a(a, c, sig, 0.0);
+        c32[mbase + l] = make_float4((float)a, (float)c, (float)sig, 0.f);
+        sig_prev = sig;
+        sig = sig_next;
     }
 }
 
@@ -384,7 +394,7 @@ static akra_status plan_build(akra_plan p)
     const int nthr = 256;
     k_geometry<<<(p->nring + nthr - 1) / nthr, nthr>>>(N, p->d_rings, p->d_units);
     AKRA_CUDA_TRY(cudaGetLastError());
-    k_coef<<<L + 1, 256>>>(L, p->d_coef64, p->d_coef32);
+    k_coef<<<(L + 1 + 127) / 128, 128>>>(L, p->d_coef64, p->d_coef32);
     AKRA_CUDA_TRY(cudaGetLastError());
     k_seed<<<(L + 1 + 127) / 128, 128>>>(L, p->d_seedC, p->d_D64, p->d_D32);
     AKRA_CUDA_TRY(cudaGetLastError());
