@@ -115,11 +115,14 @@ def make_inputs(rank, dev):
 
 
 def legendre_flops(desc, R=1):
-    """Algorithmic FP32 work of one Legendre launch over the active ring pairs: every
-    (l >= 2, m, pair) step does two monic spin recurrences (4 FMA) and 8 FMA of contraction
-    per RHS; flops = 2 x FMA."""
-    steps = desc["n_active_units"] * (desc["ntri"] - 3)
-    return steps * (4 + 8 * R) * 2, steps
+    """FP32 work of one Legendre launch over the active ring pairs: every (l, m, pair) step
+    does two monic spin recurrences (4 FMA) and 8 FMA of contraction per RHS; flops = 2 x FMA.
+    The steps counted are those the method needs: for each (m, pair) from where its harmonics
+    first exceed 2^-40 (the plan's start table) to lmax.  The full triangle (every l >= 2) is
+    returned as well."""
+    steps = desc["legendre_steps_f32"]
+    full = desc["n_active_units"] * (desc["ntri"] - 3)
+    return steps * (4 + 8 * R) * 2, steps, full
 
 
 def cpu_oracle_H_estimate(nside, lmax, target_s=15.0):
@@ -264,7 +267,7 @@ def main():
     # ---- per-stage kernel timing (CUDA events on this stream, kernels timed alone) ----
     st32 = A.akra_time_H_stages(plan, A.F32, 1, 5)
     st64 = A.akra_time_H_stages(plan, A.F64, 1, 2)
-    flops, steps = legendre_flops(desc)
+    flops, steps, full_steps = legendre_flops(desc)
     dom = "legendre_adjoint" if st32["legendre_adjoint"] >= st32["legendre_synth"] else "legendre_synth"
     achieved = flops / (st32[dom] * 1e-3) / 1e12
     peak = fp32_peak_tflops()
@@ -273,6 +276,7 @@ def main():
                 "traffic": None,
                 "peak_basis": "152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz (unit counts and maximum clock)",
                 "flops_per_launch": flops, "lm_pair_steps_per_launch": steps,
+                "lm_pair_steps_full_triangle": full_steps,
                 "stage_ms_fp32": st32, "stage_ms_fp64": st64}
 
     # ---- FP64 comparison (the plain FP64 GPU path) ----

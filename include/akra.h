@@ -80,7 +80,12 @@ typedef struct {
     double omega;                     /* pixel area 4π/npix folded into W = ω M N^-1 */
     size_t device_bytes;              /* device memory currently held by the plan */
     long long kernel_launches;        /* kernels this plan has launched so far (host count;
-                                         a captured CG iteration counts its 7 kernels) */
+                                         a captured CG iteration counts its 7-8 kernels) */
+    long long legendre_steps_f32;     /* (l, m, ring pair) steps of one FP32 Legendre pass over
+                                         the pairs H transforms, per RHS: each pair's recurrence
+                                         starts where its harmonics exceed 2^-40 (Sec. II B
+                                         recurrences; the terms below are negligible) */
+    long long legendre_steps_f64;     /* the same for FP64 (threshold 2^-90) */
 } akra_plan_desc;
 
 /* Create a plan for (nside, lmax): HEALPix ring tables, spin-2 recurrence tables, ring
@@ -227,10 +232,22 @@ akra_status akra_batch_describe(akra_batch batch, int *P, int *RG, long long *la
 /* Host-side wall-clock budget (seconds, > 0) for blocking solves; default 3600. */
 akra_status akra_set_timeout(double seconds);
 
-/* Pick the Legendre tile shape (units per thread, threads per block) for this plan,
- * precision and RHS count by timing the candidates on `stream`; the choice is cached in
- * the plan and used by every later call with the same (prec, R).  Blocking. */
+/* Pick the Legendre tile shapes for this plan, precision and RHS count by timing the
+ * candidates on `stream`: ring pairs per thread of the synthesis and, separately, of the
+ * adjoint, with a common number of RHS per block.  The choice is cached in the plan and used
+ * by every later call with the same (prec, R).  Blocking. */
 akra_status akra_autotune(akra_plan plan, akra_prec prec, int R, void *stream);
+
+/* Legendre tile shape used for (prec, R), prec AKRA_F64 or AKRA_F32: ring pairs per thread of
+ * the synthesis (*P) and of the adjoint (*PA), RHS per block (*RG) -- the autotuned or forced
+ * choice if there is one, else the default.  Errors: EINVAL. */
+akra_status akra_plan_get_shape(akra_plan plan, akra_prec prec, int R, int *P, int *PA, int *RG);
+
+/* Force the Legendre tile shape for (prec, R), replacing a default or autotuned choice (for
+ * reproducible timing, or to test every compiled shape).  Compiled shapes: (P, RG) and
+ * (PA, RG) in {(1,1), (2,1), (4,1), (1,2), (2,2), (1,4)}, and for AKRA_F32 also (8,1).
+ * The results do not depend on the shape beyond rounding order.  Errors: EINVAL. */
+akra_status akra_plan_set_shape(akra_plan plan, akra_prec prec, int R, int P, int PA, int RG);
 
 /* Time the four stages of one H application (Legendre synthesis, ring FFT x W x FFT,
  * Legendre adjoint, epilogue) with CUDA events on `stream`, averaged over `reps` runs after

@@ -42,7 +42,8 @@ class PlanDesc(ctypes.Structure):
                 ("n_active_units", ctypes.c_int),
                 ("lambda_", ctypes.c_double), ("lambda_eff", ctypes.c_double),
                 ("precond", ctypes.c_double), ("omega", ctypes.c_double),
-                ("device_bytes", ctypes.c_size_t), ("kernel_launches", ctypes.c_longlong)]
+                ("device_bytes", ctypes.c_size_t), ("kernel_launches", ctypes.c_longlong),
+                ("legendre_steps_f32", ctypes.c_longlong), ("legendre_steps_f64", ctypes.c_longlong)]
 
 
 EXPORTS = ["akra_plan_create", "akra_plan_destroy", "akra_last_error", "akra_version",
@@ -51,7 +52,8 @@ EXPORTS = ["akra_plan_create", "akra_plan_destroy", "akra_last_error", "akra_ver
            "akra_cg_solve", "akra_cg_solve_b", "akra_set_timeout", "akra_autotune",
            "akra_time_H_stages", "akra_synth_spin2_static", "akra_cg_solve_adjoint",
            "akra_weight_grad", "akra_batch_create", "akra_batch_destroy", "akra_batch_autotune",
-           "akra_batch_apply_H", "akra_batch_cg_solve", "akra_batch_describe"]
+           "akra_batch_apply_H", "akra_batch_cg_solve", "akra_batch_describe",
+           "akra_plan_get_shape", "akra_plan_set_shape"]
 
 _lib_handle = None
 
@@ -88,6 +90,8 @@ def load(build_if_missing: bool = False):
         "akra_cg_solve_b": ([vp, i, vp, vp, i, d, i, ctypes.POINTER(CgInfo), vp], i),
         "akra_set_timeout": ([d], i),
         "akra_autotune": ([vp, i, i, vp], i),
+        "akra_plan_get_shape": ([vp, i, i, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)], i),
+        "akra_plan_set_shape": ([vp, i, i, i, i, i], i),
         "akra_time_H_stages": ([vp, i, i, i, vp, ctypes.POINTER(ctypes.c_double)], i),
         "akra_synth_spin2_static": ([vp, i, vp, vp, i, vp], i),
         "akra_cg_solve_adjoint": ([vp, i, vp, vp, i, d, i, ctypes.POINTER(CgInfo), vp], i),
@@ -308,6 +312,20 @@ def akra_set_timeout(seconds: float):
 
 def akra_autotune(plan: Plan, prec: int, R: int = 1, stream=None):
     _check(load().akra_autotune(plan.handle, prec, R, _stream(stream)))
+
+
+def akra_plan_get_shape(plan: Plan, prec: int, R: int = 1) -> dict:
+    """Legendre tile shape used for (prec, R): synthesis / adjoint ring pairs per thread, RHS
+    per block."""
+    P, PA, RG = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(load().akra_plan_get_shape(plan.handle, prec, R, ctypes.byref(P), ctypes.byref(PA),
+                                      ctypes.byref(RG)))
+    return {"P": P.value, "PA": PA.value, "RG": RG.value}
+
+
+def akra_plan_set_shape(plan: Plan, prec: int, R: int, P: int, PA: int, RG: int):
+    """Force the Legendre tile shape for (prec, R)."""
+    _check(load().akra_plan_set_shape(plan.handle, prec, R, P, PA, RG))
 
 
 def akra_time_H_stages(plan: Plan, prec: int, R: int = 1, reps: int = 3, stream=None) -> dict:

@@ -343,7 +343,7 @@ static akra_status cg_graph(akra_plan p, int R, CgBufs &b, cudaGraphExec_t *out)
     // reserve the operator workspaces before capture (no allocation may happen inside)
     const LegShape s = leg_shape(p, PrecIdx<T>::v == 0 ? AKRA_F64 : AKRA_F32, R);
     AKRA_TRY(ws_reserve(p, p->phi, (size_t)R * p->nring * (2 * (size_t)p->lmax + 1) * sizeof(cx_t<T>)));
-    const int nch = (p->n_active_units + s.NT * s.P - 1) / (s.NT * s.P);
+    const int nch = legendre_chunks(p->n_active_units, s);
     AKRA_TRY(ws_reserve(p, p->partial, (size_t)nch * R * p->ntri * 4 * sizeof(T)));
     AKRA_TRY(cg_reserve(p, R, b));   // pointers are stable now (nothing grows below)
     void **v = vecs<T>(b);

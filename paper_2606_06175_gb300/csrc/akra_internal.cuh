@@ -50,6 +50,10 @@ template <typename T> using v4_t = typename V4t<T>::type;
 
 // scaled-recurrence parameters: a value v with exponent index e < 0 stands for
 // v * 2^(Q e); a rescale by 2^-Q happens when |v| > 2^(Q/2); contributions start when e == 0
+// recurrences start at grid points l0 + kStartGrid j (a multiple of every l-tile width)
+constexpr int kStartGrid = 64;
+constexpr int kNeverLive = 0x7fffffff;   // start index of a pair whose harmonics stay negligible
+
 template <typename T> struct Scale;
 template <> struct Scale<float> {
     static constexpr int Q = 64;
@@ -91,9 +95,11 @@ constexpr int kMaxNside = 2048;
 
 // Legendre tile shape (chosen per precision and RHS count; see autotune)
 struct LegShape {
-    int P;                 // ring pairs per thread
+    int P;                 // ring pairs per thread (synthesis)
     int NT;                // threads per block
     int RG;                // RHS handled together by one block
+    int PA = 0;            // ring pairs per thread of the adjoint (0: same as P)
+    int adjP() const { return PA > 0 ? PA : P; }
 };
 
 // arguments of one Legendre kernel instance (one plan; the batched launches hold an array)
@@ -104,7 +110,8 @@ struct LegArgs {
     const int *units;                 // ring pairs to process
     const UnitInfo *uinfo;
     const v4_t<T> *coef;              // recurrence coefficients
-    const v4_t<T> *seeds;             // seeds per (m, ring pair)
+    const v4_t<T> *seeds;             // start states per (m, ring pair)
+    const int2 *start;                // their grid points and exponent indices
     const T *fl;                      // synthesis: per-l factor (nullptr = -1)
     const cx_t<T> *alm;               // synthesis input  [R][2][ntri]
     cx_t<T> *phi;                     // synthesis output [R][nring][2L+1]
@@ -154,8 +161,16 @@ struct akra_plan_s {
     double4_32a *d_coef64 = nullptr;            // [ntri] {A, A B, A 2m/(l(l+1)), 0}
     float4 *d_coef32 = nullptr;
     double *d_seedC = nullptr;               // [lmax + 1] log2 seed prefactor per m
-    float4 *d_seed32 = nullptr;              // [(lmax+1) nunit] {2λ_l0, (-2)λ_l0, e bits, 0} (FP64-computed)
-    double4_32a *d_seed64 = nullptr;         // [(lmax+1) nunit] {2λ_l0, (-2)λ_l0, e, 0}
+    // start states of the recurrences per (m, ring pair), computed in FP64 at plan time:
+    // {μ+_g, μ-_g, μ+_{g-1}, μ-_{g-1}} at the grid point g (l0 + 64 j) where the pair's
+    // harmonics first exceed the precision's threshold, scaled by 2^(-Q e)
+    float4 *d_seed32 = nullptr;              // [(lmax+1) nunit]
+    double4_32a *d_seed64 = nullptr;         // [(lmax+1) nunit]
+    int2 *d_start32 = nullptr;               // [(lmax+1) nunit] {g (kNeverLive: none), e}
+    int2 *d_start64 = nullptr;
+    unsigned long long *d_steps = nullptr;   // [2 nunit] Σ_m (lmax + 1 - g) per ring pair, FP32 / FP64
+    std::vector<unsigned long long> steps32, steps64;   // host copies
+    std::vector<int> h_active_units;         // host copy of the active pairs
     double *d_D64 = nullptr;                 // [lmax + 1] KS kernel D_l
     float *d_D32 = nullptr;
     double2 *d_tw64 = nullptr;               // ring twiddles e^{iπ t/n}
@@ -165,6 +180,12 @@ struct akra_plan_s {
     long long *d_fft32_off = nullptr;        // [nside + 1] offset of the chirp spectrum
     float2 *d_fft32_tw2 = nullptr;           // e^{-2πi t/MMAX}
     float2 *d_fft32_bhat = nullptr;          // chirp spectra (DIF output order)
+    std::vector<int> fft32_M_host;           // [nside + 1] host copy of d_fft32_M
+    int fft32_msmall = 0;                    // largest M below fft32_mmax (0: a single class)
+    int *d_fft32_rings_all = nullptr;        // [nring] all rings, those with M <= msmall first
+    int fft32_nsmall_all = 0;
+    int *d_fft32_rings_act = nullptr;        // [nring] active rings in the same order
+    int fft32_nsmall_act = 0;
     int *d_all_rings = nullptr;              // [nring] 0..nring-1
     int *d_all_units = nullptr;              // [nunit] 0..nunit-1
 
@@ -230,6 +251,7 @@ akra_status ring_fft(akra_plan p, FftMode mode, void *phi, const void *map_in, v
                      bool weighted, int R, const int *rings, int nrings, cudaStream_t st);
 // FP32 ring FFT with Bluestein for non-power-of-two rings (akra_ringfft32.cu)
 akra_status ring_fft32_build(akra_plan p);
+akra_status ring_fft32_order(akra_plan p, const std::vector<int> &rings, int *d_out, int *nsmall);
 Fft32Args fft32_args(akra_plan p, bool weighted, const int *rings);
 akra_status ring_fft32(akra_plan p, FftMode mode, void *phi, const void *map_in, void *map_out,
                        bool weighted, int R, const int *rings, int nrings, cudaStream_t st);

@@ -14,6 +14,8 @@
 // rings through even/odd (l+m) accumulators.  Seeds at l0 = max(m,2) are formed in FP64 in
 // log2 form; the recurrence carries a per-unit exponent index e (value = v 2^(Q e)) and
 // contributes only once e == 0.
+#include <type_traits>
+
 #include "akra_legendre_impl.cuh"
 
 namespace akra {
@@ -70,6 +72,9 @@ template <> const double4_32a *coef_ptr<double>(akra_plan p) { return p->d_coef6
 template <typename T> const v4_t<T> *seed_ptr(akra_plan p);
 template <> const float4 *seed_ptr<float>(akra_plan p) { return p->d_seed32; }
 template <> const double4_32a *seed_ptr<double>(akra_plan p) { return p->d_seed64; }
+template <typename T> static const int2 *start_ptr(akra_plan p);
+template <> const int2 *start_ptr<float>(akra_plan p) { return p->d_start32; }
+template <> const int2 *start_ptr<double>(akra_plan p) { return p->d_start64; }
 template <typename T> const T *D_ptr(akra_plan p);
 template <> const float *D_ptr<float>(akra_plan p) { return p->d_D32; }
 template <> const double *D_ptr<double>(akra_plan p) { return p->d_D64; }
@@ -89,6 +94,7 @@ LegArgs<T> leg_args(akra_plan p, const LegShape &s, LegMode mode, const int *uni
     a.uinfo = p->d_units;
     a.coef = coef_ptr<T>(p);
     a.seeds = seed_ptr<T>(p);
+    a.start = start_ptr<T>(p);
     a.fl = mode == LegMode::KS ? D_ptr<T>(p) : nullptr;
     a.ring_active = units == p->d_all_units ? nullptr : p->d_ring_active;
     a.skip = p->cur_skip;
@@ -132,6 +138,7 @@ akra_status legendre_synth(akra_plan p, const LegShape &s, LegMode mode, const v
         return AKRA_OK;                                                                     \
     }
     AKRA_S(1, 1) AKRA_S(2, 1) AKRA_S(4, 1) AKRA_S(1, 2) AKRA_S(2, 2) AKRA_S(1, 4)
+    if constexpr (std::is_same<T, float>::value) { AKRA_S(8, 1) }
 #undef AKRA_S
     set_error("no synthesis kernel for P=%d RG=%d", s.P, s.RG);
     return AKRA_EINVAL;
@@ -144,16 +151,18 @@ akra_status legendre_adjoint(akra_plan p, const LegShape &s, const void *phi, vo
 {
     *nchunks_out = 0;
     if (nunits <= 0) return AKRA_OK;
+    const int pa = s.adjP();
 #define AKRA_A(PP, RR)                                                                      \
-    if (s.P == PP && s.RG == RR) {                                                          \
+    if (pa == PP && s.RG == RR) {                                                           \
         *nchunks_out = launch_adjoint<T, PP, RR, 128>(p, phi, partial, R, units, nunits, st); \
         AKRA_CUDA_TRY(cudaGetLastError());                                                  \
         p->launches++;                                                                      \
         return AKRA_OK;                                                                     \
     }
     AKRA_A(1, 1) AKRA_A(2, 1) AKRA_A(4, 1) AKRA_A(1, 2) AKRA_A(2, 2) AKRA_A(1, 4)
+    if constexpr (std::is_same<T, float>::value) { AKRA_A(8, 1) }
 #undef AKRA_A
-    set_error("no adjoint kernel for P=%d RG=%d", s.P, s.RG);
+    set_error("no adjoint kernel for P=%d RG=%d", pa, s.RG);
     return AKRA_EINVAL;
 }
 
@@ -171,7 +180,12 @@ akra_status adjoint_epilogue(akra_plan p, LegMode mode, const void *partial, int
     return AKRA_OK;
 }
 
-int legendre_chunks(int nunits, const LegShape &s) { return (nunits + s.NT * s.P - 1) / (s.NT * s.P); }
+// chunks of the adjoint (its partial sums are laid out per chunk)
+int legendre_chunks(int nunits, const LegShape &s)
+{
+    const int per = s.NT * s.adjP();
+    return (nunits + per - 1) / per;
+}
 
 template LegArgs<float> leg_args<float>(akra_plan, const LegShape &, LegMode, const int *, int, int);
 template LegArgs<double> leg_args<double>(akra_plan, const LegShape &, LegMode, const int *, int, int);

@@ -10,21 +10,38 @@ constexpr int TL = 64;  // l-steps staged in shared memory per tile (even)
 
 // seeds 2λ_{l0 m} (vp) and (-2)λ_{l0 m} (vm) with their shared exponent index e, from the
 // plan's table (computed in FP64 at plan creation)
-__device__ __forceinline__ void load_seed(const float4 *__restrict__ t, size_t i, float &vp,
-                                          float &vm, int &e)
+// smallest start grid point over the block (kNeverLive if no pair of the block ever starts)
+template <int NT>
+__device__ __forceinline__ int block_min_start(int v)
 {
-    const float4 s = t[i];
-    vp = s.x;
-    vm = s.y;
-    e = __float_as_int(s.z);
+    __shared__ int s_first;
+    if (threadIdx.x == 0) s_first = kNeverLive;
+    __syncthreads();
+    v = __reduce_min_sync(0xffffffffu, v);
+    if ((threadIdx.x & 31) == 0) atomicMin(&s_first, v);
+    __syncthreads();
+    return s_first;
 }
-__device__ __forceinline__ void load_seed(const double4_32a *__restrict__ t, size_t i, double &vp,
-                                          double &vm, int &e)
+
+// at an l-tile that begins at lt (a grid point, even offset from l0, so that vp / vm hold the
+// current values): load the state of every pair whose recurrence starts here
+template <typename V4, typename T, int P>
+__device__ __forceinline__ void start_pairs(const V4 *__restrict__ seeds, const int2 *__restrict__ start,
+                                            size_t base, int lt, const int (&uid)[P],
+                                            const int (&gs)[P], T (&vp)[P], T (&vm)[P],
+                                            T (&vpo)[P], T (&vmo)[P], int (&e)[P])
 {
-    const double4_32a s = t[i];
-    vp = s.x;
-    vm = s.y;
-    e = (int)s.z;
+#pragma unroll
+    for (int k = 0; k < P; k++) {
+        if (gs[k] == lt) {
+            const V4 s = seeds[base + uid[k]];
+            vp[k] = s.x;
+            vm[k] = s.y;
+            vpo[k] = s.z;
+            vmo[k] = s.w;
+            e[k] = start[base + uid[k]].y;
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -42,6 +59,7 @@ __device__ __forceinline__ void leg_synth_item(const LegArgs<T> &a, const int m,
     const UnitInfo *__restrict__ uinfo = a.uinfo;
     const v4_t<T> *__restrict__ coef = a.coef;
     const v4_t<T> *__restrict__ seeds = a.seeds;
+    const int2 *__restrict__ start = a.start;
     const unsigned char *__restrict__ ring_active = a.ring_active;
     const T *__restrict__ fl = a.fl;
     const cx_t<T> *__restrict__ alm = a.alm;
@@ -50,28 +68,33 @@ __device__ __forceinline__ void leg_synth_item(const LegArgs<T> &a, const int m,
     const int tid = threadIdx.x;
     const long long mbase = (long long)m * (2 * L + 1 - m) / 2;
 
+    // every pair's recurrence starts at its grid point gs (state loaded there); until then
+    // its state is zero, which the recurrence keeps and the contraction ignores
     T x[P], vp[P], vm[P], vpo[P], vmo[P];
-    int e[P], uid[P];
+    int e[P], uid[P], gs[P];
     T acc[P][RG][16];
+    int my_first = kNeverLive;
 #pragma unroll
     for (int k = 0; k < P; k++) {
         const int iu = (chunk * P + k) * NT + tid;
         uid[k] = iu < nunits ? (units ? units[iu] : iu) : -1;
         x[k] = 0;
-        vp[k] = vm[k] = 0;
+        vp[k] = vm[k] = vpo[k] = vmo[k] = 0;
         e[k] = 0;
+        gs[k] = kNeverLive;
         if (uid[k] >= 0) {
             x[k] = (T)uinfo[uid[k]].x;
-            load_seed(seeds, (size_t)m * nunit_all + uid[k], vp[k], vm[k], e[k]);
+            gs[k] = start[(size_t)m * nunit_all + uid[k]].x;
         }
-        vpo[k] = vmo[k] = 0;
+        my_first = min(my_first, gs[k]);
 #pragma unroll
         for (int r = 0; r < RG; r++)
 #pragma unroll
             for (int j = 0; j < 16; j++) acc[k][r][j] = 0;
     }
+    const int l_first = block_min_start<NT>(my_first);
 
-    for (int lt = l0; lt <= L; lt += TL) {
+    for (int lt = l_first; lt <= L; lt += TL) {
         __syncthreads();
         for (int i = tid; i < TL; i += NT) {
             const int l = lt + i;
@@ -94,6 +117,7 @@ __device__ __forceinline__ void leg_synth_item(const LegArgs<T> &a, const int m,
         }
         __syncthreads();
         const int nl = min(TL, L - lt + 1);
+        start_pairs(seeds, start, (size_t)m * nunit_all, lt, uid, gs, vp, vm, vpo, vmo, e);
         bool live = true;
 #pragma unroll
         for (int k = 0; k < P; k++) live &= (e[k] == 0);
@@ -113,8 +137,8 @@ __device__ __forceinline__ void leg_synth_item(const LegArgs<T> &a, const int m,
         }                                                                                   \
         if (any) {                                                                          \
             _Pragma("unroll") for (int k = 0; k < P; k++) {                                 \
-                const T lp = (GATED && e[k] != 0) ? T(0) : vp[k];                           \
-                const T lm = (GATED && e[k] != 0) ? T(0) : vm[k];                           \
+                const T lp = (GATED && e[k] != 0) ? T(0) : ((S) == 0 ? vp[k] : vpo[k]);     \
+                const T lm = (GATED && e[k] != 0) ? T(0) : ((S) == 0 ? vm[k] : vmo[k]);     \
                 _Pragma("unroll") for (int r = 0; r < RG; r++) {                            \
                     const V4 a = s_alm[I][r];                                               \
                     T *ac = &acc[k][r][(S) * 8];                                            \
@@ -132,14 +156,12 @@ __device__ __forceinline__ void leg_synth_item(const LegArgs<T> &a, const int m,
         _Pragma("unroll") for (int k = 0; k < P; k++) {                                     \
             const T t1 = fma(c.x, x[k], c.y);                                               \
             const T t2 = fma(c.x, x[k], -c.y);                                              \
-            const T np = fma(t1, vp[k], -vpo[k]);                                           \
-            const T nm = fma(t2, vm[k], -vmo[k]);                                           \
-            vpo[k] = vp[k];                                                                 \
-            vmo[k] = vm[k];                                                                 \
-            vp[k] = np;                                                                     \
-            vm[k] = nm;                                                                     \
-            if (GATED && e[k] < 0 &&                                                        \
-                (fabs(vp[k]) > Scale<T>::hi() || fabs(vm[k]) > Scale<T>::hi())) {           \
+            /* the new value overwrites the older register; the roles swap every step */    \
+            T &cp_ = (S) == 0 ? vp[k] : vpo[k], &op_ = (S) == 0 ? vpo[k] : vp[k];           \
+            T &cm_ = (S) == 0 ? vm[k] : vmo[k], &om_ = (S) == 0 ? vmo[k] : vm[k];           \
+            op_ = fma(t1, cp_, -op_);                                                       \
+            om_ = fma(t2, cm_, -om_);                                                       \
+            if (GATED && e[k] < 0 && (fabs(op_) > Scale<T>::hi() || fabs(om_) > Scale<T>::hi())) { \
                 vp[k] *= Scale<T>::inv();                                                   \
                 vm[k] *= Scale<T>::inv();                                                   \
                 vpo[k] *= Scale<T>::inv();                                                  \
@@ -266,6 +288,7 @@ __device__ __forceinline__ void leg_adjoint_item(
     const UnitInfo *__restrict__ uinfo = a.uinfo;
     const v4_t<T> *__restrict__ coef = a.coef;
     const v4_t<T> *__restrict__ seeds = a.seeds;
+    const int2 *__restrict__ start = a.start;
     const unsigned char *__restrict__ ring_active = a.ring_active;
     const cx_t<T> *__restrict__ phi = a.phi_in;
     T *__restrict__ partial = a.partial;
@@ -277,7 +300,8 @@ __device__ __forceinline__ void leg_adjoint_item(
     const bool swap = ((l0 + m) & 1) != 0;
 
     T x[P], vp[P], vm[P], vpo[P], vmo[P];
-    int e[P];
+    int e[P], uid[P], gs[P];
+    int my_first = kNeverLive;
     // per unit and RHS, the partners of 2λ and (-2)λ in slot A (l - l0 even):
     //   E += 2λ X1 + (-2)λ X2,  B += 2λ X3 + (-2)λ X4;   slot B: E += 2λ X3 - (-2)λ X4,
     //   B += 2λ X1 - (-2)λ X2   (X = U1..U4, or U3, -U4, U1, -U2 when l0+m is odd)
@@ -286,16 +310,19 @@ __device__ __forceinline__ void leg_adjoint_item(
     for (int k = 0; k < P; k++) {
         const int iu = (chunk * P + k) * NT + tid;
         const int u = iu < nunits ? (units ? units[iu] : iu) : -1;
+        uid[k] = u;
         x[k] = 0;
         vp[k] = vm[k] = vpo[k] = vmo[k] = 0;
         e[k] = 0;
+        gs[k] = kNeverLive;
         UnitInfo ui;
         ui.ring_n = ui.ring_s = -1;
         if (u >= 0) {
             ui = uinfo[u];
             x[k] = (T)ui.x;
-            load_seed(seeds, (size_t)m * nunit_all + u, vp[k], vm[k], e[k]);
+            gs[k] = start[(size_t)m * nunit_all + u].x;
         }
+        my_first = min(my_first, gs[k]);
 #pragma unroll
         for (int rr = 0; rr < RG; rr++) {
             const int r = r0 + rr;
@@ -324,7 +351,14 @@ __device__ __forceinline__ void leg_adjoint_item(
     }
 
     T (*tr)[S] = s_tr[warp];
-    for (int lt = l0; lt <= L; lt += TLA) {
+    const int l_first = block_min_start<NT>(my_first);
+    // the l below the first start get zero partial sums
+    for (int i = tid; i < (min(l_first, L + 1) - l0) * RG * 4; i += NT) {
+        const int step = i / (RG * 4), rem = i - step * RG * 4, rr = rem >> 2, q = rem & 3;
+        const int r = r0 + rr;
+        if (r < R) partial[(((size_t)chunk * R + r) * ntri + mbase + l0 + step) * 4 + q] = T(0);
+    }
+    for (int lt = l_first; lt <= L; lt += TLA) {
         __syncthreads();
         for (int i = tid; i < TLA; i += NT) {
             const int l = lt + i;
@@ -332,6 +366,7 @@ __device__ __forceinline__ void leg_adjoint_item(
         }
         __syncthreads();
         const int nl = min(TLA, L - lt + 1);
+        start_pairs(seeds, start, (size_t)m * nunit_all, lt, uid, gs, vp, vm, vpo, vmo, e);
         bool live = true;
 #pragma unroll
         for (int k = 0; k < P; k++) live &= (e[k] == 0);
@@ -356,8 +391,8 @@ __device__ __forceinline__ void leg_adjoint_item(
             }                                                                                   \
             if (any) {                                                                          \
                 _Pragma("unroll") for (int k = 0; k < P; k++) {                                 \
-                    const T lp = (GATED && e[k] != 0) ? T(0) : vp[k];                           \
-                    const T lm0 = (GATED && e[k] != 0) ? T(0) : vm[k];                          \
+                    const T lp = (GATED && e[k] != 0) ? T(0) : (slotA ? vp[k] : vpo[k]);        \
+                    const T lm0 = (GATED && e[k] != 0) ? T(0) : (slotA ? vm[k] : vmo[k]);       \
                     const T lm = slotA ? lm0 : -lm0;                                            \
                     _Pragma("unroll") for (int rr = 0; rr < RG; rr++) {                         \
                         const C2 eP = slotA ? X1[k][rr] : X3[k][rr];                            \
@@ -375,14 +410,13 @@ __device__ __forceinline__ void leg_adjoint_item(
             _Pragma("unroll") for (int k = 0; k < P; k++) {                                     \
                 const T t1 = fma(c.x, x[k], c.y);                                               \
                 const T t2 = fma(c.x, x[k], -c.y);                                              \
-                const T np = fma(t1, vp[k], -vpo[k]);                                           \
-                const T nm = fma(t2, vm[k], -vmo[k]);                                           \
-                vpo[k] = vp[k];                                                                 \
-                vmo[k] = vm[k];                                                                 \
-                vp[k] = np;                                                                     \
-                vm[k] = nm;                                                                     \
+                /* the new value overwrites the older register (K is even) */               \
+                T &cp_ = slotA ? vp[k] : vpo[k], &op_ = slotA ? vpo[k] : vp[k];                 \
+                T &cm_ = slotA ? vm[k] : vmo[k], &om_ = slotA ? vmo[k] : vm[k];                 \
+                op_ = fma(t1, cp_, -op_);                                                       \
+                om_ = fma(t2, cm_, -om_);                                                       \
                 if (GATED && e[k] < 0 &&                                                        \
-                    (fabs(vp[k]) > Scale<T>::hi() || fabs(vm[k]) > Scale<T>::hi())) {           \
+                    (fabs(op_) > Scale<T>::hi() || fabs(om_) > Scale<T>::hi())) {               \
                     vp[k] *= Scale<T>::inv();                                                   \
                     vm[k] *= Scale<T>::inv();                                                   \
                     vpo[k] *= Scale<T>::inv();                                                  \

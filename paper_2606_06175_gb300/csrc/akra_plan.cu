@@ -6,6 +6,8 @@
 #include <algorithm>
 #include <mutex>
 
+#include <type_traits>
+
 #include "akra_internal.cuh"
 
 namespace akra {
@@ -149,18 +151,85 @@ __device__ void seed_values(int m, double Cm, double ls, double lc, int Q, doubl
     e = ee;
 }
 
-__global__ void k_seeds(int L, int nunit, const double *seedC, const UnitInfo *units, float4 *s32,
-                        double4_32a *s64)
+// Start states of the recurrences for every (m, ring pair).  The FP64 monic recurrence runs
+// from the seed at l0 (exponent index with Q = 600) until the larger of |2λ_l|, |(-2)λ_l|
+// first exceeds 2^-90 (FP64 kernels) and 2^-40 (FP32 kernels); below that the pair's
+// contributions are negligible at the precision's rounding level.  Each precision's start is
+// the last grid point g = l0 + 64 j at or before that l, with the state (μ_g, μ_{g-1}) of both
+// spins re-scaled to the precision's exponent index (Q = 64 for FP32).  Pairs that stay below
+// the threshold up to lmax get g = kNeverLive.  Also accumulates per pair the steps
+// Σ_m (lmax + 1 - g) that the kernels take.
+__global__ void k_start_states(int L, int nunit, const double *seedC, const UnitInfo *units,
+                               const double4_32a *coef, float4 *s32, double4_32a *s64,
+                               int2 *g32, int2 *g64, unsigned long long *steps)
 {
-    const int m = blockIdx.x;
-    for (int u = threadIdx.x; u < nunit; u += blockDim.x) {
-        const UnitInfo ui = units[u];
-        double vp, vm;
-        int e;
-        seed_values(m, seedC[m], ui.ls, ui.lc, Scale<float>::Q, vp, vm, e);
-        s32[(size_t)m * nunit + u] = make_float4((float)vp, (float)vm, __int_as_float(e), 0.f);
-        seed_values(m, seedC[m], ui.ls, ui.lc, Scale<double>::Q, vp, vm, e);
-        s64[(size_t)m * nunit + u] = make_double4_32a(vp, vm, (double)e, 0.0);
+    const int m = blockIdx.y;
+    const int u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= nunit) return;
+    const UnitInfo ui = units[u];
+    const int l0 = m > 2 ? m : 2;
+    const long long mbase = (long long)m * (2 * L + 1 - m) / 2;
+    const size_t o = (size_t)m * nunit + u;
+    const double x = ui.x;
+    double vp, vm, vpo = 0, vmo = 0;
+    int e;
+    seed_values(m, seedC[m], ui.ls, ui.lc, Scale<double>::Q, vp, vm, e);
+    double gp = vp, gm = vm, gpo = 0, gmo = 0;
+    int ge = e, gl = l0;
+    bool have64 = false;
+    const double thr64 = 0x1p-90, thr32 = 0x1p-40;
+    int l = l0;
+    for (; l <= L; l++) {
+        if (((l - l0) & (kStartGrid - 1)) == 0) {
+            gp = vp;
+            gm = vm;
+            gpo = vpo;
+            gmo = vmo;
+            ge = e;
+            gl = l;
+        }
+        const double4_32a c = coef[mbase + l];
+        // |λ| = σ |μ| 2^(600 e); below 2^-300 while e < 0
+        const double mag = e == 0 ? fmax(fabs(vp), fabs(vm)) * c.z : 0.0;
+        if (!have64 && mag > thr64) {
+            s64[o] = make_double4_32a(gp, gm, gpo, gmo);
+            g64[o] = make_int2(gl, ge);
+            atomicAdd(&steps[nunit + u], (unsigned long long)(L + 1 - gl));
+            have64 = true;
+        }
+        if (mag > thr32) {
+            // FP32 exponent index: the largest of the four values in [2^-32, 2^32)
+            const double mx = fmax(fmax(fabs(gp), fabs(gm)), fmax(fabs(gpo), fabs(gmo)));
+            int e32 = (int)floor((log2(mx) + (double)Scale<double>::Q * ge + 32.0) / 64.0);
+            if (e32 > 0) e32 = 0;
+            const int sh = Scale<double>::Q * ge - Scale<float>::Q * e32;
+            s32[o] = make_float4((float)ldexp(gp, sh), (float)ldexp(gm, sh), (float)ldexp(gpo, sh),
+                                 (float)ldexp(gmo, sh));
+            g32[o] = make_int2(gl, e32);
+            atomicAdd(&steps[u], (unsigned long long)(L + 1 - gl));
+            break;
+        }
+        const double np = fma(fma(c.x, x, c.y), vp, -vpo);
+        const double nm = fma(fma(c.x, x, -c.y), vm, -vmo);
+        vpo = vp;
+        vmo = vm;
+        vp = np;
+        vm = nm;
+        if (e < 0 && (fabs(vp) > Scale<double>::hi() || fabs(vm) > Scale<double>::hi())) {
+            vp *= Scale<double>::inv();
+            vm *= Scale<double>::inv();
+            vpo *= Scale<double>::inv();
+            vmo *= Scale<double>::inv();
+            e++;
+        }
+    }
+    if (l > L) {
+        s32[o] = make_float4(0.f, 0.f, 0.f, 0.f);
+        g32[o] = make_int2(kNeverLive, 0);
+        if (!have64) {
+            s64[o] = make_double4_32a(0.0, 0.0, 0.0, 0.0);
+            g64[o] = make_int2(kNeverLive, 0);
+        }
     }
 }
 
@@ -375,6 +444,9 @@ static akra_status plan_build(akra_plan p)
     AKRA_TRY(dev_alloc(p, &p->d_D64, sizeof(double) * (L + 1)));
     AKRA_TRY(dev_alloc(p, &p->d_seed32, sizeof(float4) * (size_t)(L + 1) * p->nunit));
     AKRA_TRY(dev_alloc(p, &p->d_seed64, sizeof(double4_32a) * (size_t)(L + 1) * p->nunit));
+    AKRA_TRY(dev_alloc(p, &p->d_start32, sizeof(int2) * (size_t)(L + 1) * p->nunit));
+    AKRA_TRY(dev_alloc(p, &p->d_start64, sizeof(int2) * (size_t)(L + 1) * p->nunit));
+    AKRA_TRY(dev_alloc(p, &p->d_steps, sizeof(unsigned long long) * 2 * p->nunit));
     AKRA_TRY(dev_alloc(p, &p->d_D32, sizeof(float) * (L + 1)));
     const size_t ntw = 4ull * N * (N + 1);
     AKRA_TRY(dev_alloc(p, &p->d_tw64, sizeof(double2) * ntw));
@@ -398,8 +470,17 @@ static akra_status plan_build(akra_plan p)
     AKRA_CUDA_TRY(cudaGetLastError());
     k_seed<<<(L + 1 + 127) / 128, 128>>>(L, p->d_seedC, p->d_D64, p->d_D32);
     AKRA_CUDA_TRY(cudaGetLastError());
-    k_seeds<<<L + 1, 256>>>(L, p->nunit, p->d_seedC, p->d_units, p->d_seed32, p->d_seed64);
+    AKRA_CUDA_TRY(cudaMemset(p->d_steps, 0, sizeof(unsigned long long) * 2 * p->nunit));
+    k_start_states<<<dim3((p->nunit + 127) / 128, L + 1), 128>>>(
+        L, p->nunit, p->d_seedC, p->d_units, p->d_coef64, p->d_seed32, p->d_seed64, p->d_start32,
+        p->d_start64, p->d_steps);
     AKRA_CUDA_TRY(cudaGetLastError());
+    p->steps32.assign(p->nunit, 0);
+    p->steps64.assign(p->nunit, 0);
+    AKRA_CUDA_TRY(cudaMemcpy(p->steps32.data(), p->d_steps, sizeof(unsigned long long) * p->nunit,
+                             cudaMemcpyDeviceToHost));
+    AKRA_CUDA_TRY(cudaMemcpy(p->steps64.data(), p->d_steps + p->nunit,
+                             sizeof(unsigned long long) * p->nunit, cudaMemcpyDeviceToHost));
     k_twiddles<<<dim3(4, N), 256>>>(N, p->d_tw64, p->d_tw32);
     AKRA_CUDA_TRY(cudaGetLastError());
     k_iota<<<(p->nring + 255) / 256, 256>>>(p->nring, p->d_all_rings);
@@ -463,7 +544,9 @@ extern "C" void akra_plan_destroy(akra_plan p)
                     p->d_D64, p->d_D32, p->d_tw64, p->d_tw32, p->d_all_rings, p->d_all_units,
                     p->d_active_rings, p->d_active_units, p->d_ring_active, p->d_W64, p->d_W32,
                     p->phi.ptr, p->partial.ptr, p->cg.ptr, p->red.ptr, p->d_fft32_M,
-                    p->d_fft32_off, p->d_fft32_tw2, p->d_fft32_bhat, p->d_seed32, p->d_seed64};
+                    p->d_fft32_off, p->d_fft32_tw2, p->d_fft32_bhat, p->d_seed32, p->d_seed64,
+                    p->d_start32, p->d_start64, p->d_steps,
+                    p->d_fft32_rings_all, p->d_fft32_rings_act};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     if (p->stream) cudaStreamDestroy(p->stream);
@@ -493,6 +576,20 @@ extern "C" akra_status akra_plan_describe(akra_plan p, akra_plan_desc *out)
     out->omega = p->omega;
     out->device_bytes = plan_device_bytes(p);
     out->kernel_launches = p->launches;
+    long long s32 = 0, s64 = 0;
+    if (p->has_weights) {
+        for (int u : p->h_active_units) {
+            s32 += (long long)p->steps32[u];
+            s64 += (long long)p->steps64[u];
+        }
+    } else {
+        for (int u = 0; u < p->nunit; u++) {
+            s32 += (long long)p->steps32[u];
+            s64 += (long long)p->steps64[u];
+        }
+    }
+    out->legendre_steps_f32 = s32;
+    out->legendre_steps_f64 = s64;
     return AKRA_OK;
 }
 
@@ -553,12 +650,14 @@ extern "C" akra_status akra_plan_set_weights(akra_plan p, const double *d_ninv, 
                                  cudaMemcpyHostToDevice));
     p->n_active_rings = (int)rings.size();
     p->n_active_units = (int)units.size();
+    p->h_active_units = units;
     p->lambda = lambda;
     p->lambda_eff = cnt > 0 ? lambda * sum / cnt : 0.0;
     p->precond = 1.0 / (sum / (double)p->npix + p->lambda_eff);
     if (!std::isfinite(p->precond)) p->precond = 1.0;
     p->has_weights = true;
-    return AKRA_OK;
+    p->ws_gen++;   // captured CG iterations hold the previous active lists and λ_eff
+    return ring_fft32_order(p, rings, p->d_fft32_rings_act, &p->fft32_nsmall_act);
 }
 
 static akra_status check_common(akra_plan p, akra_prec prec, const void *a, const void *b, int R,
@@ -640,8 +739,9 @@ extern "C" akra_status akra_apply_H(akra_plan p, akra_prec prec, const void *d_x
 }
 
 // ---------------------------------------------------------------------------
-// autotuner: time every compiled Legendre tile shape (synthesis + adjoint over the units
-// the operator will use) and keep the fastest for this (precision, R)
+// autotuner: time every compiled Legendre tile shape over the units the operator will use,
+// the synthesis and the adjoint separately, and keep for this (precision, R) the RHS grouping
+// whose fastest synthesis + fastest adjoint is smallest
 // ---------------------------------------------------------------------------
 template <typename T>
 static akra_status tune_one(akra_plan p, akra_prec prec, int R, cudaStream_t st)
@@ -652,6 +752,7 @@ static akra_status tune_one(akra_plan p, akra_prec prec, int R, cudaStream_t st)
         cands.push_back({2, 128, 2});
         cands.push_back({1, 128, 2});
     }
+    if (std::is_same<T, float>::value) cands.push_back({8, 128, 1});
     cands.push_back({4, 128, 1});
     cands.push_back({2, 128, 1});
     cands.push_back({1, 128, 1});
@@ -672,36 +773,79 @@ static akra_status tune_one(akra_plan p, akra_prec prec, int R, cudaStream_t st)
     }
     cudaMemsetAsync(alm, 0, abytes, st);
     cudaMemsetAsync(p->phi.ptr, 0, p->phi.bytes, st);
-    cudaEvent_t e0, e1;
+    cudaEvent_t e0, e1, e2;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    float best = 1e30f;
-    LegShape pick = cands.back();
+    cudaEventCreate(&e2);
+    std::vector<float> ts(cands.size(), 0.f), ta(cands.size(), 0.f);
     akra_status s = AKRA_OK;
-    for (auto &c : cands) {
-        float tot = 0;
+    for (size_t k = 0; k < cands.size() && s == AKRA_OK; k++) {
+        const LegShape &c = cands[k];
         for (int rep = 0; rep < 3 && s == AKRA_OK; rep++) {
             int nch = 0;
             cudaEventRecord(e0, st);
             s = legendre_synth<T>(p, c, LegMode::KS, alm, p->phi.ptr, R, units, nunits, st);
-            if (s == AKRA_OK) s = legendre_adjoint<T>(p, c, p->phi.ptr, p->partial.ptr, R, units, nunits, &nch, st);
             cudaEventRecord(e1, st);
-            cudaEventSynchronize(e1);
-            float ms = 0;
-            cudaEventElapsedTime(&ms, e0, e1);
-            if (rep > 0) tot += ms;   // the first run is a warm-up
-        }
-        if (s != AKRA_OK) break;
-        if (tot < best) {
-            best = tot;
-            pick = c;
+            if (s == AKRA_OK) s = legendre_adjoint<T>(p, c, p->phi.ptr, p->partial.ptr, R, units, nunits, &nch, st);
+            cudaEventRecord(e2, st);
+            cudaEventSynchronize(e2);
+            float m1 = 0, m2 = 0;
+            cudaEventElapsedTime(&m1, e0, e1);
+            cudaEventElapsedTime(&m2, e1, e2);
+            if (rep > 0) {   // the first run is a warm-up
+                ts[k] += m1;
+                ta[k] += m2;
+            }
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    cudaEventDestroy(e2);
     cudaFree(alm);
     if (s != AKRA_OK) return s;
+    LegShape pick = cands.back();
+    float best = 1e30f;
+    for (size_t k = 0; k < cands.size(); k++)        // synthesis shape k ...
+        for (size_t j = 0; j < cands.size(); j++) {  // ... with adjoint shape j of the same RG
+            if (cands[j].RG != cands[k].RG || ts[k] + ta[j] >= best) continue;
+            best = ts[k] + ta[j];
+            pick = LegShape{cands[k].P, cands[k].NT, cands[k].RG, cands[j].P};
+        }
     p->shapes[(long long)prec * 1000 + (R > 999 ? 999 : R)] = pick;
+    p->ws_gen++;   // captured CG iterations used the previous shape
+    return AKRA_OK;
+}
+
+static bool shape_compiled(akra_prec prec, int P, int RG)
+{
+    if (RG == 1) return P == 1 || P == 2 || P == 4 || (P == 8 && prec == AKRA_F32);
+    if (RG == 2) return P == 1 || P == 2;
+    return RG == 4 && P == 1;
+}
+
+extern "C" akra_status akra_plan_get_shape(akra_plan p, akra_prec prec, int R, int *P, int *PA,
+                                           int *RG)
+{
+    if (!p || !P || !PA || !RG || R < 1 || (prec != AKRA_F64 && prec != AKRA_F32)) {
+        set_error("akra_plan_get_shape: invalid argument");
+        return AKRA_EINVAL;
+    }
+    const LegShape s = leg_shape(p, prec, R);
+    *P = s.P;
+    *PA = s.adjP();
+    *RG = s.RG;
+    return AKRA_OK;
+}
+
+extern "C" akra_status akra_plan_set_shape(akra_plan p, akra_prec prec, int R, int P, int PA, int RG)
+{
+    if (!p || R < 1 || R > 65535 || (prec != AKRA_F64 && prec != AKRA_F32) ||
+        !shape_compiled(prec, P, RG) || !shape_compiled(prec, PA, RG)) {
+        set_error("akra_plan_set_shape: invalid argument or no compiled kernel for P=%d PA=%d RG=%d",
+                  P, PA, RG);
+        return AKRA_EINVAL;
+    }
+    p->shapes[(long long)prec * 1000 + (R > 999 ? 999 : R)] = LegShape{P, 128, RG, PA};
     p->ws_gen++;   // captured CG iterations used the previous shape
     return AKRA_OK;
 }

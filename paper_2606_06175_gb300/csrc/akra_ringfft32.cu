@@ -79,17 +79,27 @@ akra_status ring_fft32_build(akra_plan p)
         mmax = std::max(mmax, M[i]);
     }
     p->fft32_mmax = mmax;
+    p->fft32_M_host = M;
+    p->fft32_msmall = 0;
+    for (int i = 1; i <= N; i++)
+        if (M[i] < mmax) p->fft32_msmall = std::max(p->fft32_msmall, M[i]);
     size_t bytes = sizeof(int) * (N + 1) + sizeof(long long) * (N + 1) + sizeof(float2) * F32_MMAX +
                    sizeof(float2) * (size_t)std::max(total, 1LL);
     if (cudaMalloc(&p->d_fft32_M, sizeof(int) * (N + 1)) != cudaSuccess ||
         cudaMalloc(&p->d_fft32_off, sizeof(long long) * (N + 1)) != cudaSuccess ||
         cudaMalloc(&p->d_fft32_tw2, sizeof(float2) * F32_MMAX) != cudaSuccess ||
-        cudaMalloc(&p->d_fft32_bhat, sizeof(float2) * (size_t)std::max(total, 1LL)) != cudaSuccess) {
+        cudaMalloc(&p->d_fft32_bhat, sizeof(float2) * (size_t)std::max(total, 1LL)) != cudaSuccess ||
+        cudaMalloc(&p->d_fft32_rings_all, sizeof(int) * p->nring) != cudaSuccess ||
+        cudaMalloc(&p->d_fft32_rings_act, sizeof(int) * p->nring) != cudaSuccess) {
         cudaGetLastError();
         set_error("ring FFT table allocation failed");
         return AKRA_ENOMEM;
     }
-    p->bytes_tables += bytes;
+    p->bytes_tables += bytes + 2 * sizeof(int) * (size_t)p->nring;
+    std::vector<int> all(p->nring);
+    for (int r = 0; r < p->nring; r++) all[r] = r;
+    AKRA_TRY(ring_fft32_order(p, all, p->d_fft32_rings_all, &p->fft32_nsmall_all));
+    AKRA_TRY(ring_fft32_order(p, all, p->d_fft32_rings_act, &p->fft32_nsmall_act));
     AKRA_CUDA_TRY(cudaMemcpy(p->d_fft32_M, M.data(), sizeof(int) * (N + 1), cudaMemcpyHostToDevice));
     AKRA_CUDA_TRY(cudaMemcpy(p->d_fft32_off, off.data(), sizeof(long long) * (N + 1), cudaMemcpyHostToDevice));
     k_tw2<<<(F32_MMAX + 255) / 256, 256>>>(p->d_fft32_tw2);
@@ -107,6 +117,26 @@ akra_status ring_fft32_build(akra_plan p)
     AKRA_CUDA_TRY(cudaFuncSetAttribute(k_ring_fft32<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     AKRA_CUDA_TRY(cudaFuncSetAttribute(k_ring_fft32_batch<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (F32_MMAX + F32_NT) * (int)sizeof(float2)));
+    return AKRA_OK;
+}
+
+// Order a ring list for the FP32 FFT launches: rings whose convolution length M is at most
+// fft32_msmall first (their launch reserves less shared memory, so two 1024-thread blocks
+// fit on an SM), then those with M = fft32_mmax.  Writes the list to d_out (device).
+akra_status ring_fft32_order(akra_plan p, const std::vector<int> &rings, int *d_out, int *nsmall)
+{
+    const int N = p->nside;
+    std::vector<int> lo, hi;
+    for (int r : rings) {
+        const int i = r + 1;                                   // 1-based ring index
+        const int n = i < N ? 4 * i : (i <= 3 * N ? 4 * N : 4 * (4 * N - i));
+        const int M = p->fft32_M_host[n / 4];
+        (p->fft32_msmall > 0 && M <= p->fft32_msmall ? lo : hi).push_back(r);
+    }
+    *nsmall = (int)lo.size();
+    lo.insert(lo.end(), hi.begin(), hi.end());
+    if (!lo.empty())
+        AKRA_CUDA_TRY(cudaMemcpy(d_out, lo.data(), sizeof(int) * lo.size(), cudaMemcpyHostToDevice));
     return AKRA_OK;
 }
 
@@ -134,22 +164,37 @@ akra_status ring_fft32(akra_plan p, FftMode mode, void *phi, const void *map_in,
                        bool weighted, int R, const int *rings, int nrings, cudaStream_t st)
 {
     if (nrings <= 0) return AKRA_OK;
-    const int mmax = p->fft32_mmax;
-    const size_t smem = (size_t)(mmax + F32_NT) * sizeof(float2);
-    dim3 grid(nrings, R);
-    Fft32Args a = fft32_args(p, weighted, rings);
+    // the plan's own ring lists go out in two launches by convolution length
+    const int *list = rings;
+    int nsmall = 0;
+    if (p->fft32_msmall > 0 && rings == p->d_active_rings && nrings == p->n_active_rings) {
+        list = p->d_fft32_rings_act;
+        nsmall = p->fft32_nsmall_act;
+    } else if (p->fft32_msmall > 0 && rings == p->d_all_rings && nrings == p->nring) {
+        list = p->d_fft32_rings_all;
+        nsmall = p->fft32_nsmall_all;
+    }
+    Fft32Args a = fft32_args(p, weighted, list);
     a.phi = (float2 *)phi;
     a.map_in = (const float *)map_in;
     a.map_out = (float *)map_out;
+    for (int part = 0; part < 2; part++) {
+        const int cnt = part == 0 ? nsmall : nrings - nsmall;
+        if (cnt <= 0) continue;
+        a.rings = list + (part == 0 ? 0 : nsmall);
+        a.mmax = part == 0 ? p->fft32_msmall : p->fft32_mmax;   // buffer length; scratch follows it
+        const size_t smem = (size_t)(a.mmax + F32_NT) * sizeof(float2);
+        dim3 grid(cnt, R);
 #define AKRA_F32_LAUNCH(MD) k_ring_fft32<MD><<<grid, F32_NT, smem, st>>>(a)
-    switch (mode) {
-    case FftMode::Synth: AKRA_F32_LAUNCH(0); break;
-    case FftMode::Adjoint: AKRA_F32_LAUNCH(1); break;
-    default: AKRA_F32_LAUNCH(2); break;
-    }
+        switch (mode) {
+        case FftMode::Synth: AKRA_F32_LAUNCH(0); break;
+        case FftMode::Adjoint: AKRA_F32_LAUNCH(1); break;
+        default: AKRA_F32_LAUNCH(2); break;
+        }
 #undef AKRA_F32_LAUNCH
-    AKRA_CUDA_TRY(cudaGetLastError());
-    p->launches++;
+        AKRA_CUDA_TRY(cudaGetLastError());
+        p->launches++;
+    }
     return AKRA_OK;
 }
 

@@ -100,6 +100,66 @@ def test_H_matches_oracle(N, L, prec):
     assert err < (TOL64 if prec == A.F64 else tol32(L)), err
 
 
+SHAPES = [(1, 1), (2, 1), (4, 1), (8, 1), (1, 2), (2, 2), (1, 4)]
+
+
+@pytest.mark.parametrize("P,RG", SHAPES)
+@pytest.mark.parametrize("prec", [A.F64, A.F32])
+def test_every_tile_shape_matches_oracle(P, RG, prec):
+    """Each compiled Legendre shape (synthesis and adjoint) on H, with R = RG + 1 RHS so that
+    the last RHS group is ragged; the adjoint uses a different P where one is compiled."""
+    if P == 8 and prec == A.F64:
+        pytest.skip("P = 8 is compiled for FP32 only")
+    N, L, R = 16, 40, RG + 1
+    if RG == 1:
+        pa = {1: 2, 2: 1, 4: 8 if prec == A.F32 else 1, 8: 4}[P]
+    else:
+        pa = 2 if (RG, P) == (2, 1) else 1 if RG == 2 else 1
+    p = A.akra_plan_create(N, L)
+    rng = np.random.default_rng(97 + P + 10 * RG)
+    th, ph = O.pixel_angles(N)
+    ninv = np.where(np.cos(th) < 0.4, 1.0 + rng.random(12 * N * N), 0.0)
+    A.akra_plan_set_weights(p, torch.from_numpy(ninv).to(DEV), 1e-3)
+    A.akra_plan_set_shape(p, prec, R, P, pa, RG)
+    assert A.akra_plan_get_shape(p, prec, R) == {"P": P, "PA": pa, "RG": RG}
+    pairs = [(S.random_alm(L, rng), S.random_alm(L, rng)) for _ in range(R)]
+    y = A.akra_apply_H(p, prec, alm_dev(pairs, prec)).to(torch.complex128).cpu().numpy()
+    w = O.Weights(N, ninv, 1e-3)
+    for r in range(R):
+        ref = np.stack(O.apply_H(N, L, w, *pairs[r]))
+        assert rel(y[r], ref) < (TOL64 if prec == A.F64 else tol32(L)), (P, RG, r)
+    # the adjoint alone on every ring (unweighted) with the forced shape
+    maps = [tuple(rng.normal(size=(2, 12 * N * N))) for _ in range(R)]
+    a = A.akra_adjoint_synth_spin2(p, prec, map_dev(maps, prec)).to(torch.complex128).cpu().numpy()
+    for r in range(R):
+        ref = np.stack(O.adjoint_synth_spin2(N, L, *maps[r]))
+        assert rel(a[r], ref) < (TOL64 if prec == A.F64 else tol32(L)), (P, RG, r)
+
+
+def test_start_table_step_counts():
+    """The per-pair start points only drop steps: FP32 (threshold 2^-40) takes no more steps
+    than FP64 (2^-90), and neither more than the full triangle."""
+    N, L = 64, 150
+    p = A.akra_plan_create(N, L)
+    d = A.akra_plan_describe(p)
+    full = d["nunit"] * (d["ntri"] - 3)
+    assert 0 < d["legendre_steps_f32"] <= d["legendre_steps_f64"] <= full
+    th, _ = O.pixel_angles(N)
+    A.akra_plan_set_weights(p, torch.from_numpy(np.where(np.cos(th) > 0.5, 1.0, 0.0)).to(DEV), 1e-3)
+    d2 = A.akra_plan_describe(p)
+    assert 0 < d2["legendre_steps_f32"] <= d2["legendre_steps_f64"] <= d2["n_active_units"] * (d["ntri"] - 3)
+    assert d2["legendre_steps_f32"] < d["legendre_steps_f32"]
+
+
+def test_shape_errors():
+    p = A.akra_plan_create(8, 12)
+    for bad in [(3, 3, 1), (4, 4, 2), (2, 2, 4), (8, 8, 1)]:
+        with pytest.raises(A.AkraError):
+            A.akra_plan_set_shape(p, A.F64, 1, *bad)
+    with pytest.raises(A.AkraError):
+        A.akra_plan_set_shape(p, A.MIXED, 1, 1, 1, 1)
+
+
 @pytest.mark.parametrize("prec", [A.F64, A.F32])
 def test_apply_A_and_At_match_oracle(prec):
     N, L = 16, 40
@@ -228,6 +288,28 @@ def test_cg_solve_b_equals_cg_solve(cap32_ref):
     b = A.akra_apply_At(p, A.F64, torch.from_numpy(y[None]).to(DEV), weighted=True)
     x, info = A.akra_cg_solve_b(p, A.F64, b, tol=1e-12, maxiter=3000)
     assert rel(x[0].cpu().numpy(), xref) < TOL64
+
+
+def test_reweighting_after_a_solve(cap32_ref):
+    """New weights (another footprint, so other active rings and λ_eff) after solves whose
+    CG iterations were captured: the next solves use the new operator."""
+    wl, N, L, y, xref, _, _ = cap32_ref
+    p = A.akra_plan_create(N, L)
+    A.akra_plan_set_weights(p, torch.from_numpy(wl["ninv"]).to(DEV), 1e-3)
+    yd = torch.from_numpy(y[None]).to(DEV)
+    A.akra_cg_solve(p, A.F64, yd, tol=1e-12, maxiter=3000)
+    A.akra_cg_solve(p, A.MIXED, yd, tol=1e-9, maxiter=3000)
+    th, _ = O.pixel_angles(N)
+    ninv2 = np.where(th > 2.38, 3.0 * wl["ninv"], 0.0)   # the southern half of the cap
+    y2 = np.where(ninv2 > 0, y, 0.0)
+    A.akra_plan_set_weights(p, torch.from_numpy(ninv2).to(DEV), 1e-3)
+    w2 = O.Weights(N, ninv2, 1e-3)
+    x2ref = np.stack(O.cg_solve(N, L, w2, y2[0], y2[1], tol=1e-12, maxiter=3000)[0])
+    y2d = torch.from_numpy(y2[None]).to(DEV)
+    x, info = A.akra_cg_solve(p, A.F64, y2d, tol=1e-12, maxiter=3000)
+    assert info["status"] == 0 and rel(x[0].cpu().numpy(), x2ref) < TOL64
+    x, info = A.akra_cg_solve(p, A.MIXED, y2d, tol=1e-9, maxiter=3000)
+    assert info["status"] == 0 and rel(x[0].cpu().numpy(), x2ref) < 1e-6
 
 
 # ---------------------------------------------------------------------------
