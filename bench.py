@@ -277,6 +277,7 @@ def main():
                 "peak_basis": "152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz (unit counts and maximum clock)",
                 "flops_per_launch": flops, "lm_pair_steps_per_launch": steps,
                 "lm_pair_steps_full_triangle": full_steps,
+                "lm_pair_steps_per_launch_fp64": desc["legendre_steps_f64"],
                 "stage_ms_fp32": st32, "stage_ms_fp64": st64}
 
     # ---- FP64 comparison (the plain FP64 GPU path) ----

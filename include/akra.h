@@ -229,6 +229,17 @@ akra_status akra_batch_cg_solve(akra_batch batch, akra_prec prec, const void *co
 /* Current tile shape (ring pairs per thread, RHS per block) and batched launches so far. */
 akra_status akra_batch_describe(akra_batch batch, int *P, int *RG, long long *launches);
 
+/* Inner tolerance of the mixed-precision solves (Sec. II C: FP32 inner CG, FP64 refinement):
+ * each outer step runs FP32 CG on the normalised FP64 residual to the relative tolerance
+ * max(floor, min(0.1, inner_factor · tol / (‖r‖/‖b‖))), i.e. to what this step must gain
+ * times a safety factor, but not below the floor.  After an outer step the FP64 residual is
+ * about (FP32 tolerance + FP32 operator error) × the previous one, so iterating the FP32 CG
+ * below the FP32 operator's relative error (~0.1-0.2 · 2^-24 · lmax) gains nothing.
+ * inner_floor = 0 (default) selects that floor, 0.1 · 2^-24 · lmax within [5e-6, 1e-3];
+ * inner_factor defaults to 0.5.  Process-wide.  Errors: EINVAL unless 0 <= inner_floor < 0.1
+ * and 0 < inner_factor <= 1. */
+akra_status akra_set_mixed_policy(double inner_floor, double inner_factor);
+
 /* Host-side wall-clock budget (seconds, > 0) for blocking solves; default 3600. */
 akra_status akra_set_timeout(double seconds);
 

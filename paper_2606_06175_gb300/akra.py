@@ -53,7 +53,7 @@ EXPORTS = ["akra_plan_create", "akra_plan_destroy", "akra_last_error", "akra_ver
            "akra_time_H_stages", "akra_synth_spin2_static", "akra_cg_solve_adjoint",
            "akra_weight_grad", "akra_batch_create", "akra_batch_destroy", "akra_batch_autotune",
            "akra_batch_apply_H", "akra_batch_cg_solve", "akra_batch_describe",
-           "akra_plan_get_shape", "akra_plan_set_shape"]
+           "akra_plan_get_shape", "akra_plan_set_shape", "akra_set_mixed_policy"]
 
 _lib_handle = None
 
@@ -89,6 +89,7 @@ def load(build_if_missing: bool = False):
         "akra_cg_solve": ([vp, i, vp, vp, i, d, i, ctypes.POINTER(CgInfo), vp], i),
         "akra_cg_solve_b": ([vp, i, vp, vp, i, d, i, ctypes.POINTER(CgInfo), vp], i),
         "akra_set_timeout": ([d], i),
+        "akra_set_mixed_policy": ([d, d], i),
         "akra_autotune": ([vp, i, i, vp], i),
         "akra_plan_get_shape": ([vp, i, i, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)], i),
         "akra_plan_set_shape": ([vp, i, i, i, i, i], i),
@@ -308,6 +309,12 @@ def akra_weight_grad(plan: Plan, prec: int, Au: torch.Tensor, y: torch.Tensor, A
 
 def akra_set_timeout(seconds: float):
     _check(load().akra_set_timeout(float(seconds)))
+
+
+def akra_set_mixed_policy(inner_floor: float = 0.0, inner_factor: float = 0.5):
+    """FP32 inner tolerance of mixed-precision solves: max(floor, min(0.1, factor·tol/relres));
+    floor 0 = automatic (0.1 · 2^-24 · lmax within [5e-6, 1e-3])."""
+    _check(load().akra_set_mixed_policy(float(inner_floor), float(inner_factor)))
 
 
 def akra_autotune(plan: Plan, prec: int, R: int = 1, stream=None):

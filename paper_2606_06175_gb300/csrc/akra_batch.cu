@@ -530,7 +530,7 @@ extern "C" akra_status akra_batch_cg_solve(akra_batch b, akra_prec prec, const v
                 if (w >= tol && !bad) {
                     act[i] = 1;
                     any = true;
-                    tl[i] = std::max(5e-6, std::min(0.1, 0.05 * tol / w));
+                    tl[i] = std::max(inner_floor(b->plans[i]->lmax), std::min(0.1, g_inner_factor * tol / w));
                 }
             }
             if (!any || budget <= 0) break;

@@ -379,6 +379,16 @@ static akra_status cg_graph(akra_plan p, int R, CgBufs &b, cudaGraphExec_t *out)
 }
 
 double g_timeout_s = 3600.0;
+// MIXED inner tolerance: max(floor, min(0.1, factor · tol / current FP64 residual)).
+// floor <= 0 selects the automatic floor, the FP32 operator's own accuracy (below it the FP32
+// CG gains nothing on the FP64 residual): 0.1 · 2^-24 · lmax, within [5e-6, 1e-3].
+double g_inner_floor = 0.0, g_inner_factor = 0.5;
+
+double inner_floor(int lmax)
+{
+    if (g_inner_floor > 0) return g_inner_floor;
+    return std::min(1e-3, std::max(5e-6, 0.1 * 0x1p-24 * (double)lmax));
+}
 
 // wait for the event with a wall-clock budget (no unbounded device wait)
 akra_status bounded_wait(cudaEvent_t ev, std::chrono::steady_clock::time_point deadline)
@@ -542,7 +552,7 @@ static akra_status solve_b(akra_plan p, akra_prec prec, const void *bsrc, void *
                 break;
             }
             // inner tolerance: what this outer step must gain, but not below FP32 reach
-            const double tin = std::max(5e-6, std::min(0.1, 0.05 * tol / worst));
+            const double tin = std::max(inner_floor(p->lmax), std::min(0.1, g_inner_factor * tol / worst));
             k_cast_scaled<<<RED_NB, RED_NT, 0, cs>>>(2 * p->ntri, R, (const double2 *)r64, b.res,
                                                      (float2 *)b.v32[0]);
             AKRA_CUDA_TRY(cudaGetLastError());
@@ -721,6 +731,17 @@ static akra_status join_user(akra_plan p, cudaStream_t user, CgBufs &b)
 }  // namespace akra
 
 using namespace akra;
+
+extern "C" akra_status akra_set_mixed_policy(double inner_floor, double inner_factor)
+{
+    if (!(inner_floor >= 0) || !(inner_floor < 0.1) || !(inner_factor > 0) || !(inner_factor <= 1)) {
+        set_error("akra_set_mixed_policy: need 0 <= inner_floor < 0.1 and 0 < inner_factor <= 1");
+        return AKRA_EINVAL;
+    }
+    g_inner_floor = inner_floor;
+    g_inner_factor = inner_factor;
+    return AKRA_OK;
+}
 
 extern "C" akra_status akra_set_timeout(double seconds)
 {

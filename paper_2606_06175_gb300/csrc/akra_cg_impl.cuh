@@ -52,6 +52,8 @@ template <typename T>
 inline void **vecs(CgBufs &b) { return PrecIdx<T>::v == 0 ? b.v64 : b.v32; }
 
 extern double g_timeout_s;
+extern double g_inner_floor, g_inner_factor;
+double inner_floor(int lmax);
 akra_status cg_reserve(akra_plan p, int R, CgBufs &b);
 akra_status bounded_wait(cudaEvent_t ev, std::chrono::steady_clock::time_point deadline);
 // x = 0, r = b (slot 0), p = P r, state and ctl initialised (precision T region)

@@ -23,6 +23,8 @@ def main():
     ap.add_argument("--prec", default="f32", choices=["f32", "f64"])
     ap.add_argument("--reps", type=int, default=2)
     ap.add_argument("--solve", action="store_true", help="one mixed-precision solve instead")
+    ap.add_argument("--shape", type=int, nargs=3, metavar=("P", "PA", "RG"),
+                    help="force the Legendre tile shape of --prec (R = 1)")
     args = ap.parse_args()
     N, L = args.nside, args.lmax
     sv = S.survey(N, "des", S.SEEDS["des2048"])
@@ -30,6 +32,8 @@ def main():
     plan = A.akra_plan_create(N, L)
     A.akra_plan_set_weights(plan, torch.from_numpy(sv["ninv"]).to(dev), 1e-3)
     prec = A.F32 if args.prec == "f32" else A.F64
+    if args.shape:
+        A.akra_plan_set_shape(plan, prec, 1, *args.shape)
     kE = S.grf_alm(L, S.cl_kappa(L), sv["rng_alm"])
     x64 = torch.from_numpy(np.stack([kE, np.zeros_like(kE)])[None]).to(dev)
     if args.solve:

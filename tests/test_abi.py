@@ -53,6 +53,13 @@ def test_null_arguments_are_rejected(lib):
     assert lib.akra_apply_H(None, 0, None, None, 1, None) == 1
     assert lib.akra_cg_solve(None, 0, None, None, 1, 1e-6, 10, None, None) == 1
     assert lib.akra_set_timeout(ctypes.c_double(-1.0)) == 1
+    lib.akra_set_mixed_policy.argtypes = [ctypes.c_double, ctypes.c_double]
+    assert lib.akra_set_mixed_policy(-1.0, 0.5) == 1
+    assert lib.akra_set_mixed_policy(0.0, 0.0) == 1
+    assert lib.akra_set_mixed_policy(0.0, 2.0) == 1
+    assert lib.akra_set_mixed_policy(0.0, 0.5) == 0     # the defaults
+    assert lib.akra_plan_get_shape(None, 0, 1, None, None, None) == 1
+    assert lib.akra_plan_set_shape(None, 0, 1, 1, 1, 1) == 1
     assert lib.akra_plan_describe(None, None) == 1
     lib.akra_plan_destroy(None)   # no-op
     assert b"NULL" in lib.akra_last_error() or len(lib.akra_last_error()) > 0
