@@ -279,6 +279,20 @@ def main():
                 "lm_pair_steps_full_triangle": full_steps,
                 "lm_pair_steps_per_launch_fp64": desc["legendre_steps_f64"],
                 "stage_ms_fp32": st32, "stage_ms_fp64": st64}
+    # measured FMA rates (saturating FMA-chain kernel on this GPU) beside the nominal peak
+    f32_meas = A.akra_fma_rate(A.F32)
+    f64_meas = A.akra_fma_rate(A.F64)
+    flops64 = desc["legendre_steps_f64"] * (4 + 8) * 2
+    roofline["measured_fma_tflops"] = {"fp32": f32_meas, "fp64": f64_meas}
+    roofline["frac_of_measured_fp32"] = achieved / f32_meas
+    roofline["fp64_legendre"] = {
+        k: {"achieved": flops64 / (st64[k] * 1e-3) / 1e12,
+            "frac_of_measured_fp64": flops64 / (st64[k] * 1e-3) / 1e12 / f64_meas}
+        for k in ("legendre_synth", "legendre_adjoint")}
+    roofline["fp32_legendre"] = {
+        k: {"achieved": flops / (st32[k] * 1e-3) / 1e12,
+            "frac_of_measured_fp32": flops / (st32[k] * 1e-3) / 1e12 / f32_meas}
+        for k in ("legendre_synth", "legendre_adjoint")}
 
     # ---- FP64 comparison (the plain FP64 GPU path) ----
     t_h64 = st64["total"] * 1e-3

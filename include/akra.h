@@ -260,6 +260,12 @@ akra_status akra_plan_get_shape(akra_plan plan, akra_prec prec, int R, int *P, i
  * The results do not depend on the shape beyond rounding order.  Errors: EINVAL. */
 akra_status akra_plan_set_shape(akra_plan plan, akra_prec prec, int R, int P, int PA, int RG);
 
+/* Measured FMA rate of the current device in TFLOP/s (2 flops per FMA) for prec AKRA_F32 or
+ * AKRA_F64: a saturating kernel of independent FMA chains on every SM, timed with CUDA events
+ * (tens of milliseconds; blocking).  The denominator of the Legendre kernels' pipe fractions;
+ * the paper has no counterpart.  Errors: EINVAL, ENOMEM, ECUDA. */
+akra_status akra_fma_rate(akra_prec prec, double *tflops);
+
 /* Time the four stages of one H application (Legendre synthesis, ring FFT x W x FFT,
  * Legendre adjoint, epilogue) with CUDA events on `stream`, averaged over `reps` runs after
  * one warm-up, on the plan's own scratch input.  ms_out[0..3] receive the per-stage

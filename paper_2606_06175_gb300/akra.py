@@ -53,7 +53,7 @@ EXPORTS = ["akra_plan_create", "akra_plan_destroy", "akra_last_error", "akra_ver
            "akra_time_H_stages", "akra_synth_spin2_static", "akra_cg_solve_adjoint",
            "akra_weight_grad", "akra_batch_create", "akra_batch_destroy", "akra_batch_autotune",
            "akra_batch_apply_H", "akra_batch_cg_solve", "akra_batch_describe",
-           "akra_plan_get_shape", "akra_plan_set_shape", "akra_set_mixed_policy"]
+           "akra_plan_get_shape", "akra_plan_set_shape", "akra_set_mixed_policy", "akra_fma_rate"]
 
 _lib_handle = None
 
@@ -90,6 +90,7 @@ def load(build_if_missing: bool = False):
         "akra_cg_solve_b": ([vp, i, vp, vp, i, d, i, ctypes.POINTER(CgInfo), vp], i),
         "akra_set_timeout": ([d], i),
         "akra_set_mixed_policy": ([d, d], i),
+        "akra_fma_rate": ([i, ctypes.POINTER(d)], i),
         "akra_autotune": ([vp, i, i, vp], i),
         "akra_plan_get_shape": ([vp, i, i, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)], i),
         "akra_plan_set_shape": ([vp, i, i, i, i, i], i),
@@ -333,6 +334,13 @@ def akra_plan_get_shape(plan: Plan, prec: int, R: int = 1) -> dict:
 def akra_plan_set_shape(plan: Plan, prec: int, R: int, P: int, PA: int, RG: int):
     """Force the Legendre tile shape for (prec, R)."""
     _check(load().akra_plan_set_shape(plan.handle, prec, R, P, PA, RG))
+
+
+def akra_fma_rate(prec: int) -> float:
+    """Measured FMA rate of the current device, TFLOP/s (FP32 or FP64)."""
+    v = ctypes.c_double()
+    _check(load().akra_fma_rate(prec, ctypes.byref(v)))
+    return v.value
 
 
 def akra_time_H_stages(plan: Plan, prec: int, R: int = 1, reps: int = 3, stream=None) -> dict:
