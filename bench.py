@@ -200,6 +200,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--fp64-solve", action="store_true", help="also run one full FP64 CG solve")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fields", action="store_true",
+                    help="also time the E-only solve and the conditional B-mode solve (App. A)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -312,6 +314,27 @@ def main():
         fp64["cg_solve_s_extrapolated"] = (inner + 1) * t_h64
         fp64["extrapolation"] = "FP64 H time x (mixed inner iterations + 1)"
 
+    # ---- field-restricted solves (App. A), same workload and tolerance ----
+    fields = None
+    if args.fields:
+        xf = torch.empty_like(x)
+        A.akra_cg_solve_fields(plan, A.MIXED, A.SOLVE_E, y, xf, tol=TOL, maxiter=2000)   # capture
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, ie = A.akra_cg_solve_fields(plan, A.MIXED, A.SOLVE_E, y, xf, tol=TOL, maxiter=2000)
+        torch.cuda.synchronize()
+        t_e = time.perf_counter() - t0
+        A.akra_cg_solve_fields(plan, A.MIXED, A.SOLVE_B_GIVEN_E, y, xf.clone(), tol=TOL, maxiter=2000)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, ib = A.akra_cg_solve_fields(plan, A.MIXED, A.SOLVE_B_GIVEN_E, y, xf, tol=TOL, maxiter=2000)
+        torch.cuda.synchronize()
+        t_b = time.perf_counter() - t0
+        fields = {"e_only": {"solve_s": t_e, "inner_iters": ie["iters"], "outer": ie["outer"],
+                             "h_applies_f64": ie["h_applies_f64"], "relres": ie["relres"]},
+                  "b_given_e": {"solve_s": t_b, "inner_iters": ib["iters"], "outer": ib["outer"],
+                                "h_applies_f64": ib["h_applies_f64"], "relres": ib["relres"]}}
+
     # ---- end to end through the C ABI with host buffers ----
     y_host = y.cpu().pin_memory()
     x_host = torch.empty(x.shape, dtype=x.dtype).pin_memory()
@@ -351,6 +374,8 @@ def main():
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
         "gpu_launches": launches, "clocks": clk.summary(),
     }
+    if fields is not None:
+        line["fields"] = fields
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

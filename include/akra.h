@@ -229,6 +229,22 @@ akra_status akra_batch_cg_solve(akra_batch batch, akra_prec prec, const void *co
 /* Current tile shape (ring pairs per thread, RHS per block) and batched launches so far. */
 akra_status akra_batch_describe(akra_batch batch, int *P, int *RG, long long *launches);
 
+/* Field-restricted solves (App. A, "Conditional B-mode solve").  With b = A^T W y as in
+ * akra_cg_solve and H_EE, H_BB, H_BE the E/B blocks of the joint operator (Eqs. A3-A6):
+ *   AKRA_SOLVE_E: the E-mode normal equations H_EE κ_E = b_E (κ_B held at zero; the B rows
+ *     are dropped).  d_x [R][2][ntri] receives (κ̂_E, 0).
+ *   AKRA_SOLVE_B_GIVEN_E: the reduced B-mode equation H_BB κ_B = b_B - H_BE κ̂_E (Eq. A8),
+ *     with κ̂_E read from the E field of d_x on input (e.g. from an AKRA_SOLVE_E call); the
+ *     correction H_BE κ̂_E costs one H application (FP64 unless prec is F32).  d_x keeps its
+ *     E field and receives κ̂_B in its B field.
+ * Precisions, layouts, blocking behaviour and statuses as akra_cg_solve; info->relres is
+ * relative to the reduced right-hand side (b_E, or b_B - H_BE κ̂_E).  Errors: as
+ * akra_cg_solve, and EINVAL for any other value of fields. */
+typedef enum { AKRA_SOLVE_E = 1, AKRA_SOLVE_B_GIVEN_E = 2 } akra_fields;
+akra_status akra_cg_solve_fields(akra_plan plan, akra_prec prec, akra_fields fields,
+                                 const void *d_shear, void *d_x, int R, double tol, int maxiter,
+                                 akra_cg_info *info, void *stream);
+
 /* Inner tolerance of the mixed-precision solves (Sec. II C: FP32 inner CG, FP64 refinement):
  * each outer step runs FP32 CG on the normalised FP64 residual to the relative tolerance
  * max(floor, min(0.1, inner_factor · tol / (‖r‖/‖b‖))), i.e. to what this step must gain

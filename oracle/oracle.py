@@ -407,6 +407,35 @@ def cg_solve(nside: int, lmax: int, wts: Weights, y1, y2, tol: float = 1e-8, max
     return pcg(lambda e, bb: apply_H(nside, lmax, wts, e, bb), b, wts.precond, lmax, tol, maxiter)
 
 
+def cg_solve_E(nside: int, lmax: int, wts: Weights, y1, y2, tol: float = 1e-8, maxiter: int = 1000):
+    """E-mode normal equations H_EE κ_E = b_E (App. A: the E block row and column of Eq. A3,
+    κ_B held at zero) by PCG on the E field; returns ((κ̂_E, 0), iterations, relres, history)."""
+    bE, _ = rhs_b(nside, lmax, wts, y1, y2)
+    zero = np.zeros_like(bE)
+
+    def apply_EE(e, _b):
+        hE, _ = apply_H(nside, lmax, wts, e, zero)
+        return hE, zero
+
+    return pcg(apply_EE, (bE, zero), wts.precond, lmax, tol, maxiter)
+
+
+def cg_solve_B_given_E(nside: int, lmax: int, wts: Weights, y1, y2, kE, tol: float = 1e-8,
+                       maxiter: int = 1000):
+    """Conditional B-mode solve (App. A, Eq. A8): H_BB κ_B = b_B - H_BE κ̂_E, where H_BE κ̂_E is
+    the B part of H applied to (κ̂_E, 0).  Returns ((0, κ̂_B), iterations, relres, history)."""
+    _, bB = rhs_b(nside, lmax, wts, y1, y2)
+    zero = np.zeros_like(bB)
+    _, hBE = apply_H(nside, lmax, wts, np.asarray(kE, np.complex128), zero)
+    rhs = bB - hBE
+
+    def apply_BB(_e, b):
+        _, hB = apply_H(nside, lmax, wts, zero, b)
+        return zero, hB
+
+    return pcg(apply_BB, (zero, rhs), wts.precond, lmax, tol, maxiter)
+
+
 def lanczos_condition(hist) -> float:
     """κ of the (preconditioned) operator from CG's α, β (the CG-Lanczos tridiagonal)."""
     k = len(hist)

@@ -53,7 +53,8 @@ EXPORTS = ["akra_plan_create", "akra_plan_destroy", "akra_last_error", "akra_ver
            "akra_time_H_stages", "akra_synth_spin2_static", "akra_cg_solve_adjoint",
            "akra_weight_grad", "akra_batch_create", "akra_batch_destroy", "akra_batch_autotune",
            "akra_batch_apply_H", "akra_batch_cg_solve", "akra_batch_describe",
-           "akra_plan_get_shape", "akra_plan_set_shape", "akra_set_mixed_policy", "akra_fma_rate"]
+           "akra_plan_get_shape", "akra_plan_set_shape", "akra_set_mixed_policy", "akra_fma_rate",
+           "akra_cg_solve_fields"]
 
 _lib_handle = None
 
@@ -88,6 +89,7 @@ def load(build_if_missing: bool = False):
         "akra_apply_H": ([vp, i, vp, vp, i, vp], i),
         "akra_cg_solve": ([vp, i, vp, vp, i, d, i, ctypes.POINTER(CgInfo), vp], i),
         "akra_cg_solve_b": ([vp, i, vp, vp, i, d, i, ctypes.POINTER(CgInfo), vp], i),
+        "akra_cg_solve_fields": ([vp, i, i, vp, vp, i, d, i, ctypes.POINTER(CgInfo), vp], i),
         "akra_set_timeout": ([d], i),
         "akra_set_mixed_policy": ([d, d], i),
         "akra_fma_rate": ([i, ctypes.POINTER(d)], i),
@@ -277,6 +279,27 @@ def akra_cg_solve(plan: Plan, prec: int, shear: torch.Tensor, out=None, tol: flo
     R = shear.shape[0]
     _need(shear, (R, 2, plan.npix), torch.float32 if prec == F32 else torch.float64, "shear")
     return _solve(load().akra_cg_solve, plan, prec, shear, out, R, tol, maxiter, stream, raise_on_noconv)
+
+
+SOLVE_E, SOLVE_B_GIVEN_E = 1, 2
+
+
+def akra_cg_solve_fields(plan: Plan, prec: int, fields: int, shear: torch.Tensor, out=None,
+                         tol: float = 1e-6, maxiter: int = 1000, stream=None,
+                         raise_on_noconv: bool = False):
+    """E-only solve (fields=SOLVE_E) or the conditional B-mode solve given κ̂_E in the E field
+    of `out` (fields=SOLVE_B_GIVEN_E); see akra_cg_solve_fields in akra.h."""
+    R = shear.shape[0]
+    _need(shear, (R, 2, plan.npix), torch.float32 if prec == F32 else torch.float64, "shear")
+    if fields == SOLVE_B_GIVEN_E:
+        if out is None:
+            raise ValueError("SOLVE_B_GIVEN_E reads κ_E from `out`")
+        _need(out, (R, 2, plan.ntri), _cdtype(F64 if prec == MIXED else prec), "out")
+
+    def fn(h, pr, src, dst, r, tl, mi, inf, st):
+        return load().akra_cg_solve_fields(h, pr, fields, src, dst, r, tl, mi, inf, st)
+
+    return _solve(fn, plan, prec, shear, out, R, tol, maxiter, stream, raise_on_noconv)
 
 
 def akra_cg_solve_b(plan: Plan, prec: int, b: torch.Tensor, out=None, tol: float = 1e-6,

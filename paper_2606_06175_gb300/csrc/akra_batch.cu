@@ -32,6 +32,7 @@ struct akra_batch_s {
     std::vector<int> nch;                 // Legendre chunks per instance (current shape)
     cudaGraphExec_t graph = nullptr;
     std::vector<unsigned> graph_gens;
+    long long graph_kernels = 0;
     akra::LegShape graph_shape{0, 0, 0};
     int *h_flags = nullptr;               // pinned: one done flag per instance
     long long launches = 0;
@@ -230,16 +231,25 @@ static akra_status batch_graph(akra_batch b, std::vector<CgBufs> &cb)
         sk[i] = &cb[i].ctl[1]->all_done;
     }
     AKRA_TRY(batch_args(b, xs.data(), ys.data(), sk.data(), b->stream));
+    // capturing launches nothing: keep the launch counters as they are
+    const long long b_launches = b->launches;
+    std::vector<long long> p_launches(b->ninst);
+    for (int i = 0; i < b->ninst; i++) p_launches[i] = b->plans[i]->launches;
     AKRA_CUDA_TRY(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
     akra_status s = batch_H32(b, xs.data(), ys.data(), sk.data(), b->stream);
     for (int i = 0; i < b->ninst && s == AKRA_OK; i++) s = cg_launch_tail<float>(b->plans[i], cb[i], b->stream);
     cudaGraph_t graph = nullptr;
     const cudaError_t e = cudaStreamEndCapture(b->stream, &graph);
+    b->launches = b_launches;
+    for (int i = 0; i < b->ninst; i++) b->plans[i]->launches = p_launches[i];
     if (s != AKRA_OK) {
         if (graph) cudaGraphDestroy(graph);
         return s;
     }
     AKRA_CUDA_TRY(e);
+    size_t nnodes = 0;
+    cudaGraphGetNodes(graph, nullptr, &nnodes);
+    b->graph_kernels = (long long)nnodes;   // every captured node is a kernel launch
     const cudaError_t e2 = cudaGraphInstantiate(&b->graph, graph, 0);
     cudaGraphDestroy(graph);
     AKRA_CUDA_TRY(e2);
@@ -270,7 +280,7 @@ static akra_status batch_cg32(akra_batch b, std::vector<CgBufs> &cb, const std::
     while (launched < maxiter) {
         const int k = std::min(chunk, maxiter - launched);
         for (int j = 0; j < k; j++) AKRA_CUDA_TRY(cudaGraphLaunch(b->graph, st));
-        b->launches += (long long)k * (4 + 4 * b->ninst);
+        b->launches += (long long)k * b->graph_kernels;
         launched += k;
         for (int i = 0; i < b->ninst; i++)
             AKRA_CUDA_TRY(cudaMemcpyAsync(&b->h_flags[i], &cb[i].ctl[1]->all_done, sizeof(int),

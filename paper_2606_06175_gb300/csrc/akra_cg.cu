@@ -326,7 +326,7 @@ akra_status cg_reserve(akra_plan p, int R, CgBufs &b)
 template <typename T>
 static akra_status cg_graph(akra_plan p, int R, CgBufs &b, cudaGraphExec_t *out)
 {
-    const long long key = PrecIdx<T>::v * 1000 + R;
+    const long long key = ((long long)p->fields << 40) | ((long long)PrecIdx<T>::v << 32) | (long long)R;
     CgGraph *g = p->graphs.count(key) ? p->graphs[key] : nullptr;
     if (g && g->exec && g->gen == p->ws_gen) {
         *out = g->exec;
@@ -352,8 +352,10 @@ static akra_status cg_graph(akra_plan p, int R, CgBufs &b, cudaGraphExec_t *out)
     cudaStream_t cs = p->stream;
     AKRA_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
     p->cur_skip = &ctl->all_done;
+    const long long launched_before = p->launches;   // capturing launches nothing
     akra_status s1 = op_H<T>(p, v[3], v[4], R, cs);
     p->cur_skip = nullptr;
+    p->launches = launched_before;
     if (s1 == AKRA_OK) {
         k_cg_dot_pq<T><<<RED_NB, RED_NT, 0, cs>>>(p->lmax, p->ntri, (const cx_t<T> *)v[3],
                                                   (const cx_t<T> *)v[4], st, ctl, b.scratch);
@@ -370,6 +372,9 @@ static akra_status cg_graph(akra_plan p, int R, CgBufs &b, cudaGraphExec_t *out)
         return s1;
     }
     AKRA_CUDA_TRY(e);
+    size_t nnodes = 0;
+    cudaGraphGetNodes(graph, nullptr, &nnodes);
+    g->kernels = (long long)nnodes;   // every captured node is a kernel launch
     e = cudaGraphInstantiate(&g->exec, graph, 0);
     cudaGraphDestroy(graph);
     AKRA_CUDA_TRY(e);
@@ -416,6 +421,8 @@ static akra_status cg_run(akra_plan p, int R, CgBufs &b, double tol, int maxiter
 {
     cudaGraphExec_t exec;
     AKRA_TRY(cg_graph<T>(p, R, b, &exec));
+    const long long per_iter =
+        p->graphs[((long long)p->fields << 40) | ((long long)PrecIdx<T>::v << 32) | (long long)R]->kernels;
     void **v = vecs<T>(b);
     CgState *st = b.st[PrecIdx<T>::v];
     CgCtl *ctl = b.ctl[PrecIdx<T>::v];
@@ -436,7 +443,7 @@ static akra_status cg_run(akra_plan p, int R, CgBufs &b, double tol, int maxiter
     while (launched < maxiter) {
         const int k = std::min(chunk, maxiter - launched);
         for (int i = 0; i < k; i++) AKRA_CUDA_TRY(cudaGraphLaunch(exec, cs));
-        p->launches += 7LL * k;
+        p->launches += per_iter * k;
         launched += k;
         AKRA_CUDA_TRY(cudaMemcpyAsync(h_done, &ctl->all_done, sizeof(int), cudaMemcpyDeviceToHost, cs));
         AKRA_CUDA_TRY(cudaEventRecord(p->ev_a, cs));
@@ -717,6 +724,47 @@ static akra_status check_cg(akra_plan p, akra_prec prec, const void *a, const vo
     return AKRA_OK;
 }
 
+// out = a - b over n complex entries
+template <typename T>
+__global__ void k_sub(long long n, const cx_t<T> *__restrict__ a, const cx_t<T> *__restrict__ b,
+                      cx_t<T> *__restrict__ out)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const cx_t<T> u = a[i], v = b[i];
+        out[i] = cx_t<T>{u.x - v.x, u.y - v.y};
+    }
+}
+
+// zero field f (0 = E, 1 = B) of an [R][2][ntri] complex array
+static akra_status zero_field(akra_plan p, void *v, size_t elem, int R, int f, cudaStream_t st)
+{
+    const size_t fb = (size_t)p->ntri * elem;
+    AKRA_CUDA_TRY(cudaMemset2DAsync((char *)v + f * fb, 2 * fb, 0, fb, R, st));
+    return AKRA_OK;
+}
+
+// copy field f of an [R][2][ntri] complex array to / from a packed [R][ntri] one
+static akra_status copy_field(akra_plan p, void *dst, const void *src, size_t elem, int R, int f,
+                              bool to_packed, cudaStream_t st)
+{
+    const size_t fb = (size_t)p->ntri * elem;
+    if (to_packed)
+        AKRA_CUDA_TRY(cudaMemcpy2DAsync(dst, fb, (const char *)src + f * fb, 2 * fb, fb, R,
+                                        cudaMemcpyDeviceToDevice, st));
+    else
+        AKRA_CUDA_TRY(cudaMemcpy2DAsync((char *)dst + f * fb, 2 * fb, src, fb, fb, R,
+                                        cudaMemcpyDeviceToDevice, st));
+    return AKRA_OK;
+}
+
+// H acts on the given fields for the lifetime of the guard (field-restricted solves)
+struct FieldGuard {
+    akra_plan p;
+    FieldGuard(akra_plan q, int fields) : p(q) { p->fields = fields; }
+    ~FieldGuard() { p->fields = 3; }
+};
+
 // the internal stream starts after everything already queued on the caller's stream
 static akra_status join_user(akra_plan p, cudaStream_t user, CgBufs &b)
 {
@@ -800,4 +848,60 @@ extern "C" akra_status akra_cg_solve_adjoint(akra_plan p, akra_prec prec, const 
     const bool dbl = prec != AKRA_F32;
     AKRA_TRY(metric_inverse(p, dbl, d_g, dbl ? b.v64[0] : b.v32[0], R, p->stream));
     return solve_b(p, prec, nullptr, d_u, R, tol, maxiter, info, user, true, b, 0);
+}
+
+extern "C" akra_status akra_cg_solve_fields(akra_plan p, akra_prec prec, akra_fields fields,
+                                            const void *d_shear, void *d_x, int R, double tol,
+                                            int maxiter, akra_cg_info *info, void *stream)
+{
+    AKRA_TRY(check_cg(p, prec, d_shear, d_x, R, tol, maxiter, "akra_cg_solve_fields"));
+    if (fields != AKRA_SOLVE_E && fields != AKRA_SOLVE_B_GIVEN_E) {
+        set_error("akra_cg_solve_fields: fields must be AKRA_SOLVE_E or AKRA_SOLVE_B_GIVEN_E");
+        return AKRA_EINVAL;
+    }
+    cudaStream_t user = (cudaStream_t)stream;
+    CgBufs b;
+    AKRA_TRY(cg_reserve(p, R, b));
+    AKRA_TRY(join_user(p, user, b));
+    cudaStream_t cs = p->stream;
+    const bool dbl = prec != AKRA_F32;
+    const size_t elem = dbl ? sizeof(double2) : sizeof(float2);
+    // b = A^T W y (the joint right-hand side; FP64 unless the whole solve is FP32)
+    akra_status s = dbl ? op_adjoint<double>(p, LegMode::KS, d_shear, b.v64[0], true, R, cs)
+                        : op_adjoint<float>(p, LegMode::KS, d_shear, b.v32[0], true, R, cs);
+    if (s != AKRA_OK) return s;
+    AKRA_TRY(cg_reserve(p, R, b));
+    void **v = dbl ? b.v64 : b.v32;
+    int h64 = dbl ? 1 : 0;
+    if (fields == AKRA_SOLVE_E) {
+        // E-mode normal equations H_EE κ_E = b_E: B rows dropped, κ_B held at zero
+        AKRA_TRY(zero_field(p, v[0], elem, R, 1, cs));
+        FieldGuard guard(p, 1);
+        return solve_b(p, prec, nullptr, d_x, R, tol, maxiter, info, user, true, b, h64);
+    }
+    // reduced B-mode equation (Eq. A8): b~_B = b_B - H_BE κ_E = [b - H (κ_E, 0)]_B
+    AKRA_CUDA_TRY(cudaMemcpyAsync(v[1], d_x, (size_t)R * 2 * p->ntri * elem, cudaMemcpyDeviceToDevice, cs));
+    AKRA_TRY(zero_field(p, v[1], elem, R, 1, cs));
+    s = dbl ? op_H<double>(p, v[1], v[4], R, cs) : op_H<float>(p, v[1], v[4], R, cs);
+    if (s != AKRA_OK) return s;
+    h64 += dbl ? 1 : 0;
+    const long long n = (long long)R * 2 * p->ntri;
+    if (dbl)
+        k_sub<double><<<RED_NB, RED_NT, 0, cs>>>(n, (const double2 *)v[0], (const double2 *)v[4], (double2 *)v[0]);
+    else
+        k_sub<float><<<RED_NB, RED_NT, 0, cs>>>(n, (const float2 *)v[0], (const float2 *)v[4], (float2 *)v[0]);
+    AKRA_CUDA_TRY(cudaGetLastError());
+    p->launches++;
+    AKRA_TRY(zero_field(p, v[0], elem, R, 0, cs));
+    // keep κ_E aside: the solve writes the whole of d_x
+    AKRA_TRY(ws_reserve(p, p->xsave, (size_t)R * p->ntri * elem));
+    AKRA_TRY(cg_reserve(p, R, b));
+    AKRA_TRY(copy_field(p, p->xsave.ptr, d_x, elem, R, 0, true, cs));
+    {
+        FieldGuard guard(p, 2);
+        s = solve_b(p, prec, nullptr, d_x, R, tol, maxiter, info, user, true, b, h64);
+    }
+    if (s != AKRA_OK) return s;
+    // the caller's stream already waits for the solve: put κ_E back after it
+    return copy_field(p, d_x, p->xsave.ptr, elem, R, 0, false, user);
 }

@@ -26,6 +26,7 @@ constexpr int RED_NT = 256;
 struct CgGraph {
     cudaGraphExec_t exec = nullptr;
     unsigned gen = 0;
+    long long kernels = 0;   // kernel nodes of one captured iteration
 };
 
 // ---------------------------------------------------------------------------

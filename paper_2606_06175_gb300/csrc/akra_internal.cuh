@@ -189,6 +189,9 @@ struct akra_plan_s {
     int *d_all_rings = nullptr;              // [nring] 0..nring-1
     int *d_all_units = nullptr;              // [nunit] 0..nunit-1
 
+    // fields H acts on inside a field-restricted solve (bit 0 E, bit 1 B); 3 everywhere else
+    int fields = 3;
+
     // weights
     bool has_weights = false;
     double lambda = 0, lambda_eff = 0, precond = 1, omega = 0;
@@ -202,6 +205,7 @@ struct akra_plan_s {
 
     // workspaces (grown on demand)
     akra::Workspace phi, partial, cg, red;
+    akra::Workspace xsave;                   // κ_E kept aside by the conditional B-mode solve
     cudaStream_t stream = nullptr;           // internal stream for captured CG graphs
     cudaEvent_t ev_a = nullptr, ev_b = nullptr;
     std::map<long long, akra::LegShape> shapes;   // key: prec*1000 + R
@@ -240,10 +244,12 @@ template <typename T>
 akra_status legendre_adjoint(akra_plan p, const LegShape &s, const void *phi, void *partial,
                              int R, const int *units, int nunits, int *nchunks_out,
                              cudaStream_t st);
-// partial sums -> alm (with f_l/2, E/B recombination and optional + λ x)
+// partial sums -> alm (with f_l/2, E/B recombination and optional + λ x); fields: bit 0 E,
+// bit 1 B -- a field outside the set is written as zero
 template <typename T>
 akra_status adjoint_epilogue(akra_plan p, LegMode mode, const void *partial, int nchunks,
-                             const void *x_reg, double lam, void *alm_out, int R, cudaStream_t st);
+                             const void *x_reg, double lam, void *alm_out, int R, cudaStream_t st,
+                             int fields = 3);
 
 enum class FftMode { Synth = 0, Adjoint = 1, Happly = 2 };
 template <typename T>

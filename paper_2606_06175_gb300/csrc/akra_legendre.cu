@@ -28,7 +28,7 @@ template <typename T>
 __global__ void k_adj_epilogue(int L, long long ntri, int nchunks, int R,
                                const T *__restrict__ partial, const T *__restrict__ fl,
                                const cx_t<T> *__restrict__ xreg, T lam, cx_t<T> *__restrict__ out,
-                               const int *__restrict__ skip)
+                               const int *__restrict__ skip, int fields)
 {
     if (skip && *skip) return;
     using C2 = cx_t<T>;
@@ -58,6 +58,9 @@ __global__ void k_adj_epilogue(int L, long long ntri, int nchunks, int R,
             B.y += lam * xb.y;
         }
         if (m == 0) E.y = B.y = 0;
+        // a field outside the solve's field set is held at zero (its block row is dropped)
+        if (!(fields & 1)) E = C2{0, 0};
+        if (!(fields & 2)) B = C2{0, 0};
         out[((size_t)r * 2 + 0) * ntri + idx] = E;
         out[((size_t)r * 2 + 1) * ntri + idx] = B;
     }
@@ -168,13 +171,14 @@ akra_status legendre_adjoint(akra_plan p, const LegShape &s, const void *phi, vo
 
 template <typename T>
 akra_status adjoint_epilogue(akra_plan p, LegMode mode, const void *partial, int nchunks,
-                             const void *x_reg, double lam, void *alm_out, int R, cudaStream_t st)
+                             const void *x_reg, double lam, void *alm_out, int R, cudaStream_t st,
+                             int fields)
 {
     dim3 grid(p->lmax + 1, R);
     k_adj_epilogue<T><<<grid, 128, 0, st>>>(p->lmax, p->ntri, nchunks, R, (const T *)partial,
                                             mode == LegMode::KS ? D_ptr<T>(p) : nullptr,
                                             (const cx_t<T> *)x_reg, (T)lam, (cx_t<T> *)alm_out,
-                                            p->cur_skip);
+                                            p->cur_skip, fields);
     AKRA_CUDA_TRY(cudaGetLastError());
     p->launches++;
     return AKRA_OK;
@@ -198,8 +202,8 @@ template akra_status legendre_adjoint<float>(akra_plan, const LegShape &, const 
 template akra_status legendre_adjoint<double>(akra_plan, const LegShape &, const void *, void *, int,
                                               const int *, int, int *, cudaStream_t);
 template akra_status adjoint_epilogue<float>(akra_plan, LegMode, const void *, int, const void *,
-                                             double, void *, int, cudaStream_t);
+                                             double, void *, int, cudaStream_t, int);
 template akra_status adjoint_epilogue<double>(akra_plan, LegMode, const void *, int, const void *,
-                                              double, void *, int, cudaStream_t);
+                                              double, void *, int, cudaStream_t, int);
 
 }  // namespace akra

@@ -327,7 +327,8 @@ akra_status ws_reserve(akra_plan p, Workspace &w, size_t bytes)
 
 size_t plan_device_bytes(akra_plan p)
 {
-    return p->bytes_tables + p->phi.bytes + p->partial.bytes + p->cg.bytes + p->red.bytes;
+    return p->bytes_tables + p->phi.bytes + p->partial.bytes + p->cg.bytes + p->red.bytes +
+           p->xsave.bytes;
 }
 
 LegShape leg_shape(akra_plan p, akra_prec prec, int R)
@@ -398,7 +399,8 @@ akra_status op_H(akra_plan p, const void *x, void *y, int R, cudaStream_t st)
     int nch = 0;
     AKRA_TRY(legendre_adjoint<T>(p, s, p->phi.ptr, p->partial.ptr, R, p->d_active_units,
                                  p->n_active_units, &nch, st));
-    return adjoint_epilogue<T>(p, LegMode::KS, p->partial.ptr, nch, x, p->lambda_eff, y, R, st);
+    return adjoint_epilogue<T>(p, LegMode::KS, p->partial.ptr, nch, x, p->lambda_eff, y, R, st,
+                               p->fields);
 }
 
 template akra_status op_synth<float>(akra_plan, LegMode, const void *, void *, bool, int, cudaStream_t);
@@ -543,7 +545,7 @@ extern "C" void akra_plan_destroy(akra_plan p)
     void *ptrs[] = {p->d_rings, p->d_units, p->d_factors, p->d_coef64, p->d_coef32, p->d_seedC,
                     p->d_D64, p->d_D32, p->d_tw64, p->d_tw32, p->d_all_rings, p->d_all_units,
                     p->d_active_rings, p->d_active_units, p->d_ring_active, p->d_W64, p->d_W32,
-                    p->phi.ptr, p->partial.ptr, p->cg.ptr, p->red.ptr, p->d_fft32_M,
+                    p->phi.ptr, p->partial.ptr, p->cg.ptr, p->red.ptr, p->xsave.ptr, p->d_fft32_M,
                     p->d_fft32_off, p->d_fft32_tw2, p->d_fft32_bhat, p->d_seed32, p->d_seed64,
                     p->d_start32, p->d_start64, p->d_steps,
                     p->d_fft32_rings_all, p->d_fft32_rings_act};

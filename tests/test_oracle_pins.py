@@ -264,6 +264,56 @@ def test_noise_free_pure_E_recovers_input_and_zero_B():
     assert np.max(np.abs(gB)) < 1e-10 * np.abs(xE).max()
 
 
+def test_e_only_solve_equals_dense_EE_block():
+    """App. A: the E-mode solve is the E block of the dense normal matrix, solved directly."""
+    N, L = 8, 10
+    w, rng = _small_problem(N, L)
+    y1, y2 = O.forward_A(N, L, S.random_alm(L, rng, lmin=2), S.random_alm(L, rng, lmin=2))
+    y1 = y1 + 0.01 * rng.normal(size=y1.shape)
+    b = O.rhs_b(N, L, w, y1, y2)
+    H, vecs = O.dense_H(N, L, w)
+    n = H.shape[0] // 2                       # basis: the E field first, then B
+    rhs = np.array([O.pair_dot(L, v, (b[0], np.zeros_like(b[0]))) for v in vecs[:n]])
+    c = np.linalg.solve(np.linalg.cholesky(H[:n, :n]).T,
+                        np.linalg.solve(np.linalg.cholesky(H[:n, :n]), rhs))
+    xE = sum(ci * v[0] for ci, v in zip(c, vecs[:n]))
+    (gE, gB), it, rr, _ = O.cg_solve_E(N, L, w, y1, y2, tol=1e-13, maxiter=500)
+    assert np.max(np.abs(gE - xE)) < 1e-10 * np.abs(xE).max()
+    assert not np.any(gB)
+    # and it differs from the joint solve's E part (the mask couples E and B)
+    (jE, _), _, _, _ = O.cg_solve(N, L, w, y1, y2, tol=1e-13, maxiter=500)
+    assert np.max(np.abs(gE - jE)) > 1e-6 * np.abs(jE).max()
+
+
+def test_conditional_B_given_joint_E_reproduces_joint_B():
+    """Eq. A7 is the lower block row of the joint system, so with κ̂_E of the joint solve the
+    reduced B equation (Eq. A8) returns the joint κ̂_B."""
+    N, L = 8, 12
+    w, rng = _small_problem(N, L)
+    y1, y2 = O.forward_A(N, L, S.random_alm(L, rng, lmin=2), S.random_alm(L, rng, lmin=2))
+    y1 = y1 + 0.01 * rng.normal(size=y1.shape)
+    y2 = y2 + 0.01 * rng.normal(size=y2.shape)
+    (jE, jB), _, _, _ = O.cg_solve(N, L, w, y1, y2, tol=1e-13, maxiter=1000)
+    (zE, cB), it, rr, _ = O.cg_solve_B_given_E(N, L, w, y1, y2, jE, tol=1e-13, maxiter=1000)
+    assert not np.any(zE)
+    assert np.max(np.abs(cB - jB)) < 1e-9 * np.abs(jB).max()
+
+
+def test_e_only_then_conditional_B_on_noise_free_pure_E():
+    """y = A (x_E, 0), λ = 0, full-rank footprint: the E solve returns x_E and the conditional
+    B solve returns zero B (the E-to-B leakage term cancels b_B exactly)."""
+    N, L = 16, 12
+    w, rng = _small_problem(N, L, lam=0.0, cap=0.3)
+    xE = S.random_alm(L, rng, lmin=2)
+    y1, y2 = O.forward_A(N, L, xE, np.zeros_like(xE))
+    (gE, _), _, _, _ = O.cg_solve_E(N, L, w, y1, y2, tol=1e-13, maxiter=2000)
+    assert np.max(np.abs(gE - xE)) < 1e-10 * np.abs(xE).max()
+    _, bB = O.rhs_b(N, L, w, y1, y2)
+    assert np.abs(bB).max() > 1e-3 * np.abs(O.rhs_b(N, L, w, y1, y2)[0]).max()   # b_B is not 0
+    (_, gB), _, rr, _ = O.cg_solve_B_given_E(N, L, w, y1, y2, gE, tol=1e-13, maxiter=2000)
+    assert np.max(np.abs(gB)) < 1e-9 * np.abs(xE).max()
+
+
 def test_full_sky_uniform_weight_is_nearly_diagonal():
     """M ≡ 1, uniform N^-1: H_EB ≈ 0 and H ≈ <N^-1> D_l^2 (App. A), within HEALPix quadrature."""
     N, L = 16, 16
