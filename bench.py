@@ -202,6 +202,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fields", action="store_true",
                     help="also time the E-only solve and the conditional B-mode solve (App. A)")
+    ap.add_argument("--noise-realisations", type=int, default=0, metavar="K",
+                    help="also time the shuffled-noise pipeline with K realisations in one batched solve")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -335,6 +337,24 @@ def main():
                   "b_given_e": {"solve_s": t_b, "inner_iters": ib["iters"], "outer": ib["outer"],
                                 "h_applies_f64": ib["h_applies_f64"], "relres": ib["relres"]}}
 
+    # ---- noise-realisation pipeline (Sec. IV): K shuffled maps as the RHS of one solve ----
+    noise = None
+    if args.noise_realisations > 0:
+        from paper_2606_06175_gb300 import spectra as SP
+        K = args.noise_realisations
+        perms = SP.shuffle_permutations(wl["mask"], K, seed=2024)
+        A.akra_autotune(plan, A.MIXED, K)
+        SP.noise_realisations(plan, A.MIXED, y[0], perms, tol=TOL, maxiter=2000)   # capture
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        bp, _, inf = SP.noise_realisations(plan, A.MIXED, y[0], perms, tol=TOL, maxiter=2000)
+        torch.cuda.synchronize()
+        t_n = time.perf_counter() - t0
+        noise = {"realisations": K, "total_s": t_n, "s_per_realisation": t_n / K,
+                 "inner_iters": inf["iters"], "outer": inf["outer"], "relres": inf["relres"],
+                 "shape_f32": A.akra_plan_get_shape(plan, A.F32, K),
+                 "noise_bias_EE_band_powers": SP.noise_bias(bp)[0][0].cpu().tolist()}
+
     # ---- end to end through the C ABI with host buffers ----
     y_host = y.cpu().pin_memory()
     x_host = torch.empty(x.shape, dtype=x.dtype).pin_memory()
@@ -376,6 +396,8 @@ def main():
     }
     if fields is not None:
         line["fields"] = fields
+    if noise is not None:
+        line["noise_realisations"] = noise
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

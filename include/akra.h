@@ -245,6 +245,29 @@ akra_status akra_cg_solve_fields(akra_plan plan, akra_prec prec, akra_fields fie
                                  const void *d_shear, void *d_x, int R, double tol, int maxiter,
                                  akra_cg_info *info, void *stream);
 
+/* Noise-realisation pipeline, shuffling step (Sec. IV, "Power spectrum results": the observed
+ * shear values are shuffled among the unmasked pixels, which keeps the survey geometry and
+ * noise level and destroys the signal's spatial correlations).  d_shear [2][npix] (γ1, γ2),
+ * d_perm [R][npix] int32 source pixel per output pixel (a permutation of the unmasked pixels
+ * onto themselves, masked pixels mapping to themselves, for the paper's procedure; any gather
+ * is computed as given), d_out [R][2][npix]: out[r][c][p] = shear[c][perm[r][p]].  prec F64 or
+ * F32 selects the map type.  The random permutations are the caller's (the library draws no
+ * random numbers).  Blocking (reads back an index check).  Errors: EINVAL (arguments, or any
+ * perm entry outside [0, npix): those outputs are 0), ENOMEM, ECUDA. */
+akra_status akra_shuffle_shear(akra_plan plan, akra_prec prec, const void *d_shear,
+                               const int *d_perm, void *d_out, int R, void *stream);
+
+/* E/B power spectra of reconstructed convergence alm (Sec. IV, "Power spectrum results"):
+ *   C_l^{XY} = [Re a_X,l0 Re b_Y,l0 + 2 Re Σ_{m>0} a_X,lm conj(b_Y,lm)] / (2l + 1),
+ * for (X, Y) = (E,E), (E,B), (B,E), (B,B), per RHS, accumulated in FP64 -- an auto spectrum with
+ * d_b = d_a, a cross spectrum of two reconstructions otherwise.  d_a, d_b [R][2][ntri] complex
+ * in prec (F64 or F32).  nbins = 0: d_out [R][4][lmax+1] receives C_l; nbins in [1, 64]:
+ * d_out [R][4][nbins] receives band powers, the mean of C_l over l in (edges[b], edges[b+1]]
+ * (0 for a bin holding no l), edges a host array of nbins + 1 increasing values.  Asynchronous
+ * on `stream`.  Errors: EINVAL, ENOMEM (workspace), ECUDA. */
+akra_status akra_cl_spectra(akra_plan plan, akra_prec prec, const void *d_a, const void *d_b, int R,
+                            int nbins, const double *edges, double *d_out, void *stream);
+
 /* Inner tolerance of the mixed-precision solves (Sec. II C: FP32 inner CG, FP64 refinement):
  * each outer step runs FP32 CG on the normalised FP64 residual to the relative tolerance
  * max(floor, min(0.1, inner_factor · tol / (‖r‖/‖b‖))), i.e. to what this step must gain

@@ -539,6 +539,38 @@ def band_power_grad(lmax: int, kE, edges):
     return g
 
 
+def shuffle_shear(y, perm):
+    """Pixel shuffling of the observed shear (Sec. IV, "Power spectrum results"): output pixel
+    p takes the (γ1, γ2) of pixel perm[p]."""
+    y = np.asarray(y)
+    return np.stack([y[0][perm], y[1][perm]])
+
+
+def cl_spectra(lmax: int, a, b):
+    """C_l^{XY} = [Re a_X,l0 Re b_Y,l0 + 2 Re Σ_{m>0} a_X,lm conj(b_Y,lm)]/(2l+1) for
+    (X, Y) = EE, EB, BE, BB (the real-dof inner product of item 3 restricted to one l)."""
+    ls, ms = lm_arrays(lmax)
+    out = np.zeros((4, lmax + 1))
+    for k, (x, y) in enumerate([(a[0], b[0]), (a[0], b[1]), (a[1], b[0]), (a[1], b[1])]):
+        x = np.asarray(x)
+        y = np.asarray(y)
+        prod = np.where(ms == 0, x.real * y.real, 2.0 * (x * np.conj(y)).real)
+        out[k] = np.bincount(ls, weights=prod, minlength=lmax + 1) / (2 * np.arange(lmax + 1) + 1)
+    return out
+
+
+def band_powers(cl, edges):
+    """Mean of C_l over l in (e_b, e_{b+1}] per bin (0 for an empty bin); cl [..., lmax+1]."""
+    cl = np.asarray(cl)
+    ell = np.arange(cl.shape[-1])
+    out = np.zeros(cl.shape[:-1] + (len(edges) - 1,))
+    for b in range(len(edges) - 1):
+        sel = (ell > edges[b]) & (ell <= edges[b + 1])
+        if sel.any():
+            out[..., b] = cl[..., sel].mean(axis=-1)
+    return out
+
+
 def solve_grad(nside: int, lmax: int, ninv, y, lam: float, gfun, tol: float = 1e-13,
                maxiter: int = 5000):
     """x̂ = H^{-1} A^T W y and the gradient of L(x̂) w.r.t. y and N^-1 (λ_eff held fixed).

@@ -54,7 +54,7 @@ EXPORTS = ["akra_plan_create", "akra_plan_destroy", "akra_last_error", "akra_ver
            "akra_weight_grad", "akra_batch_create", "akra_batch_destroy", "akra_batch_autotune",
            "akra_batch_apply_H", "akra_batch_cg_solve", "akra_batch_describe",
            "akra_plan_get_shape", "akra_plan_set_shape", "akra_set_mixed_policy", "akra_fma_rate",
-           "akra_cg_solve_fields"]
+           "akra_cg_solve_fields", "akra_shuffle_shear", "akra_cl_spectra"]
 
 _lib_handle = None
 
@@ -92,6 +92,8 @@ def load(build_if_missing: bool = False):
         "akra_cg_solve_fields": ([vp, i, i, vp, vp, i, d, i, ctypes.POINTER(CgInfo), vp], i),
         "akra_set_timeout": ([d], i),
         "akra_set_mixed_policy": ([d, d], i),
+        "akra_shuffle_shear": ([vp, i, vp, vp, vp, i, vp], i),
+        "akra_cl_spectra": ([vp, i, vp, vp, i, i, ctypes.POINTER(d), vp, vp], i),
         "akra_fma_rate": ([i, ctypes.POINTER(d)], i),
         "akra_autotune": ([vp, i, i, vp], i),
         "akra_plan_get_shape": ([vp, i, i, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)], i),
@@ -357,6 +359,37 @@ def akra_plan_get_shape(plan: Plan, prec: int, R: int = 1) -> dict:
 def akra_plan_set_shape(plan: Plan, prec: int, R: int, P: int, PA: int, RG: int):
     """Force the Legendre tile shape for (prec, R)."""
     _check(load().akra_plan_set_shape(plan.handle, prec, R, P, PA, RG))
+
+
+def akra_shuffle_shear(plan: Plan, prec: int, shear: torch.Tensor, perm: torch.Tensor,
+                       out: torch.Tensor = None, stream=None) -> torch.Tensor:
+    """Gather shear [2, npix] through perm [R, npix] (int32) into [R, 2, npix]."""
+    R = perm.shape[0]
+    _need(shear, (2, plan.npix), _rdtype(prec), "shear")
+    _need(perm, (R, plan.npix), torch.int32, "perm")
+    if out is None:
+        out = torch.empty((R, 2, plan.npix), dtype=_rdtype(prec), device=shear.device)
+    _need(out, (R, 2, plan.npix), _rdtype(prec), "out")
+    _check(load().akra_shuffle_shear(plan.handle, prec, _ptr(shear), _ptr(perm), _ptr(out), R,
+                                     _stream(stream)))
+    return out
+
+
+def akra_cl_spectra(plan: Plan, prec: int, a: torch.Tensor, b: torch.Tensor = None, edges=None,
+                    stream=None) -> torch.Tensor:
+    """E/B auto (b = None) or cross spectra [R, 4, lmax+1] (EE, EB, BE, BB), or band powers
+    [R, 4, nbins] for the given bin edges."""
+    R = a.shape[0]
+    _need(a, (R, 2, plan.ntri), _cdtype(prec), "a")
+    if b is None:
+        b = a
+    _need(b, (R, 2, plan.ntri), _cdtype(prec), "b")
+    nb = 0 if edges is None else len(edges) - 1
+    e = (ctypes.c_double * (nb + 1))(*([] if edges is None else [float(v) for v in edges]))
+    out = torch.empty((R, 4, nb if nb else plan.lmax + 1), dtype=torch.float64, device=a.device)
+    _check(load().akra_cl_spectra(plan.handle, prec, _ptr(a), _ptr(b), R, nb,
+                                  e if nb else None, _ptr(out), _stream(stream)))
+    return out
 
 
 def akra_fma_rate(prec: int) -> float:

@@ -206,6 +206,7 @@ struct akra_plan_s {
     // workspaces (grown on demand)
     akra::Workspace phi, partial, cg, red;
     akra::Workspace xsave;                   // κ_E kept aside by the conditional B-mode solve
+    akra::Workspace red_cl;                  // per-l spectra before binning into band powers
     cudaStream_t stream = nullptr;           // internal stream for captured CG graphs
     cudaEvent_t ev_a = nullptr, ev_b = nullptr;
     std::map<long long, akra::LegShape> shapes;   // key: prec*1000 + R

@@ -328,7 +328,7 @@ akra_status ws_reserve(akra_plan p, Workspace &w, size_t bytes)
 size_t plan_device_bytes(akra_plan p)
 {
     return p->bytes_tables + p->phi.bytes + p->partial.bytes + p->cg.bytes + p->red.bytes +
-           p->xsave.bytes;
+           p->xsave.bytes + p->red_cl.bytes;
 }
 
 LegShape leg_shape(akra_plan p, akra_prec prec, int R)
@@ -545,7 +545,8 @@ extern "C" void akra_plan_destroy(akra_plan p)
     void *ptrs[] = {p->d_rings, p->d_units, p->d_factors, p->d_coef64, p->d_coef32, p->d_seedC,
                     p->d_D64, p->d_D32, p->d_tw64, p->d_tw32, p->d_all_rings, p->d_all_units,
                     p->d_active_rings, p->d_active_units, p->d_ring_active, p->d_W64, p->d_W32,
-                    p->phi.ptr, p->partial.ptr, p->cg.ptr, p->red.ptr, p->xsave.ptr, p->d_fft32_M,
+                    p->phi.ptr, p->partial.ptr, p->cg.ptr, p->red.ptr, p->xsave.ptr, p->red_cl.ptr,
+                    p->d_fft32_M,
                     p->d_fft32_off, p->d_fft32_tw2, p->d_fft32_bhat, p->d_seed32, p->d_seed64,
                     p->d_start32, p->d_start64, p->d_steps,
                     p->d_fft32_rings_all, p->d_fft32_rings_act};

@@ -314,6 +314,57 @@ def test_e_only_then_conditional_B_on_noise_free_pure_E():
     assert np.max(np.abs(gB)) < 1e-9 * np.abs(xE).max()
 
 
+def test_cl_spectra_parseval_single_mode_and_symmetry():
+    """Σ_l (2l+1) C_l^EE = <a_E, a_E> (real-dof metric); a single (l, m>0) mode gives
+    C_l = 2|c|^2/(2l+1); C^EB(a, b) = C^BE(b, a); the binned EE auto spectrum equals the
+    band-power loss of the differentiation workload."""
+    L = 40
+    rng = np.random.default_rng(4)
+    a = (S.random_alm(L, rng), S.random_alm(L, rng))
+    b = (S.random_alm(L, rng), S.random_alm(L, rng))
+    cl = O.cl_spectra(L, a, a)
+    ell = np.arange(L + 1)
+    assert abs(np.sum((2 * ell + 1) * cl[0]) - O.realdof_dot(L, a[0], a[0])) < 1e-10 * np.sum((2 * ell + 1) * cl[0])
+    one = np.zeros(O.ntri(L), np.complex128)
+    one[O.tri_index(L, 5, 3)] = 0.3 - 0.4j
+    c1 = O.cl_spectra(L, (one, one * 0), (one, one * 0))
+    assert abs(c1[0, 5] - 2 * 0.25 / 11) < 1e-15 and np.count_nonzero(c1) == 1
+    ab, ba = O.cl_spectra(L, a, b), O.cl_spectra(L, b, a)
+    assert np.allclose(ab[1], ba[2], rtol=0, atol=1e-14) and np.allclose(ab[0], ba[0], rtol=0, atol=1e-14)
+    edges = np.geomspace(3, 40, 5)
+    assert abs(O.band_powers(cl[0], edges).sum() - O.band_power_loss(L, a[0], edges)) < 1e-12
+
+
+def test_cl_of_gaussian_field_matches_its_power_spectrum():
+    """A Gaussian realisation's C_l averaged over 100 < l <= 300 matches the input C_l within
+    a few times the cosmic-variance error sqrt(2/Σ(2l+1)) (about 0.4 %)."""
+    L = 300
+    rng = np.random.default_rng(11)
+    cl_in = S.cl_kappa(L)
+    aE = S.grf_alm(L, cl_in, rng)
+    cl = O.cl_spectra(L, (aE, 0 * aE), (aE, 0 * aE))[0]
+    sel = np.arange(101, L + 1)
+    ratio = np.sum((2 * sel + 1) * cl[sel]) / np.sum((2 * sel + 1) * cl_in[sel])
+    assert abs(ratio - 1) < 4 * np.sqrt(2.0 / np.sum(2 * sel + 1))
+
+
+def test_shuffle_permutes_only_unmasked_values():
+    from paper_2606_06175_gb300 import spectra as SP
+    N = 8
+    rng = np.random.default_rng(2)
+    mask = rng.random(12 * N * N) < 0.4
+    y = np.where(mask, rng.normal(size=(2, 12 * N * N)), 0.0)
+    perms = SP.shuffle_permutations(mask, 3, seed=9)
+    for r in range(3):
+        z = O.shuffle_shear(y, perms[r])
+        assert not np.any(z[:, ~mask])
+        assert np.array_equal(np.sort(z[0][mask]), np.sort(y[0][mask]))
+        assert np.array_equal(perms[r][~mask], np.nonzero(~mask)[0])
+        # both components move together (a galaxy's shear stays a pair)
+        assert np.array_equal(z[1], y[1][perms[r]])
+    assert not np.array_equal(perms[0], perms[1])
+
+
 def test_full_sky_uniform_weight_is_nearly_diagonal():
     """M ≡ 1, uniform N^-1: H_EB ≈ 0 and H ≈ <N^-1> D_l^2 (App. A), within HEALPix quadrature."""
     N, L = 16, 16
