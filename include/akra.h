@@ -295,7 +295,8 @@ akra_status akra_plan_get_shape(akra_plan plan, akra_prec prec, int R, int *P, i
 
 /* Force the Legendre tile shape for (prec, R), replacing a default or autotuned choice (for
  * reproducible timing, or to test every compiled shape).  Compiled shapes: (P, RG) and
- * (PA, RG) in {(1,1), (2,1), (4,1), (1,2), (2,2), (1,4)}, and for AKRA_F32 also (8,1).
+ * (PA, RG) in {(1,1), (2,1), (4,1), (1,2), (2,2), (1,4)}, and for AKRA_F32 also (3,1), (5,1),
+ * (6,1) and (8,1).
  * The results do not depend on the shape beyond rounding order.  Errors: EINVAL. */
 akra_status akra_plan_set_shape(akra_plan plan, akra_prec prec, int R, int P, int PA, int RG);
 

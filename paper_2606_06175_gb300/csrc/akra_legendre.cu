@@ -141,7 +141,7 @@ akra_status legendre_synth(akra_plan p, const LegShape &s, LegMode mode, const v
         return AKRA_OK;                                                                     \
     }
     AKRA_S(1, 1) AKRA_S(2, 1) AKRA_S(4, 1) AKRA_S(1, 2) AKRA_S(2, 2) AKRA_S(1, 4)
-    if constexpr (std::is_same<T, float>::value) { AKRA_S(8, 1) }
+    if constexpr (std::is_same<T, float>::value) { AKRA_S(3, 1) AKRA_S(5, 1) AKRA_S(6, 1) AKRA_S(8, 1) }
 #undef AKRA_S
     set_error("no synthesis kernel for P=%d RG=%d", s.P, s.RG);
     return AKRA_EINVAL;
@@ -163,7 +163,7 @@ akra_status legendre_adjoint(akra_plan p, const LegShape &s, const void *phi, vo
         return AKRA_OK;                                                                     \
     }
     AKRA_A(1, 1) AKRA_A(2, 1) AKRA_A(4, 1) AKRA_A(1, 2) AKRA_A(2, 2) AKRA_A(1, 4)
-    if constexpr (std::is_same<T, float>::value) { AKRA_A(8, 1) }
+    if constexpr (std::is_same<T, float>::value) { AKRA_A(3, 1) AKRA_A(5, 1) AKRA_A(6, 1) AKRA_A(8, 1) }
 #undef AKRA_A
     set_error("no adjoint kernel for P=%d RG=%d", pa, s.RG);
     return AKRA_EINVAL;

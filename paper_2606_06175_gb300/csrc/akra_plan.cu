@@ -755,7 +755,8 @@ static akra_status tune_one(akra_plan p, akra_prec prec, int R, cudaStream_t st)
         cands.push_back({2, 128, 2});
         cands.push_back({1, 128, 2});
     }
-    if (std::is_same<T, float>::value) cands.push_back({8, 128, 1});
+    if (std::is_same<T, float>::value)
+        for (int pp : {8, 6, 5, 3}) cands.push_back({pp, 128, 1});
     cands.push_back({4, 128, 1});
     cands.push_back({2, 128, 1});
     cands.push_back({1, 128, 1});
@@ -821,7 +822,7 @@ static akra_status tune_one(akra_plan p, akra_prec prec, int R, cudaStream_t st)
 
 static bool shape_compiled(akra_prec prec, int P, int RG)
 {
-    if (RG == 1) return P == 1 || P == 2 || P == 4 || (P == 8 && prec == AKRA_F32);
+    if (RG == 1) return P == 1 || P == 2 || P == 4 || (prec == AKRA_F32 && (P == 3 || P == 5 || P == 6 || P == 8));
     if (RG == 2) return P == 1 || P == 2;
     return RG == 4 && P == 1;
 }
