@@ -202,6 +202,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fields", action="store_true",
                     help="also time the E-only solve and the conditional B-mode solve (App. A)")
+    ap.add_argument("--per-l-precond", action="store_true",
+                    help="also time the mixed solve with the per-l diagonal preconditioner")
     ap.add_argument("--noise-realisations", type=int, default=0, metavar="K",
                     help="also time the shuffled-noise pipeline with K realisations in one batched solve")
     args = ap.parse_args()
@@ -337,6 +339,20 @@ def main():
                   "b_given_e": {"solve_s": t_b, "inner_iters": ib["iters"], "outer": ib["outer"],
                                 "h_applies_f64": ib["h_applies_f64"], "relres": ib["relres"]}}
 
+    # ---- the per-l diagonal preconditioner (beyond the paper's scalar Eq. 15) ----
+    per_l = None
+    if args.per_l_precond:
+        A.akra_plan_set_preconditioner(plan, A.PRECOND_PER_L)
+        xp = torch.empty_like(x)
+        A.akra_cg_solve(plan, A.MIXED, y, xp, tol=TOL, maxiter=2000)   # capture
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, ip = A.akra_cg_solve(plan, A.MIXED, y, xp, tol=TOL, maxiter=2000)
+        torch.cuda.synchronize()
+        per_l = {"solve_s": time.perf_counter() - t0, "inner_iters": ip["iters"], "outer": ip["outer"],
+                 "relres": ip["relres"]}
+        A.akra_plan_set_preconditioner(plan, A.PRECOND_SCALAR)
+
     # ---- noise-realisation pipeline (Sec. IV): K shuffled maps as the RHS of one solve ----
     noise = None
     if args.noise_realisations > 0:
@@ -398,6 +414,8 @@ def main():
         line["fields"] = fields
     if noise is not None:
         line["noise_realisations"] = noise
+    if per_l is not None:
+        line["per_l_preconditioner"] = per_l
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -229,6 +229,16 @@ akra_status akra_batch_cg_solve(akra_batch batch, akra_prec prec, const void *co
 /* Current tile shape (ring pairs per thread, RHS per block) and batched launches so far. */
 akra_status akra_batch_describe(akra_batch batch, int *P, int *RG, long long *launches);
 
+/* Preconditioner of the plan's CG solves.  AKRA_PRECOND_SCALAR (default): the paper's scalar
+ * P = (mean_all(M N^-1) + λ_eff)^-1 of Eq. 15 (for a scalar P the PCG iterates equal the CG
+ * ones).  AKRA_PRECOND_PER_L: the per-l diagonal (mean_all(M N^-1) D_l^2 + λ_eff)^-1, the
+ * uniform-sky diagonal of H with the Eq. 3 kernel (beyond the paper; it equals 1/λ_eff on the
+ * l < 2 modes, which only the regulariser constrains).  Takes effect at the next solve that
+ * involves this plan (single-plan and batched); the weights are recomputed by
+ * akra_plan_set_weights.  Errors: EINVAL. */
+typedef enum { AKRA_PRECOND_SCALAR = 0, AKRA_PRECOND_PER_L = 1 } akra_precond;
+akra_status akra_plan_set_preconditioner(akra_plan plan, akra_precond kind);
+
 /* Field-restricted solves (App. A, "Conditional B-mode solve").  With b = A^T W y as in
  * akra_cg_solve and H_EE, H_BB, H_BE the E/B blocks of the joint operator (Eqs. A3-A6):
  *   AKRA_SOLVE_E: the E-mode normal equations H_EE κ_E = b_E (κ_B held at zero; the B rows

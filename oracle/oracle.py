@@ -328,7 +328,8 @@ class Weights:
         self.W = self.omega * np.where(mask, ninv, 0.0)
         self.lam = lam
         self.lam_eff = lam * (ninv[mask].mean() if mask.any() else 0.0)
-        self.precond = 1.0 / (np.where(mask, ninv, 0.0).mean() + self.lam_eff)
+        self.mean_mninv = np.where(mask, ninv, 0.0).mean()
+        self.precond = 1.0 / (self.mean_mninv + self.lam_eff)
 
 
 def apply_H(nside: int, lmax: int, wts: Weights, kE, kB):
@@ -359,8 +360,11 @@ def pair_dot(lmax, x, y) -> float:
     return realdof_dot(lmax, x[0], y[0]) + realdof_dot(lmax, x[1], y[1])
 
 
-def pcg(apply, b, precond: float, lmax: int, tol: float, maxiter: int, x0=None):
+def pcg(apply, b, precond, lmax: int, tol: float, maxiter: int, x0=None):
     """Preconditioned CG (Saad 2003, as cited in Sec. II B) on pairs (κ_E, κ_B).
+
+    `precond` is the scalar P of Eq. 15 or an array of per-packed-index weights (a diagonal
+    preconditioner applied to both fields).
 
     x_0 = 0, r_0 = b, z = P r, p = z; each step q = H p, α = <r,z>/<p,q>,
     x += α p, r -= α q, stop when ||r||/||b|| < tol, β = <r',z'>/<r,z>, p = z' + β p.
@@ -399,6 +403,15 @@ def pcg(apply, b, precond: float, lmax: int, tol: float, maxiter: int, x0=None):
             break
         pE, pB = zE + beta * pE, zB + beta * pB
     return (xE, xB), it, relres, hist
+
+
+def per_l_preconditioner(lmax: int, wts: Weights):
+    """Per-l diagonal preconditioner (mean_all(M N^-1) D_l^2 + λ_eff)^-1 per packed index: the
+    uniform-sky diagonal of H with the Eq. 3 kernel (beyond the paper's scalar Eq. 15)."""
+    ls, _ = lm_arrays(lmax)
+    D = ks_kernel(lmax)
+    d = wts.mean_mninv * D[ls] ** 2 + wts.lam_eff
+    return np.where(d > 0, 1.0 / np.where(d > 0, d, 1.0), 0.0)
 
 
 def cg_solve(nside: int, lmax: int, wts: Weights, y1, y2, tol: float = 1e-8, maxiter: int = 1000):

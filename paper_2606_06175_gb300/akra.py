@@ -54,7 +54,8 @@ EXPORTS = ["akra_plan_create", "akra_plan_destroy", "akra_last_error", "akra_ver
            "akra_weight_grad", "akra_batch_create", "akra_batch_destroy", "akra_batch_autotune",
            "akra_batch_apply_H", "akra_batch_cg_solve", "akra_batch_describe",
            "akra_plan_get_shape", "akra_plan_set_shape", "akra_set_mixed_policy", "akra_fma_rate",
-           "akra_cg_solve_fields", "akra_shuffle_shear", "akra_cl_spectra"]
+           "akra_cg_solve_fields", "akra_shuffle_shear", "akra_cl_spectra",
+           "akra_plan_set_preconditioner"]
 
 _lib_handle = None
 
@@ -92,6 +93,7 @@ def load(build_if_missing: bool = False):
         "akra_cg_solve_fields": ([vp, i, i, vp, vp, i, d, i, ctypes.POINTER(CgInfo), vp], i),
         "akra_set_timeout": ([d], i),
         "akra_set_mixed_policy": ([d, d], i),
+        "akra_plan_set_preconditioner": ([vp, i], i),
         "akra_shuffle_shear": ([vp, i, vp, vp, vp, i, vp], i),
         "akra_cl_spectra": ([vp, i, vp, vp, i, i, ctypes.POINTER(d), vp, vp], i),
         "akra_fma_rate": ([i, ctypes.POINTER(d)], i),
@@ -281,6 +283,14 @@ def akra_cg_solve(plan: Plan, prec: int, shear: torch.Tensor, out=None, tol: flo
     R = shear.shape[0]
     _need(shear, (R, 2, plan.npix), torch.float32 if prec == F32 else torch.float64, "shear")
     return _solve(load().akra_cg_solve, plan, prec, shear, out, R, tol, maxiter, stream, raise_on_noconv)
+
+
+PRECOND_SCALAR, PRECOND_PER_L = 0, 1
+
+
+def akra_plan_set_preconditioner(plan: Plan, kind: int):
+    """PRECOND_SCALAR (Eq. 15, default) or PRECOND_PER_L (per-l diagonal)."""
+    _check(load().akra_plan_set_preconditioner(plan.handle, kind))
 
 
 SOLVE_E, SOLVE_B_GIVEN_E = 1, 2

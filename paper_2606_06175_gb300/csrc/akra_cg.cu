@@ -22,20 +22,19 @@ namespace akra {
 // vector kernels
 // ---------------------------------------------------------------------------
 template <typename T>
-__device__ __forceinline__ double wdot(long long idx, int L, cx_t<T> a, cx_t<T> b)
+__device__ __forceinline__ double wdot(bool m0, cx_t<T> a, cx_t<T> b)
 {
-    // m = 0 entries (idx <= L inside a field) count once and are real; m > 0 twice
-    return idx <= L ? (double)a.x * (double)b.x
-                    : 2.0 * ((double)a.x * (double)b.x + (double)a.y * (double)b.y);
+    // m = 0 entries count once and are real; m > 0 twice
+    return m0 ? (double)a.x * (double)b.x : 2.0 * ((double)a.x * (double)b.x + (double)a.y * (double)b.y);
 }
 
-// block-reduce one double per RHS into scratch[r * RED_NB + blockIdx.x]; returns true on the
+// block-reduce one double per slot into scratch[k * RED_NB + blockIdx.x]; returns true on the
 // last block to finish (which may then read every partial)
-__device__ bool block_partials(double *vals, int R, double *scratch, CgCtl *ctl)
+__device__ bool block_partials(double *vals, int nslots, double *scratch, CgCtl *ctl)
 {
     __shared__ double sh[RED_NT];
     __shared__ bool last;
-    for (int r = 0; r < R; r++) {
+    for (int r = 0; r < nslots; r++) {
         sh[threadIdx.x] = vals[r];
         __syncthreads();
         for (int off = RED_NT / 2; off > 0; off >>= 1) {
@@ -60,35 +59,56 @@ __device__ double sum_partials(const double *scratch, int r)
 
 constexpr int kMaxRhsLocal = 64;
 
-// initial state: x = 0, r = b, p = P r, rz = P <r,r>, bnorm2 = <b,b>
+// per-element preconditioner weights when the plan uses the per-l diagonal, else nullptr
+template <typename T> static const T *pw_ptr(akra_plan p);
+template <> const double *pw_ptr<double>(akra_plan p) { return p->precond_kind ? p->d_pw64 : nullptr; }
+template <> const float *pw_ptr<float>(akra_plan p) { return p->precond_kind ? p->d_pw32 : nullptr; }
+
+// Grid-stride walk over the packed index j of both fields of RHS r: element o = (2r + f) ntri + j
+// (no division per element); j <= L are the m = 0 entries.
+#define AKRA_FOR_RHS_ELEMENTS(r)                                                                     \
+    for (int f_ = 0; f_ < 2; f_++)                                                                   \
+        for (long long j = blockIdx.x * (long long)RED_NT + threadIdx.x, o = ((long long)(r) * 2 + f_) * ntri + j; \
+             j < ntri; j += (long long)gridDim.x * RED_NT, o += (long long)gridDim.x * RED_NT)
+
+// preconditioner weight of packed index j: the scalar P of Eq. 15, or a per-l diagonal
+template <typename T>
+__device__ __forceinline__ T pweight(const T *pw, long long j, T P)
+{
+    return pw ? pw[j] : P;
+}
+
+// initial state: x = 0, r = b, p = z = P r, rz = <r, z>, bnorm2 = <b,b>
 template <typename T>
 __global__ void __launch_bounds__(RED_NT)
 k_cg_init(int L, long long ntri, const cx_t<T> *b, cx_t<T> *x, cx_t<T> *r, cx_t<T> *p, CgState *st,
-          CgCtl *ctl, double *scratch, double tol, int maxiter)
+          CgCtl *ctl, double *scratch, double tol, int maxiter, const T *pw)
 {
     const int R = ctl->R;
-    const double P = ctl->precond;
-    double acc[kMaxRhsLocal];
-    for (int q = 0; q < R; q++) acc[q] = 0;
-    const long long n = 2 * ntri;
+    const T P = (T)ctl->precond;
+    double acc[2 * kMaxRhsLocal];
     for (int q = 0; q < R; q++) {
-        for (long long i = blockIdx.x * (long long)RED_NT + threadIdx.x; i < n;
-             i += (long long)gridDim.x * RED_NT) {
-            const size_t o = (size_t)q * n + i;
+        double bb = 0, rz = 0;
+        AKRA_FOR_RHS_ELEMENTS(q) {
             const cx_t<T> v = b[o];
+            const T w = pweight(pw, j, P);
+            const cx_t<T> z{w * v.x, w * v.y};
             x[o] = cx_t<T>{0, 0};
             r[o] = v;
-            p[o] = cx_t<T>{(T)(P * v.x), (T)(P * v.y)};
-            acc[q] += wdot<T>(i % ntri, L, v, v);
+            p[o] = z;
+            bb += wdot<T>(j <= L, v, v);
+            rz += wdot<T>(j <= L, v, z);
         }
+        acc[2 * q] = bb;
+        acc[2 * q + 1] = rz;
     }
-    if (block_partials(acc, R, scratch, ctl)) {
+    if (block_partials(acc, 2 * R, scratch, ctl)) {
         for (int q = threadIdx.x; q < R; q += RED_NT) {
-            const double bb = sum_partials(scratch, q);
+            const double bb = sum_partials(scratch, 2 * q);
             CgState s{};
             s.bnorm2 = bb;
             s.rr = bb;
-            s.rz = P * bb;
+            s.rz = sum_partials(scratch, 2 * q + 1);
             s.tol = tol;
             s.relres = bb > 0 ? 1.0 : 0.0;
             s.done = bb > 0 ? 0 : 1;
@@ -119,15 +139,12 @@ k_cg_dot_pq(int L, long long ntri, const cx_t<T> *p, const cx_t<T> *q, CgState *
     if (ctl->all_done) return;
     const int R = ctl->R;
     double acc[kMaxRhsLocal];
-    const long long n = 2 * ntri;
     for (int r = 0; r < R; r++) {
-        acc[r] = 0;
-        if (st[r].done) continue;
-        for (long long i = blockIdx.x * (long long)RED_NT + threadIdx.x; i < n;
-             i += (long long)gridDim.x * RED_NT) {
-            const size_t o = (size_t)r * n + i;
-            acc[r] += wdot<T>(i % ntri, L, p[o], q[o]);
+        double a = 0;
+        if (!st[r].done) {
+            AKRA_FOR_RHS_ELEMENTS(r) a += wdot<T>(j <= L, p[o], q[o]);
         }
+        acc[r] = a;
     }
     if (block_partials(acc, R, scratch, ctl)) {
         for (int r = threadIdx.x; r < R; r += RED_NT) {
@@ -146,44 +163,46 @@ k_cg_dot_pq(int L, long long ntri, const cx_t<T> *p, const cx_t<T> *q, CgState *
     }
 }
 
-// x += α p, r -= α q, <r,r> -> relres, stop test, β
+// x += α p, r -= α q, <r,r> -> relres, stop test, <r, P r> -> β
 template <typename T>
 __global__ void __launch_bounds__(RED_NT)
 k_cg_update_xr(int L, long long ntri, const cx_t<T> *p, const cx_t<T> *q, cx_t<T> *x, cx_t<T> *rv,
-               CgState *st, CgCtl *ctl, double *scratch)
+               CgState *st, CgCtl *ctl, double *scratch, const T *pw)
 {
     if (ctl->all_done) return;
     const int R = ctl->R;
-    double acc[kMaxRhsLocal];
-    const long long n = 2 * ntri;
+    double acc[2 * kMaxRhsLocal];
     for (int r = 0; r < R; r++) {
-        acc[r] = 0;
-        if (st[r].done) continue;
-        const T a = (T)st[r].alpha;
-        for (long long i = blockIdx.x * (long long)RED_NT + threadIdx.x; i < n;
-             i += (long long)gridDim.x * RED_NT) {
-            const size_t o = (size_t)r * n + i;
-            const cx_t<T> pv = p[o], qv = q[o];
-            cx_t<T> xv = x[o], rr = rv[o];
-            xv.x = fma(a, pv.x, xv.x);
-            xv.y = fma(a, pv.y, xv.y);
-            rr.x = fma(-a, qv.x, rr.x);
-            rr.y = fma(-a, qv.y, rr.y);
-            x[o] = xv;
-            rv[o] = rr;
-            acc[r] += wdot<T>(i % ntri, L, rr, rr);
+        double a = 0, az = 0;
+        if (!st[r].done) {
+            const T al = (T)st[r].alpha;
+            AKRA_FOR_RHS_ELEMENTS(r) {
+                const cx_t<T> pv = p[o], qv = q[o];
+                cx_t<T> xv = x[o], rr = rv[o];
+                xv.x = fma(al, pv.x, xv.x);
+                xv.y = fma(al, pv.y, xv.y);
+                rr.x = fma(-al, qv.x, rr.x);
+                rr.y = fma(-al, qv.y, rr.y);
+                x[o] = xv;
+                rv[o] = rr;
+                const double d = wdot<T>(j <= L, rr, rr);
+                a += d;
+                if (pw) az += (double)pw[j] * d;
+            }
         }
+        acc[2 * r] = a;
+        acc[2 * r + 1] = az;
     }
-    if (block_partials(acc, R, scratch, ctl)) {
+    if (block_partials(acc, 2 * R, scratch, ctl)) {
         const double P = ctl->precond;
         for (int r = threadIdx.x; r < R; r += RED_NT) {
             CgState s = st[r];
             if (s.done) continue;
-            const double rr = sum_partials(scratch, r);
+            const double rr = sum_partials(scratch, 2 * r);
             s.rr = rr;
             s.iters += 1;
             s.relres = sqrt(rr / s.bnorm2);
-            const double rz_new = P * rr;
+            const double rz_new = pw ? sum_partials(scratch, 2 * r + 1) : P * rr;
             s.beta = rz_new / s.rz;
             s.rz = rz_new;
             if (!isfinite(rr)) {
@@ -210,22 +229,21 @@ k_cg_update_xr(int L, long long ntri, const cx_t<T> *p, const cx_t<T> *q, cx_t<T
 // p = P r + β p
 template <typename T>
 __global__ void __launch_bounds__(RED_NT)
-k_cg_update_p(long long ntri, const cx_t<T> *rv, cx_t<T> *p, const CgState *st, const CgCtl *ctl)
+k_cg_update_p(long long ntri, const cx_t<T> *rv, cx_t<T> *p, const CgState *st, const CgCtl *ctl,
+              const T *pw)
 {
     if (ctl->all_done) return;
     const int R = ctl->R;
     const T P = (T)ctl->precond;
-    const long long n = 2 * ntri;
     for (int r = 0; r < R; r++) {
         if (st[r].done) continue;
         const T b = (T)st[r].beta;
-        for (long long i = blockIdx.x * (long long)RED_NT + threadIdx.x; i < n;
-             i += (long long)gridDim.x * RED_NT) {
-            const size_t o = (size_t)r * n + i;
+        AKRA_FOR_RHS_ELEMENTS(r) {
+            const T w = pweight(pw, j, P);
             const cx_t<T> rr = rv[o];
             cx_t<T> pv = p[o];
-            pv.x = fma(b, pv.x, P * rr.x);
-            pv.y = fma(b, pv.y, P * rr.y);
+            pv.x = fma(b, pv.x, w * rr.x);
+            pv.y = fma(b, pv.y, w * rr.y);
             p[o] = pv;
         }
     }
@@ -238,18 +256,17 @@ k_residual(int L, long long ntri, int R, const cx_t<T> *b, const cx_t<T> *h, cx_
            double *res, CgCtl *ctl, double *scratch)
 {
     double acc[2 * kMaxRhsLocal];
-    const long long n = 2 * ntri;
     for (int r = 0; r < R; r++) {
-        acc[2 * r] = acc[2 * r + 1] = 0;
-        for (long long i = blockIdx.x * (long long)RED_NT + threadIdx.x; i < n;
-             i += (long long)gridDim.x * RED_NT) {
-            const size_t o = (size_t)r * n + i;
+        double a = 0, ab = 0;
+        AKRA_FOR_RHS_ELEMENTS(r) {
             const cx_t<T> bv = b[o], hv = h[o];
             const cx_t<T> d{bv.x - hv.x, bv.y - hv.y};
             if (out) out[o] = d;
-            acc[2 * r] += wdot<T>(i % ntri, L, d, d);
-            acc[2 * r + 1] += wdot<T>(i % ntri, L, bv, bv);
+            a += wdot<T>(j <= L, d, d);
+            ab += wdot<T>(j <= L, bv, bv);
         }
+        acc[2 * r] = a;
+        acc[2 * r + 1] = ab;
     }
     if (block_partials(acc, 2 * R, scratch, ctl)) {
         for (int q = threadIdx.x; q < 2 * R; q += RED_NT) res[q] = sum_partials(scratch, q);
@@ -356,15 +373,7 @@ static akra_status cg_graph(akra_plan p, int R, CgBufs &b, cudaGraphExec_t *out)
     akra_status s1 = op_H<T>(p, v[3], v[4], R, cs);
     p->cur_skip = nullptr;
     p->launches = launched_before;
-    if (s1 == AKRA_OK) {
-        k_cg_dot_pq<T><<<RED_NB, RED_NT, 0, cs>>>(p->lmax, p->ntri, (const cx_t<T> *)v[3],
-                                                  (const cx_t<T> *)v[4], st, ctl, b.scratch);
-        k_cg_update_xr<T><<<RED_NB, RED_NT, 0, cs>>>(p->lmax, p->ntri, (const cx_t<T> *)v[3],
-                                                     (const cx_t<T> *)v[4], (cx_t<T> *)v[1],
-                                                     (cx_t<T> *)v[2], st, ctl, b.scratch);
-        k_cg_update_p<T><<<RED_NB, RED_NT, 0, cs>>>(p->ntri, (const cx_t<T> *)v[2], (cx_t<T> *)v[3],
-                                                    st, ctl);
-    }
+    if (s1 == AKRA_OK) s1 = cg_launch_tail<T>(p, b, cs);
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamEndCapture(cs, &graph);
     if (s1 != AKRA_OK) {
@@ -427,16 +436,7 @@ static akra_status cg_run(akra_plan p, int R, CgBufs &b, double tol, int maxiter
     CgState *st = b.st[PrecIdx<T>::v];
     CgCtl *ctl = b.ctl[PrecIdx<T>::v];
     cudaStream_t cs = p->stream;
-    CgCtl hctl{};
-    hctl.R = R;
-    hctl.precond = p->precond;
-    hctl.maxiter = maxiter;
-    AKRA_CUDA_TRY(cudaMemcpyAsync(ctl, &hctl, sizeof(CgCtl), cudaMemcpyHostToDevice, cs));
-    k_cg_init<T><<<RED_NB, RED_NT, 0, cs>>>(p->lmax, p->ntri, (const cx_t<T> *)v[0], (cx_t<T> *)v[1],
-                                            (cx_t<T> *)v[2], (cx_t<T> *)v[3], st, ctl, b.scratch, tol,
-                                            maxiter);
-    AKRA_CUDA_TRY(cudaGetLastError());
-    p->launches++;
+    AKRA_TRY(cg_launch_init<T>(p, R, b, tol, maxiter, cs));
     int *h_done = (int *)p->h_pinned;
     int launched = 0;
     int chunk = 2;
@@ -627,7 +627,7 @@ akra_status cg_launch_init(akra_plan p, int R, CgBufs &b, double tol, int maxite
     AKRA_CUDA_TRY(cudaMemcpyAsync(ctl, &hctl, sizeof(CgCtl), cudaMemcpyHostToDevice, cs));
     k_cg_init<T><<<RED_NB, RED_NT, 0, cs>>>(p->lmax, p->ntri, (const cx_t<T> *)v[0], (cx_t<T> *)v[1],
                                             (cx_t<T> *)v[2], (cx_t<T> *)v[3], st, ctl, b.scratch, tol,
-                                            maxiter);
+                                            maxiter, pw_ptr<T>(p));
     AKRA_CUDA_TRY(cudaGetLastError());
     p->launches++;
     return AKRA_OK;
@@ -643,8 +643,9 @@ akra_status cg_launch_tail(akra_plan p, CgBufs &b, cudaStream_t cs)
                                               (const cx_t<T> *)v[4], st, ctl, b.scratch);
     k_cg_update_xr<T><<<RED_NB, RED_NT, 0, cs>>>(p->lmax, p->ntri, (const cx_t<T> *)v[3],
                                                  (const cx_t<T> *)v[4], (cx_t<T> *)v[1],
-                                                 (cx_t<T> *)v[2], st, ctl, b.scratch);
-    k_cg_update_p<T><<<RED_NB, RED_NT, 0, cs>>>(p->ntri, (const cx_t<T> *)v[2], (cx_t<T> *)v[3], st, ctl);
+                                                 (cx_t<T> *)v[2], st, ctl, b.scratch, pw_ptr<T>(p));
+    k_cg_update_p<T><<<RED_NB, RED_NT, 0, cs>>>(p->ntri, (const cx_t<T> *)v[2], (cx_t<T> *)v[3], st, ctl,
+                                                pw_ptr<T>(p));
     AKRA_CUDA_TRY(cudaGetLastError());
     return AKRA_OK;
 }

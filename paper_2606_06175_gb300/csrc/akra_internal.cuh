@@ -192,6 +192,12 @@ struct akra_plan_s {
     // fields H acts on inside a field-restricted solve (bit 0 E, bit 1 B); 3 everywhere else
     int fields = 3;
 
+    // preconditioner: 0 = the scalar P of Eq. 15, 1 = the per-l diagonal
+    // (mean_all(M N^-1) D_l^2 + λ_eff)^-1, as weights per packed index in d_pw64 / d_pw32
+    int precond_kind = 0;
+    double *d_pw64 = nullptr;
+    float *d_pw32 = nullptr;
+
     // weights
     bool has_weights = false;
     double lambda = 0, lambda_eff = 0, precond = 1, omega = 0;

@@ -247,6 +247,19 @@ __global__ void k_twiddles(int N, double2 *tw64, float2 *tw32)
     }
 }
 
+// per-l preconditioner weights per packed index: (mean_all(M N^-1) D_l^2 + λ_eff)^-1
+__global__ void k_pw(int L, const double *D, double mean_mninv, double lam_eff, double *pw64, float *pw32)
+{
+    const int m = blockIdx.x;
+    const long long mbase = (long long)m * (2 * L + 1 - m) / 2;
+    for (int l = m + threadIdx.x; l <= L; l += blockDim.x) {
+        const double d = mean_mninv * D[l] * D[l] + lam_eff;
+        const double w = d > 0 ? 1.0 / d : 0.0;
+        pw64[mbase + l] = w;
+        pw32[mbase + l] = (float)w;
+    }
+}
+
 __global__ void k_iota(int n, int *out)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -460,6 +473,8 @@ static akra_status plan_build(akra_plan p)
     AKRA_TRY(dev_alloc(p, &p->d_ring_active, p->nring));
     AKRA_TRY(dev_alloc(p, &p->d_W64, sizeof(double) * p->npix));
     AKRA_TRY(dev_alloc(p, &p->d_W32, sizeof(float) * p->npix));
+    AKRA_TRY(dev_alloc(p, &p->d_pw64, sizeof(double) * p->ntri));
+    AKRA_TRY(dev_alloc(p, &p->d_pw32, sizeof(float) * p->ntri));
 
     std::vector<FftFactors> fac(N + 1);
     for (int i = 1; i <= N; i++) fac[i] = factorize(4 * i);
@@ -548,7 +563,7 @@ extern "C" void akra_plan_destroy(akra_plan p)
                     p->phi.ptr, p->partial.ptr, p->cg.ptr, p->red.ptr, p->xsave.ptr, p->red_cl.ptr,
                     p->d_fft32_M,
                     p->d_fft32_off, p->d_fft32_tw2, p->d_fft32_bhat, p->d_seed32, p->d_seed64,
-                    p->d_start32, p->d_start64, p->d_steps,
+                    p->d_start32, p->d_start64, p->d_steps, p->d_pw64, p->d_pw32,
                     p->d_fft32_rings_all, p->d_fft32_rings_act};
     for (void *q : ptrs)
         if (q) cudaFree(q);
@@ -658,6 +673,10 @@ extern "C" akra_status akra_plan_set_weights(akra_plan p, const double *d_ninv, 
     p->lambda_eff = cnt > 0 ? lambda * sum / cnt : 0.0;
     p->precond = 1.0 / (sum / (double)p->npix + p->lambda_eff);
     if (!std::isfinite(p->precond)) p->precond = 1.0;
+    k_pw<<<p->lmax + 1, 128, 0, st>>>(p->lmax, p->d_D64, sum / (double)p->npix, p->lambda_eff, p->d_pw64,
+                                      p->d_pw32);
+    AKRA_CUDA_TRY(cudaGetLastError());
+    AKRA_CUDA_TRY(cudaStreamSynchronize(st));
     p->has_weights = true;
     p->ws_gen++;   // captured CG iterations hold the previous active lists and λ_eff
     return ring_fft32_order(p, rings, p->d_fft32_rings_act, &p->fft32_nsmall_act);
@@ -838,6 +857,17 @@ extern "C" akra_status akra_plan_get_shape(akra_plan p, akra_prec prec, int R, i
     *P = s.P;
     *PA = s.adjP();
     *RG = s.RG;
+    return AKRA_OK;
+}
+
+extern "C" akra_status akra_plan_set_preconditioner(akra_plan p, akra_precond kind)
+{
+    if (!p || (kind != AKRA_PRECOND_SCALAR && kind != AKRA_PRECOND_PER_L)) {
+        set_error("akra_plan_set_preconditioner: invalid argument");
+        return AKRA_EINVAL;
+    }
+    p->precond_kind = kind == AKRA_PRECOND_PER_L ? 1 : 0;
+    p->ws_gen++;   // captured CG iterations hold the previous weights
     return AKRA_OK;
 }
 

@@ -290,6 +290,34 @@ def test_cg_solve_b_equals_cg_solve(cap32_ref):
     assert rel(x[0].cpu().numpy(), xref) < TOL64
 
 
+@pytest.mark.parametrize("prec,tol,bound", [(A.F64, 1e-12, TOL64), (A.MIXED, 1e-9, 1e-6)])
+def test_per_l_preconditioner_matches_oracle(cap32_ref, prec, tol, bound):
+    """The per-l diagonal preconditioner: same solution as the oracle's PCG with the same
+    weights, FP64 iteration count equal up to rounding; switching back restores Eq. 15."""
+    wl, N, L, y, xref, it_ref, _ = cap32_ref
+    w = O.Weights(N, wl["ninv"], 1e-3)
+    Pl = O.per_l_preconditioner(L, w)
+    b = O.rhs_b(N, L, w, y[0], y[1])
+    (oE, oB), it_o, _, _ = O.pcg(lambda e, bb: O.apply_H(N, L, w, e, bb), b, Pl, L, 1e-12, 3000)
+    p = A.akra_plan_create(N, L)
+    A.akra_plan_set_weights(p, torch.from_numpy(wl["ninv"]).to(DEV), 1e-3)
+    yd = torch.from_numpy(y[None]).to(DEV)
+    A.akra_cg_solve(p, prec, yd, tol=tol, maxiter=3000)          # scalar form captured first
+    A.akra_plan_set_preconditioner(p, A.PRECOND_PER_L)
+    x, info = A.akra_cg_solve(p, prec, yd, tol=tol, maxiter=3000)
+    assert info["status"] == 0 and info["relres"] < tol
+    assert rel(x[0].cpu().numpy(), np.stack([oE, oB])) < bound
+    if prec == A.F64:
+        assert abs(info["iters"] - it_o) <= 2
+    A.akra_plan_set_preconditioner(p, A.PRECOND_SCALAR)
+    x2, info2 = A.akra_cg_solve(p, prec, yd, tol=tol, maxiter=3000)
+    assert rel(x2[0].cpu().numpy(), xref) < bound
+    if prec == A.F64:
+        assert abs(info2["iters"] - it_ref) <= 2
+    with pytest.raises(A.AkraError):
+        A.akra_plan_set_preconditioner(p, 7)
+
+
 def test_reweighting_after_a_solve(cap32_ref):
     """New weights (another footprint, so other active rings and λ_eff) after solves whose
     CG iterations were captured: the next solves use the new operator."""

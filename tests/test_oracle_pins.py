@@ -252,6 +252,24 @@ def test_cg_equals_dense_cholesky():
     assert np.max(np.abs(gB - cB)) < 1e-10 * scale
 
 
+def test_per_l_preconditioned_cg_equals_dense_cholesky():
+    """A diagonal preconditioner changes the iterates, not the solution: PCG with the per-l
+    weights (mean_all(M N^-1) D_l^2 + λ_eff)^-1 reaches the dense Cholesky solution."""
+    N, L = 8, 10
+    w, rng = _small_problem(N, L)
+    y1, y2 = O.forward_A(N, L, S.random_alm(L, rng, lmin=2), S.random_alm(L, rng, lmin=2))
+    y1 = y1 + 0.01 * rng.normal(size=y1.shape)
+    b = O.rhs_b(N, L, w, y1, y2)
+    (cE, cB), _ = O.cholesky_solve(N, L, w, b)
+    P = O.per_l_preconditioner(L, w)
+    ls, _ = O.lm_arrays(L)
+    assert np.allclose(P[ls < 2], 1.0 / w.lam_eff)
+    assert np.allclose(P[ls == 2], 1.0 / (w.mean_mninv * 2.0 / 3.0 + w.lam_eff))
+    (gE, gB), it, rr, _ = O.pcg(lambda e, bb: O.apply_H(N, L, w, e, bb), b, P, L, 1e-13, 500)
+    scale = max(np.abs(cE).max(), np.abs(cB).max())
+    assert np.max(np.abs(gE - cE)) < 1e-10 * scale and np.max(np.abs(gB - cB)) < 1e-10 * scale
+
+
 def test_noise_free_pure_E_recovers_input_and_zero_B():
     """y = A x_true with κ_B = 0, λ = 0 and a full-rank footprint: x̂ = x_true, κ̂_B = 0."""
     N, L = 16, 12
