@@ -181,7 +181,7 @@ static akra_status batch_H32(akra_batch b, void *const *x, void *const *y, const
 {
     AKRA_CUDA_TRY(cudaMemsetAsync(b->d_counter, 0, 2 * sizeof(int), st));
     AKRA_TRY(launch_queue(b, 0, st));
-    const size_t smem = (size_t)(b->fft_mmax + F32_NT) * sizeof(float2);
+    const size_t smem = (size_t)(f32_slots(b->fft_mmax) + F32_NT) * sizeof(float2);
     if (smem > b->fft_smem_set) {
         // the attribute belongs to this translation unit's instance of the kernel
         AKRA_CUDA_TRY(cudaFuncSetAttribute(k_ring_fft32_batch<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -34,12 +34,12 @@ k_bhat32(int N, const int *__restrict__ fftM, const long long *__restrict__ bhat
             const double2 c = tw[(int)(((long long)jj * jj) % (2 * n))];
             v = make_float2((float)c.x, (float)c.y);
         }
-        buf[j] = v;
+        buf[pd(j)] = v;
     }
     __syncthreads();
     dif<-1>(buf, M, 31 - __clz(M), tw2);
     float2 *out = bhat_all + bhat_off[i];
-    for (int j = threadIdx.x; j < M; j += blockDim.x) out[j] = buf[j];
+    for (int j = threadIdx.x; j < M; j += blockDim.x) out[j] = buf[pd(j)];
 }
 
 __global__ void k_tw2(float2 *tw2)
@@ -105,18 +105,18 @@ akra_status ring_fft32_build(akra_plan p)
     k_tw2<<<(F32_MMAX + 255) / 256, 256>>>(p->d_fft32_tw2);
     AKRA_CUDA_TRY(cudaGetLastError());
     // kernel attributes are shared by every plan: clear the largest supported length
-    const int smem_b = mmax * (int)sizeof(float2);
+    const int smem_b = f32_slots(mmax) * (int)sizeof(float2);
     AKRA_CUDA_TRY(cudaFuncSetAttribute(k_bhat32, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       F32_MMAX * (int)sizeof(float2)));
+                                       f32_slots(F32_MMAX) * (int)sizeof(float2)));
     k_bhat32<<<N, F32_NT, smem_b>>>(N, p->d_fft32_M, p->d_fft32_off, p->d_tw64, p->d_fft32_tw2,
                                     p->d_fft32_bhat);
     AKRA_CUDA_TRY(cudaGetLastError());
-    const int smem = (F32_MMAX + F32_NT) * (int)sizeof(float2);
+    const int smem = (f32_slots(F32_MMAX) + F32_NT) * (int)sizeof(float2);
     AKRA_CUDA_TRY(cudaFuncSetAttribute(k_ring_fft32<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     AKRA_CUDA_TRY(cudaFuncSetAttribute(k_ring_fft32<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     AKRA_CUDA_TRY(cudaFuncSetAttribute(k_ring_fft32<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     AKRA_CUDA_TRY(cudaFuncSetAttribute(k_ring_fft32_batch<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (F32_MMAX + F32_NT) * (int)sizeof(float2)));
+                                       (f32_slots(F32_MMAX) + F32_NT) * (int)sizeof(float2)));
     return AKRA_OK;
 }
 
@@ -183,7 +183,7 @@ akra_status ring_fft32(akra_plan p, FftMode mode, void *phi, const void *map_in,
         if (cnt <= 0) continue;
         a.rings = list + (part == 0 ? 0 : nsmall);
         a.mmax = part == 0 ? p->fft32_msmall : p->fft32_mmax;   // buffer length; scratch follows it
-        const size_t smem = (size_t)(a.mmax + F32_NT) * sizeof(float2);
+        const size_t smem = (size_t)(f32_slots(a.mmax) + F32_NT) * sizeof(float2);
         dim3 grid(cnt, R);
 #define AKRA_F32_LAUNCH(MD) k_ring_fft32<MD><<<grid, F32_NT, smem, st>>>(a)
         switch (mode) {

@@ -33,6 +33,11 @@ __device__ __forceinline__ float2 w_pow2(const float2 *__restrict__ tw2, int t, 
     return w;
 }
 
+// Shared-memory slot of element i: one float2 of padding after every 16, so that the radix-4
+// passes with element strides 1 and 4 (and every larger power of two) hit distinct banks.
+__host__ __device__ constexpr int f32_slots(int m) { return m + (m >> 4); }
+__device__ __forceinline__ int pd(int i) { return i + (i >> 4); }
+
 // in-place DIF with DFT sign S: natural order in, bit-reversed out
 template <int S>
 __device__ void dif(float2 *x, int M, int logM, const float2 *__restrict__ tw2)
@@ -41,9 +46,9 @@ __device__ void dif(float2 *x, int M, int logM, const float2 *__restrict__ tw2)
     if (logM & 1) {
         const int h = M >> 1;
         for (int i = threadIdx.x; i < h; i += blockDim.x) {
-            const float2 a = x[i], b = x[i + h];
-            x[i] = cadd(a, b);
-            x[i + h] = cm(csub(a, b), w_pow2<S>(tw2, i, M));
+            const float2 a = x[pd(i)], b = x[pd(i + h)];
+            x[pd(i)] = cadd(a, b);
+            x[pd(i + h)] = cm(csub(a, b), w_pow2<S>(tw2, i, M));
         }
         __syncthreads();
         L = h;
@@ -52,16 +57,16 @@ __device__ void dif(float2 *x, int M, int logM, const float2 *__restrict__ tw2)
         const int q = L >> 2;
         for (int b = threadIdx.x; b < (M >> 2); b += blockDim.x) {
             const int blk = b / q, i = b - blk * q;
-            float2 *p = x + blk * L + i;
-            const float2 a0 = p[0], a1 = p[q], a2 = p[2 * q], a3 = p[3 * q];
+            const int t = blk * L + i;
+            const float2 a0 = x[pd(t)], a1 = x[pd(t + q)], a2 = x[pd(t + 2 * q)], a3 = x[pd(t + 3 * q)];
             const float2 w1 = w_pow2<S>(tw2, i, L), w2 = w_pow2<S>(tw2, 2 * i, L),
                          w3 = w_pow2<S>(tw2, 3 * i, L);
             const float2 u0 = cadd(a0, a2), u1 = cadd(a1, a3), d0 = csub(a0, a2);
             const float2 d1 = mul_si<S>(csub(a1, a3));
-            p[0] = cadd(u0, u1);
-            p[q] = cm(csub(u0, u1), w2);
-            p[2 * q] = cm(cadd(d0, d1), w1);
-            p[3 * q] = cm(csub(d0, d1), w3);
+            x[pd(t)] = cadd(u0, u1);
+            x[pd(t + q)] = cm(csub(u0, u1), w2);
+            x[pd(t + 2 * q)] = cm(cadd(d0, d1), w1);
+            x[pd(t + 3 * q)] = cm(csub(d0, d1), w3);
         }
         __syncthreads();
     }
@@ -76,27 +81,27 @@ __device__ void dit(float2 *x, int M, int logM, const float2 *__restrict__ tw2)
         const int q = L >> 2;
         for (int b = threadIdx.x; b < (M >> 2); b += blockDim.x) {
             const int blk = b / q, i = b - blk * q;
-            float2 *p = x + blk * L + i;
-            const float2 p0 = p[0], p1 = p[q], p2 = p[2 * q], p3 = p[3 * q];
+            const int t = blk * L + i;
+            const float2 p0 = x[pd(t)], p1 = x[pd(t + q)], p2 = x[pd(t + 2 * q)], p3 = x[pd(t + 3 * q)];
             const float2 w1 = w_pow2<S>(tw2, i, L), w2 = w_pow2<S>(tw2, 2 * i, L);
-            float2 t = cm(p1, w2);
-            const float2 u0 = cadd(p0, t), u1 = csub(p0, t);
-            t = cm(p3, w2);
-            const float2 u2 = cadd(p2, t), u3 = csub(p2, t);
+            float2 u = cm(p1, w2);
+            const float2 u0 = cadd(p0, u), u1 = csub(p0, u);
+            u = cm(p3, w2);
+            const float2 u2 = cadd(p2, u), u3 = csub(p2, u);
             const float2 v2 = cm(u2, w1), v3 = mul_si<S>(cm(u3, w1));
-            p[0] = cadd(u0, v2);
-            p[2 * q] = csub(u0, v2);
-            p[q] = cadd(u1, v3);
-            p[3 * q] = csub(u1, v3);
+            x[pd(t)] = cadd(u0, v2);
+            x[pd(t + 2 * q)] = csub(u0, v2);
+            x[pd(t + q)] = cadd(u1, v3);
+            x[pd(t + 3 * q)] = csub(u1, v3);
         }
         __syncthreads();
     }
     if (logM & 1) {
         const int h = M >> 1;
         for (int i = threadIdx.x; i < h; i += blockDim.x) {
-            const float2 a = x[i], b = cm(x[i + h], w_pow2<S>(tw2, i, M));
-            x[i] = cadd(a, b);
-            x[i + h] = csub(a, b);
+            const float2 a = x[pd(i)], b = cm(x[pd(i + h)], w_pow2<S>(tw2, i, M));
+            x[pd(i)] = cadd(a, b);
+            x[pd(i + h)] = csub(a, b);
         }
         __syncthreads();
     }
@@ -112,25 +117,25 @@ __device__ void bluestein(float2 *x, int n, int M, int logM, const float2 *__res
     for (int j = threadIdx.x; j < M; j += blockDim.x) {
         if (j < n) {
             const float2 c = tw_ring[(int)(((long long)j * j) % n2)];
-            const float2 v = x[j];
+            const float2 v = x[pd(j)];
             // forward: x conj(c);  backward: conj(x c) (conjugation trick)
-            x[j] = S < 0 ? cmc(v, c) : make_float2(v.x * c.x - v.y * c.y, -(v.x * c.y + v.y * c.x));
+            x[pd(j)] = S < 0 ? cmc(v, c) : make_float2(v.x * c.x - v.y * c.y, -(v.x * c.y + v.y * c.x));
         } else {
-            x[j] = make_float2(0.f, 0.f);
+            x[pd(j)] = make_float2(0.f, 0.f);
         }
     }
     __syncthreads();
     dif<-1>(x, M, logM, tw2);
-    for (int k = threadIdx.x; k < M; k += blockDim.x) x[k] = cm(x[k], bhat[k]);
+    for (int k = threadIdx.x; k < M; k += blockDim.x) x[pd(k)] = cm(x[pd(k)], bhat[k]);
     __syncthreads();
     dit<+1>(x, M, logM, tw2);
     const float inv = 1.0f / (float)M;
     for (int k = threadIdx.x; k < n; k += blockDim.x) {
         const float2 c = tw_ring[(int)(((long long)k * k) % n2)];
-        const float2 y = x[k];
+        const float2 y = x[pd(k)];
         // forward: conj(c) y / M;  backward: c conj(y) / M
         const float2 r = S < 0 ? cmc(y, c) : cmc(c, y);
-        x[k] = make_float2(r.x * inv, r.y * inv);
+        x[pd(k)] = make_float2(r.x * inv, r.y * inv);
     }
     __syncthreads();
 }
@@ -176,7 +181,7 @@ __device__ __forceinline__ void ring_fft32_item(const Fft32Args &a, const int ri
                     if (sigma && (q & 1)) acc = csub(acc, v);
                     else acc = cadd(acc, v);
                 }
-                buf[k] = sigma ? cm(acc, tw[k]) : acc;
+                buf[pd(k)] = sigma ? cm(acc, tw[k]) : acc;
             }
         } else {
             const int G = F32_NT / n, g = tid / n, k = tid - g * n;
@@ -194,7 +199,7 @@ __device__ __forceinline__ void ring_fft32_item(const Fft32Args &a, const int ri
             for (int kk = tid; kk < n; kk += F32_NT) {
                 float2 acc = make_float2(0.f, 0.f);
                 for (int gg = 0; gg < G; gg++) acc = cadd(acc, red[gg * n + kk]);
-                buf[kk] = sigma ? cm(acc, tw[kk]) : acc;
+                buf[pd(kk)] = sigma ? cm(acc, tw[kk]) : acc;
             }
         }
         __syncthreads();
@@ -206,7 +211,7 @@ __device__ __forceinline__ void ring_fft32_item(const Fft32Args &a, const int ri
             float *o2 = map_out + ((size_t)r * 2 + 1) * npix + first;
             for (int k = tid; k < n; k += F32_NT) {
                 const int j = pow2 ? (int)(__brev((unsigned)k) >> (32 - logn)) : k;
-                float2 v = buf[k];
+                float2 v = buf[pd(k)];
                 if (weighted) {
                     const float wj = W[first + j];
                     v.x *= wj;
@@ -220,8 +225,8 @@ __device__ __forceinline__ void ring_fft32_item(const Fft32Args &a, const int ri
         for (int k = tid; k < n; k += F32_NT) {
             const int j = pow2 ? (int)(__brev((unsigned)k) >> (32 - logn)) : k;
             const float wj = W[first + j];
-            buf[k].x *= wj;
-            buf[k].y *= wj;
+            buf[pd(k)].x *= wj;
+            buf[pd(k)].y *= wj;
         }
         __syncthreads();
     } else {
@@ -235,7 +240,7 @@ __device__ __forceinline__ void ring_fft32_item(const Fft32Args &a, const int ri
                 v.x *= wj;
                 v.y *= wj;
             }
-            buf[k] = v;
+            buf[pd(k)] = v;
         }
         __syncthreads();
     }
@@ -246,7 +251,7 @@ __device__ __forceinline__ void ring_fft32_item(const Fft32Args &a, const int ri
     for (int mm = tid; mm < 2 * L + 1; mm += F32_NT) {
         const int m = mm - L;
         const int q = fdiv(m, n), k = m - q * n;
-        float2 v = buf[k];
+        float2 v = buf[pd(k)];
         if (sigma) {
             v = cmc(v, tw[k]);
             if (q & 1) v = make_float2(-v.x, -v.y);
@@ -263,7 +268,7 @@ __global__ void __launch_bounds__(F32_NT) k_ring_fft32(Fft32Args a)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2 *buf = reinterpret_cast<float2 *>(smem_raw);
     const int ring = a.rings ? a.rings[blockIdx.x] : (int)blockIdx.x;
-    ring_fft32_item<MODE>(a, ring, blockIdx.y, buf, buf + a.mmax);
+    ring_fft32_item<MODE>(a, ring, blockIdx.y, buf, buf + f32_slots(a.mmax));
 }
 
 // batched form over several plans: item = {instance, index into its ring list, RHS, 0}
@@ -277,7 +282,7 @@ k_ring_fft32_batch(const Fft32Args *__restrict__ insts, const int4 *__restrict__
     const Fft32Args a = insts[w.x];
     if (a.skip && *a.skip) return;
     const int ring = a.rings ? a.rings[w.y] : w.y;
-    ring_fft32_item<MODE>(a, ring, w.z, buf, buf + mmax);
+    ring_fft32_item<MODE>(a, ring, w.z, buf, buf + f32_slots(mmax));
 }
 
 }  // namespace akra
