@@ -95,6 +95,19 @@ typedef struct {
  * ENOMEM; ECUDA. */
 akra_status akra_plan_create(int nside, int lmax, akra_plan *out);
 
+/* Flat-sky variant (Sec. II B: each SHT replaced by a 2D FFT, the operator's four steps and
+ * the CG solver unchanged).  Creates a plan for an n x n periodic pixel grid, n a power of two
+ * in [16, 8192].  On such a plan the unknown x [R][n][n] complex is the unitary 2D Fourier
+ * transform of κ_E + i κ_B (rows k2, columns k1, FFT frequency order); maps are [R][2][n*n]
+ * (γ1, γ2; pixel (row y, column x) at y*n + x).  A x = F^-1(D x) with the flat-sky
+ * Kaiser-Squires kernel D(k) = (k1² - k2² + 2i k1 k2)/|k|² (D(0) = 0), A^T its exact adjoint,
+ * W = M N^-1 (no pixel-area factor; the unitary transforms carry the normalisation), λ_eff and
+ * the scalar P as for the sphere (Eqs. 14-15).  akra_plan_set_weights (d_ninv [n*n]),
+ * akra_apply_A / At / H, akra_cg_solve(_b) in F64, F32 and MIXED, akra_shuffle_shear,
+ * akra_plan_describe and akra_plan_destroy accept the plan; entry points that need the
+ * sphere's spin-2 SHTs return EINVAL.  Errors: EINVAL (n), ENOMEM, ECUDA. */
+akra_status akra_flat_plan_create(int n, akra_plan *out);
+
 /* Release every device and host resource of the plan (NULL is ignored).  Blocking. */
 void akra_plan_destroy(akra_plan plan);
 

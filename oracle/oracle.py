@@ -610,3 +610,81 @@ def solve_grad(nside: int, lmax: int, ninv, y, lam: float, gfun, tol: float = 1e
     mask = np.asarray(ninv) > 0
     dninv = np.where(mask, wts.omega * np.sum(Au * (y - Ax), axis=0), 0.0)
     return (xE, xB), dy, dninv
+
+
+# ----------------------------------------------------------------------------
+# flat-sky variant (Sec. II B: each SHT replaced by a 2D FFT; the four steps of the operator
+# and the CG solver unchanged).  Unknown x = F(κ_E + i κ_B) on an n x n periodic grid, F the
+# unitary 2D DFT (numpy's, norm="ortho", as a library step), rows k2 / y, columns k1 / x.
+# ----------------------------------------------------------------------------
+def flat_ks_kernel(n: int) -> np.ndarray:
+    """D(k) = (k1² - k2² + 2i k1 k2)/|k|², D(0) = 0, at integer FFT frequencies [k2, k1]."""
+    k = np.fft.fftfreq(n, d=1.0 / n)
+    k1, k2 = k[None, :], k[:, None]
+    q = k1 ** 2 + k2 ** 2
+    return np.where(q > 0, (k1 ** 2 - k2 ** 2 + 2j * k1 * k2) / np.where(q > 0, q, 1.0), 0.0)
+
+
+def flat_forward_A(n: int, x):
+    """(γ1, γ2) = Re / Im of F^-1 (D x)."""
+    z = np.fft.ifft2(flat_ks_kernel(n) * np.asarray(x), norm="ortho")
+    return z.real.copy(), z.imag.copy()
+
+
+def flat_adjoint_A(n: int, u1, u2):
+    """conj(D) F (u1 + i u2), the transpose of flat_forward_A in the real inner products."""
+    return np.conj(flat_ks_kernel(n)) * np.fft.fft2(np.asarray(u1) + 1j * np.asarray(u2), norm="ortho")
+
+
+class FlatWeights:
+    """W = M N^-1 on the grid (mask M = [N^-1 > 0]), λ_eff (Eq. 14) and the scalar P (Eq. 15)."""
+
+    def __init__(self, ninv, lam: float = 1e-3):
+        ninv = np.asarray(ninv, np.float64)
+        mask = ninv > 0
+        self.W = np.where(mask, ninv, 0.0)
+        self.lam_eff = lam * (ninv[mask].mean() if mask.any() else 0.0)
+        self.mean_mninv = self.W.mean()
+        self.precond = 1.0 / (self.mean_mninv + self.lam_eff)
+
+
+def flat_apply_H(n: int, wts: FlatWeights, x):
+    g1, g2 = flat_forward_A(n, x)
+    return flat_adjoint_A(n, wts.W * g1, wts.W * g2) + wts.lam_eff * np.asarray(x)
+
+
+def flat_rhs_b(n: int, wts: FlatWeights, y1, y2):
+    return flat_adjoint_A(n, wts.W * np.asarray(y1), wts.W * np.asarray(y2))
+
+
+def flat_dot(a, b) -> float:
+    """Real inner product of complex arrays: Re Σ conj(a) b."""
+    return float(np.real(np.vdot(np.asarray(a), np.asarray(b))))
+
+
+def flat_cg_solve(n: int, wts: FlatWeights, y1, y2, tol: float = 1e-8, maxiter: int = 1000):
+    """PCG (scalar P) on H x = b, b = A^T W y; returns (x, iterations, recursive relres)."""
+    b = flat_rhs_b(n, wts, y1, y2)
+    x = np.zeros_like(b)
+    r = b.copy()
+    bn = math.sqrt(flat_dot(b, b))
+    if bn == 0:
+        return x, 0, 0.0
+    z = wts.precond * r
+    p = z.copy()
+    rz = flat_dot(r, z)
+    it, relres = 0, 1.0
+    while relres >= tol and it < maxiter:
+        q = flat_apply_H(n, wts, p)
+        alpha = rz / flat_dot(p, q)
+        x = x + alpha * p
+        r = r - alpha * q
+        it += 1
+        relres = math.sqrt(flat_dot(r, r)) / bn
+        if relres < tol:
+            break
+        z = wts.precond * r
+        rz_new = flat_dot(r, z)
+        p = z + (rz_new / rz) * p
+        rz = rz_new
+    return x, it, relres

@@ -55,7 +55,7 @@ EXPORTS = ["akra_plan_create", "akra_plan_destroy", "akra_last_error", "akra_ver
            "akra_batch_apply_H", "akra_batch_cg_solve", "akra_batch_describe",
            "akra_plan_get_shape", "akra_plan_set_shape", "akra_set_mixed_policy", "akra_fma_rate",
            "akra_cg_solve_fields", "akra_shuffle_shear", "akra_cl_spectra",
-           "akra_plan_set_preconditioner"]
+           "akra_plan_set_preconditioner", "akra_flat_plan_create"]
 
 _lib_handle = None
 
@@ -78,6 +78,7 @@ def load(build_if_missing: bool = False):
     vp, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
     sig = {
         "akra_plan_create": ([i, i, ctypes.POINTER(vp)], i),
+        "akra_flat_plan_create": ([i, ctypes.POINTER(vp)], i),
         "akra_plan_destroy": ([vp], None),
         "akra_last_error": ([], ctypes.c_char_p),
         "akra_version": ([], ctypes.c_char_p),
@@ -145,6 +146,10 @@ class Plan:
         self.npix = 12 * nside * nside
         self.ntri = (lmax + 1) * (lmax + 2) // 2
 
+    def alm_shape(self, R: int):
+        """Shape of R harmonic vectors: [R, 2, ntri] (E, B) packed m-major."""
+        return (R, 2, self.ntri)
+
     def close(self):
         if self.handle:
             load().akra_plan_destroy(self.handle)
@@ -181,6 +186,26 @@ def akra_plan_create(nside: int, lmax: int) -> Plan:
     return Plan(h, nside, lmax)
 
 
+class FlatPlan(Plan):
+    """Owning handle of a flat-sky plan on an n x n periodic grid: harmonic vectors are
+    [R, n, n] complex (the unitary 2D FFT of κ_E + i κ_B), maps [R, 2, n*n]."""
+
+    def __init__(self, handle, n):
+        super().__init__(handle, n, -1)
+        self.n = n
+        self.npix = n * n
+        self.ntri = n * n // 2
+
+    def alm_shape(self, R: int):
+        return (R, self.n, self.n)
+
+
+def akra_flat_plan_create(n: int) -> FlatPlan:
+    h = ctypes.c_void_p()
+    _check(load().akra_flat_plan_create(n, ctypes.byref(h)))
+    return FlatPlan(h, n)
+
+
 def akra_plan_destroy(plan: Plan):
     plan.close()
 
@@ -198,7 +223,7 @@ def akra_plan_set_weights(plan: Plan, ninv: torch.Tensor, lam: float = 1e-3, str
 
 def akra_synth_spin2(plan: Plan, prec: int, alm: torch.Tensor, out: torch.Tensor = None, stream=None):
     R = alm.shape[0]
-    _need(alm, (R, 2, plan.ntri), _cdtype(prec), "alm")
+    _need(alm, plan.alm_shape(R), _cdtype(prec), "alm")
     if out is None:
         out = torch.empty((R, 2, plan.npix), dtype=_rdtype(prec), device=alm.device)
     _need(out, (R, 2, plan.npix), _rdtype(prec), "out")
@@ -211,7 +236,7 @@ def akra_synth_spin2_static(plan: Plan, prec: int, alm: torch.Tensor, out: torch
     library's fixed 32 MiB scratch holds the phase array).  For callers that cannot allocate
     at the point of the call, e.g. inside a stream capture or under an allocation budget."""
     R = alm.shape[0]
-    _need(alm, (R, 2, plan.ntri), _cdtype(prec), "alm")
+    _need(alm, plan.alm_shape(R), _cdtype(prec), "alm")
     _need(out, (R, 2, plan.npix), _rdtype(prec), "out")
     _check(load().akra_synth_spin2_static(plan.handle, prec, _ptr(alm), _ptr(out), R, _stream(stream)))
     return out
@@ -222,15 +247,15 @@ def akra_adjoint_synth_spin2(plan: Plan, prec: int, maps: torch.Tensor, out: tor
     R = maps.shape[0]
     _need(maps, (R, 2, plan.npix), _rdtype(prec), "maps")
     if out is None:
-        out = torch.empty((R, 2, plan.ntri), dtype=_cdtype(prec), device=maps.device)
-    _need(out, (R, 2, plan.ntri), _cdtype(prec), "out")
+        out = torch.empty(plan.alm_shape(R), dtype=_cdtype(prec), device=maps.device)
+    _need(out, plan.alm_shape(R), _cdtype(prec), "out")
     _check(load().akra_adjoint_synth_spin2(plan.handle, prec, _ptr(maps), _ptr(out), R, _stream(stream)))
     return out
 
 
 def akra_apply_A(plan: Plan, prec: int, x: torch.Tensor, weighted: bool = False, out=None, stream=None):
     R = x.shape[0]
-    _need(x, (R, 2, plan.ntri), _cdtype(prec), "x")
+    _need(x, plan.alm_shape(R), _cdtype(prec), "x")
     if out is None:
         out = torch.empty((R, 2, plan.npix), dtype=_rdtype(prec), device=x.device)
     _need(out, (R, 2, plan.npix), _rdtype(prec), "out")
@@ -243,8 +268,8 @@ def akra_apply_At(plan: Plan, prec: int, maps: torch.Tensor, weighted: bool = Fa
     R = maps.shape[0]
     _need(maps, (R, 2, plan.npix), _rdtype(prec), "maps")
     if out is None:
-        out = torch.empty((R, 2, plan.ntri), dtype=_cdtype(prec), device=maps.device)
-    _need(out, (R, 2, plan.ntri), _cdtype(prec), "out")
+        out = torch.empty(plan.alm_shape(R), dtype=_cdtype(prec), device=maps.device)
+    _need(out, plan.alm_shape(R), _cdtype(prec), "out")
     _check(load().akra_apply_At(plan.handle, prec, _ptr(maps), _ptr(out), int(weighted), R,
                                 _stream(stream)))
     return out
@@ -252,17 +277,17 @@ def akra_apply_At(plan: Plan, prec: int, maps: torch.Tensor, weighted: bool = Fa
 
 def akra_apply_H(plan: Plan, prec: int, x: torch.Tensor, out: torch.Tensor = None, stream=None):
     R = x.shape[0]
-    _need(x, (R, 2, plan.ntri), _cdtype(prec), "x")
+    _need(x, plan.alm_shape(R), _cdtype(prec), "x")
     if out is None:
         out = torch.empty_like(x)
-    _need(out, (R, 2, plan.ntri), _cdtype(prec), "out")
+    _need(out, plan.alm_shape(R), _cdtype(prec), "out")
     _check(load().akra_apply_H(plan.handle, prec, _ptr(x), _ptr(out), R, _stream(stream)))
     return out
 
 
 def _solve(fn, plan, prec, src, out, R, tol, maxiter, stream, raise_on_noconv):
     if out is None:
-        out = torch.empty((R, 2, plan.ntri), dtype=_cdtype(F64 if prec == MIXED else prec), device=src.device)
+        out = torch.empty(plan.alm_shape(R), dtype=_cdtype(F64 if prec == MIXED else prec), device=src.device)
     rel = (ctypes.c_double * R)()
     its = (ctypes.c_int * R)()
     info = CgInfo()
@@ -306,7 +331,7 @@ def akra_cg_solve_fields(plan: Plan, prec: int, fields: int, shear: torch.Tensor
     if fields == SOLVE_B_GIVEN_E:
         if out is None:
             raise ValueError("SOLVE_B_GIVEN_E reads κ_E from `out`")
-        _need(out, (R, 2, plan.ntri), _cdtype(F64 if prec == MIXED else prec), "out")
+        _need(out, plan.alm_shape(R), _cdtype(F64 if prec == MIXED else prec), "out")
 
     def fn(h, pr, src, dst, r, tl, mi, inf, st):
         return load().akra_cg_solve_fields(h, pr, fields, src, dst, r, tl, mi, inf, st)
@@ -317,14 +342,14 @@ def akra_cg_solve_fields(plan: Plan, prec: int, fields: int, shear: torch.Tensor
 def akra_cg_solve_b(plan: Plan, prec: int, b: torch.Tensor, out=None, tol: float = 1e-6,
                     maxiter: int = 1000, stream=None, raise_on_noconv: bool = False):
     R = b.shape[0]
-    _need(b, (R, 2, plan.ntri), _cdtype(F64 if prec == MIXED else prec), "b")
+    _need(b, plan.alm_shape(R), _cdtype(F64 if prec == MIXED else prec), "b")
     return _solve(load().akra_cg_solve_b, plan, prec, b, out, R, tol, maxiter, stream, raise_on_noconv)
 
 
 def akra_cg_solve_adjoint(plan: Plan, prec: int, g: torch.Tensor, out=None, tol: float = 1e-6,
                           maxiter: int = 1000, stream=None, raise_on_noconv: bool = False):
     R = g.shape[0]
-    _need(g, (R, 2, plan.ntri), _cdtype(F64 if prec == MIXED else prec), "g")
+    _need(g, plan.alm_shape(R), _cdtype(F64 if prec == MIXED else prec), "g")
     return _solve(load().akra_cg_solve_adjoint, plan, prec, g, out, R, tol, maxiter, stream,
                   raise_on_noconv)
 
@@ -390,10 +415,10 @@ def akra_cl_spectra(plan: Plan, prec: int, a: torch.Tensor, b: torch.Tensor = No
     """E/B auto (b = None) or cross spectra [R, 4, lmax+1] (EE, EB, BE, BB), or band powers
     [R, 4, nbins] for the given bin edges."""
     R = a.shape[0]
-    _need(a, (R, 2, plan.ntri), _cdtype(prec), "a")
+    _need(a, plan.alm_shape(R), _cdtype(prec), "a")
     if b is None:
         b = a
-    _need(b, (R, 2, plan.ntri), _cdtype(prec), "b")
+    _need(b, plan.alm_shape(R), _cdtype(prec), "b")
     nb = 0 if edges is None else len(edges) - 1
     e = (ctypes.c_double * (nb + 1))(*([] if edges is None else [float(v) for v in edges]))
     out = torch.empty((R, 4, nb if nb else plan.lmax + 1), dtype=torch.float64, device=a.device)

@@ -318,6 +318,7 @@ extern "C" akra_status akra_batch_create(int ninst, const akra_plan *plans, cons
             set_error("akra_batch_create: instance %d has no plan or R outside [1, 64]", i);
             return AKRA_EINVAL;
         }
+        AKRA_TRY(reject_flat(plans[i], "akra_batch_create"));
         if (!plans[i]->has_weights) {
             set_error("akra_batch_create: plan %d has no weights (akra_plan_set_weights)", i);
             return AKRA_ENOWEIGHTS;

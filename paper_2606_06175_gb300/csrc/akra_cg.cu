@@ -359,7 +359,10 @@ static akra_status cg_graph(akra_plan p, int R, CgBufs &b, cudaGraphExec_t *out)
     }
     // reserve the operator workspaces before capture (no allocation may happen inside)
     const LegShape s = leg_shape(p, PrecIdx<T>::v == 0 ? AKRA_F64 : AKRA_F32, R);
-    AKRA_TRY(ws_reserve(p, p->phi, (size_t)R * p->nring * (2 * (size_t)p->lmax + 1) * sizeof(cx_t<T>)));
+    if (is_flat(p))   // the flat-sky operator's two transpose buffers
+        AKRA_TRY(ws_reserve(p, p->phi, 2 * (size_t)R * p->npix * sizeof(cx_t<T>)));
+    else
+        AKRA_TRY(ws_reserve(p, p->phi, (size_t)R * p->nring * (2 * (size_t)p->lmax + 1) * sizeof(cx_t<T>)));
     const int nch = legendre_chunks(p->n_active_units, s);
     AKRA_TRY(ws_reserve(p, p->partial, (size_t)nch * R * p->ntri * 4 * sizeof(T)));
     AKRA_TRY(cg_reserve(p, R, b));   // pointers are stable now (nothing grows below)
@@ -855,6 +858,7 @@ extern "C" akra_status akra_cg_solve_fields(akra_plan p, akra_prec prec, akra_fi
                                             const void *d_shear, void *d_x, int R, double tol,
                                             int maxiter, akra_cg_info *info, void *stream)
 {
+    AKRA_TRY(reject_flat(p, "akra_cg_solve_fields"));
     AKRA_TRY(check_cg(p, prec, d_shear, d_x, R, tol, maxiter, "akra_cg_solve_fields"));
     if (fields != AKRA_SOLVE_E && fields != AKRA_SOLVE_B_GIVEN_E) {
         set_error("akra_cg_solve_fields: fields must be AKRA_SOLVE_E or AKRA_SOLVE_B_GIVEN_E");

@@ -64,6 +64,7 @@ using namespace akra;
 extern "C" akra_status akra_weight_grad(akra_plan p, akra_prec prec, const void *d_Au, const void *d_y,
                                         const void *d_Ax, void *d_grad, int R, void *stream)
 {
+    AKRA_TRY(reject_flat(p, "akra_weight_grad"));
     if (!p || !d_Au || !d_y || !d_Ax || !d_grad || R < 1 || R > 65535 ||
         (prec != AKRA_F64 && prec != AKRA_F32)) {
         set_error("akra_weight_grad: invalid argument");

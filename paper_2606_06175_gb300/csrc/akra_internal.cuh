@@ -150,6 +150,9 @@ struct CgGraph;            // CUDA-graph state of one CG configuration (akra_cg.
 }  // namespace akra
 
 struct akra_plan_s {
+    // 0: HEALPix sphere (spin-2 SHTs); 1: flat-sky n x n periodic patch (2D FFTs), where
+    // nside holds n, lmax is -1 (no m = 0 entries in the CG metric), npix = n^2, ntri = n^2/2
+    int kind = 0;
     int nside = 0, lmax = 0, nring = 0, nunit = 0;
     long long npix = 0, ntri = 0;
     int device = 0;
@@ -188,6 +191,13 @@ struct akra_plan_s {
     int fft32_nsmall_act = 0;
     int *d_all_rings = nullptr;              // [nring] 0..nring-1
     int *d_all_units = nullptr;              // [nunit] 0..nunit-1
+
+    // flat-sky plan: twiddles e^{-2πi t/n}, weights W = M N^-1 transposed and scaled by 1/n^2
+    int flat_logn = 0;
+    double2 *d_ftw64 = nullptr;
+    float2 *d_ftw32 = nullptr;
+    double *d_fWt64 = nullptr;
+    float *d_fWt32 = nullptr;
 
     // fields H acts on inside a field-restricted solve (bit 0 E, bit 1 B); 3 everywhere else
     int fields = 3;
@@ -264,6 +274,22 @@ akra_status ring_fft(akra_plan p, FftMode mode, void *phi, const void *map_in, v
                      bool weighted, int R, const int *rings, int nrings, cudaStream_t st);
 // FP32 ring FFT with Bluestein for non-power-of-two rings (akra_ringfft32.cu)
 akra_status ring_fft32_build(akra_plan p);
+// flat-sky operators (akra_flat.cu); the op_* entry points dispatch to them for kind == 1
+template <typename T>
+akra_status flat_op_A(akra_plan p, const void *x, void *map, bool weighted, int R, cudaStream_t st);
+template <typename T>
+akra_status flat_op_At(akra_plan p, const void *map, void *x, bool weighted, int R, cudaStream_t st);
+template <typename T>
+akra_status flat_op_H(akra_plan p, const void *x, void *y, int R, cudaStream_t st);
+akra_status flat_set_weights(akra_plan p, const double *d_ninv, double lambda, cudaStream_t st);
+inline bool is_flat(akra_plan p) { return p && p->kind == 1; }
+// entry points that need the sphere's spin-2 SHT machinery reject flat-sky plans
+inline akra_status reject_flat(akra_plan p, const char *who)
+{
+    if (!is_flat(p)) return AKRA_OK;
+    set_error("%s: not defined for a flat-sky plan", who);
+    return AKRA_EINVAL;
+}
 akra_status ring_fft32_order(akra_plan p, const std::vector<int> &rings, int *d_out, int *nsmall);
 Fft32Args fft32_args(akra_plan p, bool weighted, const int *rings);
 akra_status ring_fft32(akra_plan p, FftMode mode, void *phi, const void *map_in, void *map_out,

@@ -369,6 +369,7 @@ template <typename T>
 akra_status op_synth(akra_plan p, LegMode mode, const void *alm, void *map, bool weighted, int R,
                      cudaStream_t st)
 {
+    if (is_flat(p)) return flat_op_A<T>(p, alm, map, weighted, R, st);
     AKRA_TRY(ws_reserve(p, p->phi, phi_bytes(p, sizeof(cx_t<T>), R)));
     const LegShape s = leg_shape(p, prec_of<T>(), R);
     AKRA_TRY(legendre_synth<T>(p, s, mode, alm, p->phi.ptr, R, p->d_all_units, p->nunit, st));
@@ -382,6 +383,7 @@ template <typename T>
 akra_status op_adjoint(akra_plan p, LegMode mode, const void *map, void *alm, bool weighted, int R,
                        cudaStream_t st)
 {
+    if (is_flat(p)) return flat_op_At<T>(p, map, alm, weighted, R, st);
     const LegShape s = leg_shape(p, prec_of<T>(), R);
     // with weights, rings where W = 0 contribute exactly nothing: transform the active ones only
     const bool act = weighted && p->has_weights;
@@ -401,6 +403,7 @@ akra_status op_adjoint(akra_plan p, LegMode mode, const void *map, void *alm, bo
 template <typename T>
 akra_status op_H(akra_plan p, const void *x, void *y, int R, cudaStream_t st)
 {
+    if (is_flat(p)) return flat_op_H<T>(p, x, y, R, st);
     const LegShape s = leg_shape(p, prec_of<T>(), R);
     AKRA_TRY(ws_reserve(p, p->phi, phi_bytes(p, sizeof(cx_t<T>), R)));
     AKRA_TRY(ws_reserve(p, p->partial, (size_t)legendre_chunks(p->n_active_units, s) * R *
@@ -563,7 +566,8 @@ extern "C" void akra_plan_destroy(akra_plan p)
                     p->phi.ptr, p->partial.ptr, p->cg.ptr, p->red.ptr, p->xsave.ptr, p->red_cl.ptr,
                     p->d_fft32_M,
                     p->d_fft32_off, p->d_fft32_tw2, p->d_fft32_bhat, p->d_seed32, p->d_seed64,
-                    p->d_start32, p->d_start64, p->d_steps, p->d_pw64, p->d_pw32,
+                    p->d_start32, p->d_start64, p->d_steps, p->d_pw64, p->d_pw32, p->d_ftw64,
+                    p->d_ftw32, p->d_fWt64, p->d_fWt32,
                     p->d_fft32_rings_all, p->d_fft32_rings_act};
     for (void *q : ptrs)
         if (q) cudaFree(q);
@@ -619,6 +623,7 @@ extern "C" akra_status akra_plan_set_weights(akra_plan p, const double *d_ninv, 
         return AKRA_EINVAL;
     }
     cudaStream_t st = (cudaStream_t)stream;
+    if (is_flat(p)) return flat_set_weights(p, d_ninv, lambda, st);
     const int nr = p->nring;
     double *d_stats = nullptr;
     if (cudaMalloc(&d_stats, sizeof(double) * 3 * nr) != cudaSuccess) {
@@ -703,6 +708,7 @@ static akra_status check_common(akra_plan p, akra_prec prec, const void *a, cons
 extern "C" akra_status akra_synth_spin2(akra_plan p, akra_prec prec, const void *d_alm,
                                         void *d_map, int R, void *stream)
 {
+    AKRA_TRY(reject_flat(p, "akra_synth_spin2"));
     AKRA_TRY(check_common(p, prec, d_alm, d_map, R, "akra_synth_spin2"));
     cudaStream_t st = (cudaStream_t)stream;
     return prec == AKRA_F64 ? op_synth<double>(p, LegMode::Synth, d_alm, d_map, false, R, st)
@@ -712,6 +718,7 @@ extern "C" akra_status akra_synth_spin2(akra_plan p, akra_prec prec, const void 
 extern "C" akra_status akra_adjoint_synth_spin2(akra_plan p, akra_prec prec, const void *d_map,
                                                 void *d_alm, int R, void *stream)
 {
+    AKRA_TRY(reject_flat(p, "akra_adjoint_synth_spin2"));
     AKRA_TRY(check_common(p, prec, d_map, d_alm, R, "akra_adjoint_synth_spin2"));
     cudaStream_t st = (cudaStream_t)stream;
     return prec == AKRA_F64 ? op_adjoint<double>(p, LegMode::Synth, d_map, d_alm, false, R, st)
@@ -849,6 +856,7 @@ static bool shape_compiled(akra_prec prec, int P, int RG)
 extern "C" akra_status akra_plan_get_shape(akra_plan p, akra_prec prec, int R, int *P, int *PA,
                                            int *RG)
 {
+    AKRA_TRY(reject_flat(p, "akra_plan_get_shape"));
     if (!p || !P || !PA || !RG || R < 1 || (prec != AKRA_F64 && prec != AKRA_F32)) {
         set_error("akra_plan_get_shape: invalid argument");
         return AKRA_EINVAL;
@@ -862,6 +870,7 @@ extern "C" akra_status akra_plan_get_shape(akra_plan p, akra_prec prec, int R, i
 
 extern "C" akra_status akra_plan_set_preconditioner(akra_plan p, akra_precond kind)
 {
+    AKRA_TRY(reject_flat(p, "akra_plan_set_preconditioner"));
     if (!p || (kind != AKRA_PRECOND_SCALAR && kind != AKRA_PRECOND_PER_L)) {
         set_error("akra_plan_set_preconditioner: invalid argument");
         return AKRA_EINVAL;
@@ -873,6 +882,7 @@ extern "C" akra_status akra_plan_set_preconditioner(akra_plan p, akra_precond ki
 
 extern "C" akra_status akra_plan_set_shape(akra_plan p, akra_prec prec, int R, int P, int PA, int RG)
 {
+    AKRA_TRY(reject_flat(p, "akra_plan_set_shape"));
     if (!p || R < 1 || R > 65535 || (prec != AKRA_F64 && prec != AKRA_F32) ||
         !shape_compiled(prec, P, RG) || !shape_compiled(prec, PA, RG)) {
         set_error("akra_plan_set_shape: invalid argument or no compiled kernel for P=%d PA=%d RG=%d",
@@ -886,6 +896,7 @@ extern "C" akra_status akra_plan_set_shape(akra_plan p, akra_prec prec, int R, i
 
 extern "C" akra_status akra_autotune(akra_plan p, akra_prec prec, int R, void *stream)
 {
+    AKRA_TRY(reject_flat(p, "akra_autotune"));
     if (!p || R < 1 || R > 65535 || (prec != AKRA_F64 && prec != AKRA_F32 && prec != AKRA_MIXED)) {
         set_error("akra_autotune: invalid argument");
         return AKRA_EINVAL;
@@ -958,6 +969,7 @@ static akra_status time_stages(akra_plan p, int R, int reps, cudaStream_t st, do
 extern "C" akra_status akra_time_H_stages(akra_plan p, akra_prec prec, int R, int reps, void *stream,
                                           double *ms_out)
 {
+    AKRA_TRY(reject_flat(p, "akra_time_H_stages"));
     if (!p || !ms_out || reps < 1 || R < 1 || (prec != AKRA_F64 && prec != AKRA_F32)) {
         set_error("akra_time_H_stages: invalid argument");
         return AKRA_EINVAL;

@@ -130,6 +130,7 @@ extern "C" akra_status akra_shuffle_shear(akra_plan p, akra_prec prec, const voi
 extern "C" akra_status akra_cl_spectra(akra_plan p, akra_prec prec, const void *d_a, const void *d_b,
                                        int R, int nbins, const double *edges, double *d_out, void *stream)
 {
+    AKRA_TRY(reject_flat(p, "akra_cl_spectra"));
     if (!p || !d_a || !d_b || !d_out || R < 1 || R > 65535 || (prec != AKRA_F64 && prec != AKRA_F32) ||
         nbins < 0 || nbins > kMaxBins || (nbins > 0 && !edges)) {
         set_error("akra_cl_spectra: invalid argument (at most %d bins)", kMaxBins);

@@ -76,6 +76,7 @@ using namespace akra;
 extern "C" akra_status akra_synth_spin2_static(akra_plan p, akra_prec prec, const void *d_alm,
                                                void *d_map, int R, void *stream)
 {
+    AKRA_TRY(reject_flat(p, "akra_synth_spin2_static"));
     if (!p || !d_alm || !d_map) {
         set_error("akra_synth_spin2_static: NULL plan or array");
         return AKRA_EINVAL;

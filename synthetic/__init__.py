@@ -31,7 +31,7 @@ SIGMA_E = 0.26
 ARCMIN2_PER_SR = (180.0 * 60.0 / math.pi) ** 2
 
 # workload seeds: cap (Nside 32), DES-like 512, DES-like 2048, batched, differentiation
-SEEDS = {"cap32": 1001, "des512": 1002, "des2048": 1003, "batch": 1004, "grad512": 1005}
+SEEDS = {"cap32": 1001, "des512": 1002, "des2048": 1003, "batch": 1004, "grad512": 1005, "flat": 1006}
 
 
 def ntri(lmax: int) -> int:
@@ -227,3 +227,40 @@ def workload(name: str, nside: int = None, lmax: int = None):
     noise = shape_noise(sv["ninv"], sv["rng_noise"])[0]
     return dict(nside=nside, lmax=lmax, x_true=(kE, kB), ninv=sv["ninv"], mask=sv["mask"],
                 noise=noise, tol=tol)
+
+
+def flat_survey(n: int, seed: int = SEEDS["flat"], pix_arcmin: float = 0.86):
+    """Flat-sky workload on an n x n periodic grid of pix_arcmin pixels: a DES-like patch (a
+    rectangle over 70 % x 50 % of the grid, each edge displaced by up to 2 % of the side by a
+    sum of random-phase sinusoids), counts Poisson(5.6 arcmin^-2 x pixel area x (1 + 0.3 t)),
+    t a smooth random cubic in the pixel position with max |t| = 1 on the patch.  Returns
+    dict(ninv [n*n], mask, x_true [n, n] complex, noise [2, n*n]), x_true the unitary 2D
+    Fourier transform of a real Gaussian field with power ∝ (|k| + 10)^-2 (κ_B = 0)."""
+    r_alm, r_fp, r_depth, r_cnt, r_noise = streams(seed)
+    yy, xx = np.mgrid[0:n, 0:n] / float(n)
+    s_edges = [_edge_wiggle(r_fp) for _ in range(4)]
+    d = 0.02
+    c = np.arange(n) / float(n) * 360.0            # edges vary along the other coordinate
+    x0 = (0.15 + d * s_edges[0](c))[:, None]
+    x1 = (0.85 + d * s_edges[1](c))[:, None]
+    y0 = (0.25 + d * s_edges[2](c))[None, :]
+    y1 = (0.75 + d * s_edges[3](c))[None, :]
+    fp = (xx > x0) & (xx < x1) & (yy > y0) & (yy < y1)
+    t = np.zeros((n, n))
+    u, v = xx - 0.5, yy - 0.5
+    for a in range(4):
+        for b in range(4 - a):
+            t += r_depth.standard_normal() * u ** a * v ** b
+    t = np.where(fp, t - t[fp].mean(), 0.0)
+    t /= np.abs(t).max()
+    nbar = np.where(fp, 5.6 * pix_arcmin ** 2 * (1 + 0.3 * t), 0.0)
+    counts = r_cnt.poisson(nbar).astype(np.float64)
+    mask = fp & (counts >= 1)
+    ninv = np.where(mask, counts / SIGMA_E ** 2, 0.0).ravel()
+    k = np.fft.fftfreq(n, d=1.0 / n)
+    kk = np.sqrt(k[None, :] ** 2 + k[:, None] ** 2)
+    amp = np.sqrt(1e-4 * (kk + 10.0) ** -2.0)
+    x_true = amp * np.fft.fft2(r_alm.standard_normal((n, n)), norm="ortho")
+    x_true[0, 0] = 0.0
+    noise = shape_noise(ninv, r_noise)[0]
+    return dict(n=n, ninv=ninv, mask=mask.ravel(), x_true=x_true, noise=noise)

@@ -383,6 +383,76 @@ def test_shuffle_permutes_only_unmasked_values():
     assert not np.array_equal(perms[0], perms[1])
 
 
+def test_flat_single_mode_closed_form_and_adjoint_identity():
+    """Flat sky: one Fourier mode (k1, k2) gives γ1 + iγ2 = D(k) e^{2πi(k1 x + k2 y)/n}/n at
+    every pixel, D = e^{2iφ_k}; <A x, u> = <x, A^T u> to 1e-12."""
+    n = 16
+    for k1, k2 in [(3, 0), (2, 5), (n - 4, 7), (n // 2, 1)]:
+        x = np.zeros((n, n), np.complex128)
+        x[k2, k1] = 0.7 - 0.2j
+        g1, g2 = O.flat_forward_A(n, x)
+        f1 = k1 if k1 < n // 2 else k1 - n
+        f2 = k2 if k2 < n // 2 else k2 - n
+        D = (f1 * f1 - f2 * f2 + 2j * f1 * f2) / (f1 * f1 + f2 * f2)
+        assert abs(abs(D) - 1) < 1e-15
+        yy, xx = np.mgrid[0:n, 0:n]
+        ref = (0.7 - 0.2j) * D * np.exp(2j * np.pi * (k1 * xx + k2 * yy) / n) / n
+        assert np.max(np.abs(g1 + 1j * g2 - ref)) < 1e-14
+    rng = np.random.default_rng(1)
+    x = rng.normal(size=(n, n)) + 1j * rng.normal(size=(n, n))
+    u1, u2 = rng.normal(size=(n, n)), rng.normal(size=(n, n))
+    g1, g2 = O.flat_forward_A(n, x)
+    lhs = np.sum(g1 * u1 + g2 * u2)
+    rhs = O.flat_dot(x, O.flat_adjoint_A(n, u1, u2))
+    assert abs(lhs - rhs) < 1e-12 * abs(lhs)
+
+
+def test_flat_uniform_weights_H_is_diagonal_and_pure_E_recovered():
+    """Uniform full coverage: H x = w |D|² x + λ_eff x (= (w + λ_eff) x off k = 0).  Random
+    positive weights, λ = 0, noise-free y = A x_true with no k = 0 part: CG returns x_true."""
+    n = 16
+    rng = np.random.default_rng(2)
+    x = rng.normal(size=(n, n)) + 1j * rng.normal(size=(n, n))
+    w = O.FlatWeights(np.full((n, n), 3.0), lam=1e-3)
+    hx = O.flat_apply_H(n, w, x)
+    expect = (3.0 + w.lam_eff) * x
+    expect[0, 0] = w.lam_eff * x[0, 0]
+    assert np.max(np.abs(hx - expect)) < 1e-12 * np.abs(x).max()
+    kE = rng.normal(size=(n, n))
+    xt = np.fft.fft2(kE, norm="ortho")
+    xt[0, 0] = 0
+    w2 = O.FlatWeights(1.0 + rng.random((n, n)), lam=0.0)
+    y1, y2 = O.flat_forward_A(n, xt)
+    xs, it, rr = O.flat_cg_solve(n, w2, y1, y2, tol=1e-13, maxiter=500)
+    assert np.max(np.abs(xs - xt)) < 1e-10 * np.abs(xt).max()
+    # the recovered field is pure E: κ_B = Im F^-1 x = 0
+    assert np.max(np.abs(np.fft.ifft2(xs, norm="ortho").imag)) < 1e-10 * np.abs(kE).max()
+
+
+def test_flat_cg_equals_dense_solve():
+    """n = 8 with a mask: CG equals the dense H solved directly (H built column by column on
+    the real and imaginary unit vectors)."""
+    n = 8
+    rng = np.random.default_rng(3)
+    ninv = np.where(rng.random((n, n)) < 0.6, 1.0 + rng.random((n, n)), 0.0)
+    w = O.FlatWeights(ninv, lam=1e-2)
+    y1 = np.where(ninv > 0, rng.normal(size=(n, n)), 0.0)
+    y2 = np.where(ninv > 0, rng.normal(size=(n, n)), 0.0)
+    basis = []
+    for k in range(n * n):
+        for v in (1.0, 1j):
+            e = np.zeros(n * n, np.complex128)
+            e[k] = v
+            basis.append(e.reshape(n, n))
+    H = np.array([[O.flat_dot(bi, O.flat_apply_H(n, w, bj)) for bj in basis] for bi in basis])
+    assert np.max(np.abs(H - H.T)) < 1e-12 * np.abs(H).max()
+    b = O.flat_rhs_b(n, w, y1, y2)
+    c = np.linalg.solve(H, np.array([O.flat_dot(bi, b) for bi in basis]))
+    xd = sum(ci * bi for ci, bi in zip(c, basis))
+    xs, it, rr = O.flat_cg_solve(n, w, y1, y2, tol=1e-13, maxiter=500)
+    assert np.max(np.abs(xs - xd)) < 1e-10 * np.abs(xd).max()
+
+
 def test_full_sky_uniform_weight_is_nearly_diagonal():
     """M ≡ 1, uniform N^-1: H_EB ≈ 0 and H ≈ <N^-1> D_l^2 (App. A), within HEALPix quadrature."""
     N, L = 16, 16
