@@ -36,6 +36,18 @@ NSIDE, LMAX, TOL = 2048, 4096, 1e-6
 SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 
 
+def _hbm_gbs():
+    """Measured copy bandwidth of the GB300s (MEASURED_PEAKS.json), else 6800 GB/s."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except Exception:
+        return 6800.0
+
+
+HBM_GBS = _hbm_gbs()
+
+
 def fp32_peak_tflops(mhz=SM_MAX_MHZ):
     # 152 SMs x 128 FP32 lanes x 2 flops (FMA) x clock
     return SM_COUNT * FP32_LANES * 2 * mhz * 1e6 / 1e12
@@ -202,6 +214,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fields", action="store_true",
                     help="also time the E-only solve and the conditional B-mode solve (App. A)")
+    ap.add_argument("--flat", type=int, default=0, metavar="N",
+                    help="also time the flat-sky variant on an N x N grid (mixed solve, H applies)")
     ap.add_argument("--per-l-precond", action="store_true",
                     help="also time the mixed solve with the per-l diagonal preconditioner")
     ap.add_argument("--noise-realisations", type=int, default=0, metavar="K",
@@ -353,6 +367,50 @@ def main():
                  "relres": ip["relres"]}
         A.akra_plan_set_preconditioner(plan, A.PRECOND_SCALAR)
 
+    # ---- flat-sky variant (2D FFTs in place of the SHTs): N x N DES-like patch ----
+    flat = None
+    if args.flat > 0:
+        import synthetic as S
+        nf = args.flat
+        sv = S.flat_survey(nf)
+        fp = A.akra_flat_plan_create(nf)
+        ninv_f = torch.from_numpy(sv["ninv"]).to(dev)
+        A.akra_plan_set_weights(fp, ninv_f, 1e-3)
+        xt = torch.from_numpy(sv["x_true"][None]).to(dev)
+        yf = A.akra_apply_A(fp, A.F64, xt)
+        yf += torch.from_numpy(sv["noise"][None]).to(dev)
+        yf *= (ninv_f > 0).to(yf.dtype)
+        xf = torch.empty_like(xt)
+        A.akra_cg_solve(fp, A.MIXED, yf, xf, tol=TOL, maxiter=3000)   # capture
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, inf_f = A.akra_cg_solve(fp, A.MIXED, yf, xf, tol=TOL, maxiter=3000)
+        torch.cuda.synchronize()
+        t_f = time.perf_counter() - t0
+        h_ms = {}
+        for pr, nm in ((A.F32, "fp32"), (A.F64, "fp64")):
+            xx = xf.to(torch.complex64) if pr == A.F32 else xf
+            yy = A.akra_apply_H(fp, pr, xx)
+            for _ in range(3):
+                A.akra_apply_H(fp, pr, xx, yy)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(10):
+                A.akra_apply_H(fp, pr, xx, yy)
+            e1.record()
+            torch.cuda.synchronize()
+            h_ms[nm] = e0.elapsed_time(e1) / 10
+        # HBM traffic of one H: 5 passes over the complex field (row FFT in/out, 2 transposes,
+        # fused middle pass, last pass reading x for the λ_eff term) + the weights
+        cb = {"fp32": 8, "fp64": 16}
+        traffic = {k: (11 * cb[k] + cb[k] // 2) * nf * nf for k in cb}
+        hbm = {k: traffic[k] / (h_ms[k] * 1e-3) / 1e9 for k in cb}
+        flat = {"n": nf, "pixels": nf * nf, "solve_s": t_f, "inner_iters": inf_f["iters"],
+                "outer": inf_f["outer"], "h_applies_f64": inf_f["h_applies_f64"], "relres": inf_f["relres"],
+                "h_apply_ms": h_ms, "h_traffic_bytes": traffic, "h_achieved_gbs": hbm,
+                "h_frac_of_hbm": {k: hbm[k] / HBM_GBS for k in hbm}}
+        A.akra_plan_destroy(fp)
+
     # ---- noise-realisation pipeline (Sec. IV): K shuffled maps as the RHS of one solve ----
     noise = None
     if args.noise_realisations > 0:
@@ -416,6 +474,8 @@ def main():
         line["noise_realisations"] = noise
     if per_l is not None:
         line["per_l_preconditioner"] = per_l
+    if flat is not None:
+        line["flat_sky"] = flat
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
