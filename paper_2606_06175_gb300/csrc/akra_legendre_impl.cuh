@@ -96,9 +96,12 @@ __device__ __forceinline__ void leg_synth_item(const LegArgs<T> &a, const int m,
 
     for (int lt = l_first; lt <= L; lt += TL) {
         __syncthreads();
-        for (int i = tid; i < TL; i += NT) {
-            const int l = lt + i;
-            s_coef[i] = (l <= L) ? coef[mbase + l] : V4{0, 0, 0, 0};
+        // recurrence coefficients of two consecutive steps per entry: {A'_l, c'_l, A'_l+1, c'_l+1}
+        for (int i = tid; i < TL / 2; i += NT) {
+            const int l = lt + 2 * i;
+            const V4 c0 = (l <= L) ? coef[mbase + l] : V4{0, 0, 0, 0};
+            const V4 c1 = (l + 1 <= L) ? coef[mbase + l + 1] : V4{0, 0, 0, 0};
+            s_coef[i] = V4{c0.x, c0.y, c1.x, c1.y};
         }
         for (int i = tid; i < TL * RG; i += NT) {
             const int li = i / RG, rr = i - li * RG;
@@ -126,9 +129,8 @@ __device__ __forceinline__ void leg_synth_item(const LegArgs<T> &a, const int m,
         // one l-step: contract at l (slot S = parity of l - l0), then recur to l+1.
         // vp = 2λ, vm = (-2)λ; accumulators per slot: P1 = Σ c 2λ, P2 = Σ d (-2)λ,
         // P3 = Σ c (-2)λ, P4 = Σ d 2λ (complex)
-#define AKRA_SYNTH_STEP(I, S, GATED)                                                        \
+#define AKRA_SYNTH_STEP(I, S, GATED, CA, CC)                                                        \
     {                                                                                       \
-        const V4 c = s_coef[I];                                                             \
         bool any = true;                                                                    \
         if (GATED) {                                                                        \
             bool a_ = false;                                                                \
@@ -154,8 +156,8 @@ __device__ __forceinline__ void leg_synth_item(const LegArgs<T> &a, const int m,
             }                                                                               \
         }                                                                                   \
         _Pragma("unroll") for (int k = 0; k < P; k++) {                                     \
-            const T t1 = fma(c.x, x[k], c.y);                                               \
-            const T t2 = fma(c.x, x[k], -c.y);                                              \
+            const T t1 = fma((CA), x[k], (CC));                                             \
+            const T t2 = fma((CA), x[k], -(CC));                                            \
             /* the new value overwrites the older register; the roles swap every step */    \
             T &cp_ = (S) == 0 ? vp[k] : vpo[k], &op_ = (S) == 0 ? vpo[k] : vp[k];           \
             T &cm_ = (S) == 0 ? vm[k] : vmo[k], &om_ = (S) == 0 ? vmo[k] : vm[k];           \
@@ -173,13 +175,15 @@ __device__ __forceinline__ void leg_synth_item(const LegArgs<T> &a, const int m,
 
         if (all_live) {
             for (int i = 0; i < nl; i += 2) {
-                AKRA_SYNTH_STEP(i, 0, false)
-                AKRA_SYNTH_STEP(i + 1, 1, false)
+                const V4 cc = s_coef[i >> 1];
+                AKRA_SYNTH_STEP(i, 0, false, cc.x, cc.y)
+                AKRA_SYNTH_STEP(i + 1, 1, false, cc.z, cc.w)
             }
         } else {
             for (int i = 0; i < nl; i += 2) {
-                AKRA_SYNTH_STEP(i, 0, true)
-                AKRA_SYNTH_STEP(i + 1, 1, true)
+                const V4 cc = s_coef[i >> 1];
+                AKRA_SYNTH_STEP(i, 0, true, cc.x, cc.y)
+                AKRA_SYNTH_STEP(i + 1, 1, true, cc.z, cc.w)
             }
         }
 #undef AKRA_SYNTH_STEP
