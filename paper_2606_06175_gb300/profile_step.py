@@ -23,12 +23,25 @@ def main():
     ap.add_argument("--prec", default="f32", choices=["f32", "f64"])
     ap.add_argument("--reps", type=int, default=2)
     ap.add_argument("--solve", action="store_true", help="one mixed-precision solve instead")
+    ap.add_argument("--flat", type=int, default=0, metavar="N",
+                    help="H applications of the flat-sky variant on an N x N grid instead")
     ap.add_argument("--shape", type=int, nargs=3, metavar=("P", "PA", "RG"),
                     help="force the Legendre tile shape of --prec (R = 1)")
     args = ap.parse_args()
     N, L = args.nside, args.lmax
-    sv = S.survey(N, "des", S.SEEDS["des2048"])
     dev = torch.device("cuda", 0)
+    if args.flat:
+        sv = S.flat_survey(args.flat)
+        fp = A.akra_flat_plan_create(args.flat)
+        A.akra_plan_set_weights(fp, torch.from_numpy(sv["ninv"]).to(dev), 1e-3)
+        pr = A.F32 if args.prec == "f32" else A.F64
+        x = torch.from_numpy(sv["x_true"][None]).to(dev, torch.complex64 if pr == A.F32 else torch.complex128)
+        for _ in range(args.reps):
+            A.akra_apply_H(fp, pr, x)
+        torch.cuda.synchronize()
+        print("ok", A.akra_plan_describe(fp)["kernel_launches"])
+        return
+    sv = S.survey(N, "des", S.SEEDS["des2048"])
     plan = A.akra_plan_create(N, L)
     A.akra_plan_set_weights(plan, torch.from_numpy(sv["ninv"]).to(dev), 1e-3)
     prec = A.F32 if args.prec == "f32" else A.F64
