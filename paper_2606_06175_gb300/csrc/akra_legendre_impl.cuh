@@ -312,7 +312,8 @@ __device__ __forceinline__ void leg_adjoint_item(
     C2 X1[P][RG], X2[P][RG], X3[P][RG], X4[P][RG];
 #pragma unroll
     for (int k = 0; k < P; k++) {
-        const int iu = (chunk * P + k) * NT + tid;
+        // each warp holds 32 P consecutive pairs (close in latitude, so close in start point)
+        const int iu = chunk * P * NT + warp * 32 * P + k * 32 + lane;
         const int u = iu < nunits ? (units ? units[iu] : iu) : -1;
         uid[k] = u;
         x[k] = 0;
@@ -355,6 +356,7 @@ __device__ __forceinline__ void leg_adjoint_item(
     }
 
     T (*tr)[S] = s_tr[warp];
+    const int warp_first = __reduce_min_sync(0xffffffffu, my_first);
     const int l_first = block_min_start<NT>(my_first);
     // the l below the first start get zero partial sums
     for (int i = tid; i < (min(l_first, L + 1) - l0) * RG * 4; i += NT) {
@@ -371,6 +373,11 @@ __device__ __forceinline__ void leg_adjoint_item(
         __syncthreads();
         const int nl = min(TLA, L - lt + 1);
         start_pairs(seeds, start, (size_t)m * nunit_all, lt, uid, gs, vp, vm, vpo, vmo, e);
+        if (warp_first > lt + TLA - 1) {
+            // none of this warp's pairs has started yet: its rows of the tile sum are zero
+            T *zr = &s_red[warp][0][0][0];
+            for (int i = lane; i < TLA * RG * 4; i += 32) zr[i] = T(0);
+        } else {
         bool live = true;
 #pragma unroll
         for (int k = 0; k < P; k++) live &= (e[k] == 0);
@@ -451,6 +458,7 @@ __device__ __forceinline__ void leg_adjoint_item(
             AKRA_ADJ_KBLOCK(true)
         }
 #undef AKRA_ADJ_KBLOCK
+        }
         __syncthreads();
         // sum the warps and write this chunk's partial sums for the tile
         for (int i = tid; i < nl * RG * 4; i += NT) {
