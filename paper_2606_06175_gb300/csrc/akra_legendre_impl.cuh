@@ -92,6 +92,7 @@ __device__ __forceinline__ void leg_synth_item(const LegArgs<T> &a, const int m,
 #pragma unroll
             for (int j = 0; j < 16; j++) acc[k][r][j] = 0;
     }
+    const int warp_first = __reduce_min_sync(0xffffffffu, my_first);
     const int l_first = block_min_start<NT>(my_first);
 
     for (int lt = l_first; lt <= L; lt += TL) {
@@ -121,6 +122,7 @@ __device__ __forceinline__ void leg_synth_item(const LegArgs<T> &a, const int m,
         __syncthreads();
         const int nl = min(TL, L - lt + 1);
         start_pairs(seeds, start, (size_t)m * nunit_all, lt, uid, gs, vp, vm, vpo, vmo, e);
+        if (warp_first > lt + TL - 1) continue;   // none of this warp's pairs has started yet
         bool live = true;
 #pragma unroll
         for (int k = 0; k < P; k++) live &= (e[k] == 0);
