@@ -50,11 +50,23 @@ __device__ bool block_partials(double *vals, int nslots, double *scratch, CgCtl 
     return last;
 }
 
-__device__ double sum_partials(const double *scratch, int r)
+// in the last block: the total of every slot, summed by all threads in a fixed order (the
+// partials are read past L1, they were written by other blocks), into tot[0..nslots)
+__device__ void block_totals(const double *scratch, int nslots, double *tot)
 {
-    double s = 0;
-    for (int b = 0; b < RED_NB; b++) s += scratch[(size_t)r * RED_NB + b];
-    return s;
+    __shared__ double sh[RED_NT];
+    for (int r = 0; r < nslots; r++) {
+        double s = 0;
+        for (int b = threadIdx.x; b < RED_NB; b += RED_NT) s += __ldcg(scratch + (size_t)r * RED_NB + b);
+        sh[threadIdx.x] = s;
+        __syncthreads();
+        for (int off = RED_NT / 2; off > 0; off >>= 1) {
+            if (threadIdx.x < off) sh[threadIdx.x] += sh[threadIdx.x + off];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) tot[r] = sh[0];
+        __syncthreads();
+    }
 }
 
 constexpr int kMaxRhsLocal = 64;
@@ -68,7 +80,7 @@ template <> const float *pw_ptr<float>(akra_plan p) { return p->precond_kind ? p
 // (no division per element); j <= L are the m = 0 entries.
 #define AKRA_FOR_RHS_ELEMENTS(r)                                                                     \
     for (int f_ = 0; f_ < 2; f_++)                                                                   \
-        for (long long j = blockIdx.x * (long long)RED_NT + threadIdx.x, o = ((long long)(r) * 2 + f_) * ntri + j; \
+        _Pragma("unroll 4") for (long long j = blockIdx.x * (long long)RED_NT + threadIdx.x, o = ((long long)(r) * 2 + f_) * ntri + j; \
              j < ntri; j += (long long)gridDim.x * RED_NT, o += (long long)gridDim.x * RED_NT)
 
 // preconditioner weight of packed index j: the scalar P of Eq. 15, or a per-l diagonal
@@ -103,12 +115,14 @@ k_cg_init(int L, long long ntri, const cx_t<T> *b, cx_t<T> *x, cx_t<T> *r, cx_t<
         acc[2 * q + 1] = rz;
     }
     if (block_partials(acc, 2 * R, scratch, ctl)) {
+        __shared__ double tot[2 * kMaxRhsLocal];
+        block_totals(scratch, 2 * R, tot);
         for (int q = threadIdx.x; q < R; q += RED_NT) {
-            const double bb = sum_partials(scratch, 2 * q);
+            const double bb = tot[2 * q];
             CgState s{};
             s.bnorm2 = bb;
             s.rr = bb;
-            s.rz = sum_partials(scratch, 2 * q + 1);
+            s.rz = tot[2 * q + 1];
             s.tol = tol;
             s.relres = bb > 0 ? 1.0 : 0.0;
             s.done = bb > 0 ? 0 : 1;
@@ -147,9 +161,11 @@ k_cg_dot_pq(int L, long long ntri, const cx_t<T> *p, const cx_t<T> *q, CgState *
         acc[r] = a;
     }
     if (block_partials(acc, R, scratch, ctl)) {
+        __shared__ double tot[kMaxRhsLocal];
+        block_totals(scratch, R, tot);
         for (int r = threadIdx.x; r < R; r += RED_NT) {
             if (st[r].done) continue;
-            const double pq = sum_partials(scratch, r);
+            const double pq = tot[r];
             st[r].pq = pq;
             if (!(pq > 0) || !isfinite(pq)) {
                 st[r].status = AKRA_ENUMERIC;
@@ -194,15 +210,17 @@ k_cg_update_xr(int L, long long ntri, const cx_t<T> *p, const cx_t<T> *q, cx_t<T
         acc[2 * r + 1] = az;
     }
     if (block_partials(acc, 2 * R, scratch, ctl)) {
+        __shared__ double tot[2 * kMaxRhsLocal];
+        block_totals(scratch, 2 * R, tot);
         const double P = ctl->precond;
         for (int r = threadIdx.x; r < R; r += RED_NT) {
             CgState s = st[r];
             if (s.done) continue;
-            const double rr = sum_partials(scratch, 2 * r);
+            const double rr = tot[2 * r];
             s.rr = rr;
             s.iters += 1;
             s.relres = sqrt(rr / s.bnorm2);
-            const double rz_new = pw ? sum_partials(scratch, 2 * r + 1) : P * rr;
+            const double rz_new = pw ? tot[2 * r + 1] : P * rr;
             s.beta = rz_new / s.rz;
             s.rz = rz_new;
             if (!isfinite(rr)) {
@@ -269,7 +287,9 @@ k_residual(int L, long long ntri, int R, const cx_t<T> *b, const cx_t<T> *h, cx_
         acc[2 * r + 1] = ab;
     }
     if (block_partials(acc, 2 * R, scratch, ctl)) {
-        for (int q = threadIdx.x; q < 2 * R; q += RED_NT) res[q] = sum_partials(scratch, q);
+        __shared__ double tot[2 * kMaxRhsLocal];
+        block_totals(scratch, 2 * R, tot);
+        for (int q = threadIdx.x; q < 2 * R; q += RED_NT) res[q] = tot[q];
         if (threadIdx.x == 0) ctl->counter = 0;
     }
 }

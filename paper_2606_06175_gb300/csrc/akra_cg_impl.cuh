@@ -20,7 +20,7 @@ struct CgCtl {            // one per solver precision (device)
     double precond;
 };
 
-constexpr int RED_NB = 296;    // reduction blocks (2 per SM on 148+ SMs)
+constexpr int RED_NB = 608;    // vector-kernel blocks (4 per SM on 152 SMs)
 constexpr int RED_NT = 256;
 
 struct CgGraph {
