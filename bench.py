@@ -293,7 +293,9 @@ def main():
     peak = fp32_peak_tflops()
     roofline = {"bound": "alu", "kernel": "k_leg_adjoint<float>" if dom == "legendre_adjoint" else "k_leg_synth<float>",
                 "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None,
+                # DRAM bytes of one launch of the dominant kernel (k_leg_adjoint<float, 4, 1, 128>)
+                # read from an ncu capture (1-pass dram__bytes metrics) at this workload
+                "traffic": 574.87e6 + 786.99e6,
                 "peak_basis": "152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz (unit counts and maximum clock)",
                 "flops_per_launch": flops, "lm_pair_steps_per_launch": steps,
                 "lm_pair_steps_full_triangle": full_steps,
