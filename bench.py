@@ -214,6 +214,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fields", action="store_true",
                     help="also time the E-only solve and the conditional B-mode solve (App. A)")
+    ap.add_argument("--batch-uneven", action="store_true",
+                    help="also time the batched uneven-instance solve: 32 RHS at Nside 1024 / lmax 2048, "
+                         "16 at 512 / 1024, 16 at 256 / 512, one batched mixed solve")
     ap.add_argument("--flat", type=int, default=0, metavar="N",
                     help="also time the flat-sky variant on an N x N grid (mixed solve, H applies)")
     ap.add_argument("--per-l-precond", action="store_true",
@@ -369,6 +372,34 @@ def main():
                  "relres": ip["relres"]}
         A.akra_plan_set_preconditioner(plan, A.PRECOND_SCALAR)
 
+    # ---- batched uneven instances in one persistent launch per step ----
+    batch = None
+    if args.batch_uneven:
+        import synthetic as S
+        spec = [(1024, 2048, 32), (512, 1024, 16), (256, 512, 16)]
+        bplans, bshears = [], []
+        for k, (nb, lb, rb) in enumerate(spec):
+            svb = S.survey(nb, "des", S.SEEDS["batch"] + k)
+            pb = A.akra_plan_create(nb, lb)
+            A.akra_plan_set_weights(pb, torch.from_numpy(svb["ninv"]).to(dev), 1e-3)
+            bplans.append(pb)
+            bshears.append(torch.from_numpy(S.shape_noise(svb["ninv"], svb["rng_noise"], nreal=rb)).to(dev))
+        bt = A.akra_batch_create(bplans, [r for *_, r in spec])
+        A.akra_batch_autotune(bt)
+        A.akra_batch_cg_solve(bt, A.MIXED, bshears, tol=TOL, maxiter=3000)   # capture
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, binfos = A.akra_batch_cg_solve(bt, A.MIXED, bshears, tol=TOL, maxiter=3000)
+        torch.cuda.synchronize()
+        t_b = time.perf_counter() - t0
+        nrhs = sum(r for *_, r in spec)
+        batch = {"instances": [{"nside": nb, "lmax": lb, "rhs": rb} for nb, lb, rb in spec], "rhs": nrhs,
+                 "solve_s": t_b, "s_per_rhs": t_b / nrhs,
+                 "inner_iters": [i["iters"] for i in binfos], "outer": [i["outer"] for i in binfos],
+                 "max_relres": max(max(i["relres_rhs"]) for i in binfos),
+                 "tile": A.akra_batch_describe(bt)}
+        del bt, bplans, bshears
+
     # ---- flat-sky variant (2D FFTs in place of the SHTs): N x N DES-like patch ----
     flat = None
     if args.flat > 0:
@@ -478,6 +509,8 @@ def main():
         line["per_l_preconditioner"] = per_l
     if flat is not None:
         line["flat_sky"] = flat
+    if batch is not None:
+        line["batch_uneven"] = batch
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
