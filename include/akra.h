@@ -104,8 +104,9 @@ akra_status akra_plan_create(int nside, int lmax, akra_plan *out);
  * W = M N^-1 (no pixel-area factor; the unitary transforms carry the normalisation), λ_eff and
  * the scalar P as for the sphere (Eqs. 14-15).  akra_plan_set_weights (d_ninv [n*n]),
  * akra_apply_A / At / H, akra_cg_solve(_b) in F64, F32 and MIXED, akra_shuffle_shear,
- * akra_plan_describe and akra_plan_destroy accept the plan; entry points that need the
- * sphere's spin-2 SHTs return EINVAL.  Errors: EINVAL (n), ENOMEM, ECUDA. */
+ * akra_plan_describe and akra_plan_destroy accept the plan; the other entry points (the
+ * sphere's spin-2 SHTs, tile shapes, batches, field-restricted solves, spectra and the
+ * autograd pair) return EINVAL for it.  Errors: EINVAL (n), ENOMEM, ECUDA. */
 akra_status akra_flat_plan_create(int n, akra_plan *out);
 
 /* Release every device and host resource of the plan (NULL is ignored).  Blocking. */

@@ -863,6 +863,7 @@ extern "C" akra_status akra_cg_solve(akra_plan p, akra_prec prec, const void *d_
 extern "C" akra_status akra_cg_solve_adjoint(akra_plan p, akra_prec prec, const void *d_g, void *d_u, int R,
                                              double tol, int maxiter, akra_cg_info *info, void *stream)
 {
+    AKRA_TRY(reject_flat(p, "akra_cg_solve_adjoint"));
     AKRA_TRY(check_cg(p, prec, d_g, d_u, R, tol, maxiter, "akra_cg_solve_adjoint"));
     cudaStream_t user = (cudaStream_t)stream;
     CgBufs b;

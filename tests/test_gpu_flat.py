@@ -107,4 +107,6 @@ def test_flat_rejects_sphere_only_calls(flat256):
     with pytest.raises(A.AkraError):
         A.akra_cg_solve_fields(p, A.F64, A.SOLVE_E, torch.from_numpy(y[None]).to(DEV), tol=1e-6)
     with pytest.raises(A.AkraError):
+        A.akra_cg_solve_adjoint(p, A.F64, x, tol=1e-6)
+    with pytest.raises(A.AkraError):
         A.akra_flat_plan_create(100)
