@@ -303,15 +303,6 @@ akra_status akra_cl_spectra(akra_plan plan, akra_prec prec, const void *d_a, con
  * and 0 < inner_factor <= 1. */
 akra_status akra_set_mixed_policy(double inner_floor, double inner_factor);
 
-/* How the mixed-precision solves use their FP64 residuals.  on = 0 (default): classic
- * iterative refinement (Sec. II C) -- every outer step restarts the FP32 CG from zero on the
- * normalised FP64 residual.  on = 1: the FP32 CG is continued instead; at each outer step its
- * residual is replaced by the FP64 one (in the units of the first residual), its iterate,
- * already added to the FP64 solution, is zeroed, and its search direction is kept, so the
- * Krylov space built so far is not thrown away.  The FP64 residual still decides convergence.
- * Process-wide.  Errors: EINVAL unless on is 0 or 1. */
-akra_status akra_set_mixed_continue(int on);
-
 /* Host-side wall-clock budget (seconds, > 0) for blocking solves; default 3600. */
 akra_status akra_set_timeout(double seconds);
 

@@ -55,7 +55,7 @@ EXPORTS = ["akra_plan_create", "akra_plan_destroy", "akra_last_error", "akra_ver
            "akra_batch_apply_H", "akra_batch_cg_solve", "akra_batch_describe",
            "akra_plan_get_shape", "akra_plan_set_shape", "akra_set_mixed_policy", "akra_fma_rate",
            "akra_cg_solve_fields", "akra_shuffle_shear", "akra_cl_spectra",
-           "akra_plan_set_preconditioner", "akra_flat_plan_create", "akra_set_mixed_continue"]
+           "akra_plan_set_preconditioner", "akra_flat_plan_create"]
 
 _lib_handle = None
 
@@ -94,7 +94,6 @@ def load(build_if_missing: bool = False):
         "akra_cg_solve_fields": ([vp, i, i, vp, vp, i, d, i, ctypes.POINTER(CgInfo), vp], i),
         "akra_set_timeout": ([d], i),
         "akra_set_mixed_policy": ([d, d], i),
-        "akra_set_mixed_continue": ([i], i),
         "akra_plan_set_preconditioner": ([vp, i], i),
         "akra_shuffle_shear": ([vp, i, vp, vp, vp, i, vp], i),
         "akra_cl_spectra": ([vp, i, vp, vp, i, i, ctypes.POINTER(d), vp, vp], i),
@@ -371,12 +370,6 @@ def akra_weight_grad(plan: Plan, prec: int, Au: torch.Tensor, y: torch.Tensor, A
 
 def akra_set_timeout(seconds: float):
     _check(load().akra_set_timeout(float(seconds)))
-
-
-def akra_set_mixed_continue(on: bool):
-    """Mixed solves: restart the FP32 CG at each outer step (False, default) or continue it with
-    its residual replaced by the FP64 one (True)."""
-    _check(load().akra_set_mixed_continue(int(on)))
 
 
 def akra_set_mixed_policy(inner_floor: float = 0.0, inner_factor: float = 0.5):

@@ -294,66 +294,6 @@ k_residual(int L, long long ntri, int R, const cx_t<T> *b, const cx_t<T> *h, cx_
     }
 }
 
-// Continued refinement: replace the FP32 CG residual by the FP64 true residual r64 (in the
-// units of the first residual, s_r = ||r0_r||), zero the FP32 iterate (already added to x64),
-// and make the next direction p = P r + β' p from the kept p with β' = <r, P r> / rz_prev.
-// RHS with ptol[r] < 0 stay finished.
-template <typename T>
-__global__ void __launch_bounds__(RED_NT)
-k_cg_replace(int L, long long ntri, const double2 *r64, const double *res0, const double *ptol,
-             cx_t<T> *r, cx_t<T> *x, CgState *st, CgCtl *ctl, double *scratch, const T *pw, int maxiter)
-{
-    const int R = ctl->R;
-    const T P = (T)ctl->precond;
-    double acc[2 * kMaxRhsLocal];
-    for (int q = 0; q < R; q++) {
-        double rr = 0, rz = 0;
-        const bool act = ptol[q] >= 0;
-        const double s = res0[2 * q] > 0 ? 1.0 / sqrt(res0[2 * q]) : 0.0;
-        AKRA_FOR_RHS_ELEMENTS(q) {
-            x[o] = cx_t<T>{0, 0};   // every RHS: the last correction is already in x64
-            if (act) {
-                const double2 v = r64[o];
-                const cx_t<T> w{(T)(v.x * s), (T)(v.y * s)};
-                r[o] = w;
-                const double d = wdot<T>(j <= L, w, w);
-                rr += d;
-                rz += (double)pweight(pw, j, P) * d;
-            }
-        }
-        acc[2 * q] = rr;
-        acc[2 * q + 1] = rz;
-    }
-    if (block_partials(acc, 2 * R, scratch, ctl)) {
-        __shared__ double tot[2 * kMaxRhsLocal];
-        block_totals(scratch, 2 * R, tot);
-        for (int q = threadIdx.x; q < R; q += RED_NT) {
-            if (ptol[q] < 0) {
-                st[q].done = 1;
-                continue;
-            }
-            CgState s = st[q];
-            const double rz_prev = (s.beta > 0 && s.rz > 0) ? s.rz / s.beta : 0.0;
-            s.rr = tot[2 * q];
-            s.relres = sqrt(s.rr / s.bnorm2);
-            s.beta = rz_prev > 0 ? tot[2 * q + 1] / rz_prev : 0.0;
-            s.rz = tot[2 * q + 1];
-            s.tol = ptol[q];
-            s.status = AKRA_OK;
-            s.done = s.relres < s.tol ? 1 : 0;
-            st[q] = s;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            int all = 1;
-            for (int q = 0; q < R; q++) all &= st[q].done;
-            ctl->all_done = all;
-            ctl->maxiter = maxiter;
-            ctl->counter = 0;
-        }
-    }
-}
-
 // r32 = (float) (r64 * s_r), s_r = 1/||r64_r||  (per RHS scale from res[2r])
 __global__ void k_cast_scaled(long long n, int R, const double2 *r64, const double *res, float2 *r32)
 {
@@ -394,9 +334,8 @@ akra_status cg_reserve(akra_plan p, int R, CgBufs &b)
     const size_t V32 = (size_t)R * 2 * p->ntri * sizeof(float2);
     AKRA_TRY(ws_reserve(p, p->cg, 5 * V64 + 5 * V32));
     const size_t nst = (size_t)kMaxRhsLocal;
-    // after the partials: res [2 nst], res0 [2 nst] (the first residual's norms), ptol [nst]
     const size_t red = 2 * nst * sizeof(CgState) + 2 * 64 + (size_t)RED_NB * 2 * nst * sizeof(double) +
-                       5 * nst * sizeof(double);
+                       2 * nst * sizeof(double);
     AKRA_TRY(ws_reserve(p, p->red, red));
     char *c = (char *)p->cg.ptr;
     for (int i = 0; i < 5; i++) b.v64[i] = c + i * V64;
@@ -481,9 +420,6 @@ double g_timeout_s = 3600.0;
 // floor <= 0 selects the automatic floor, the FP32 operator's own accuracy (below it the FP32
 // CG gains nothing on the FP64 residual): 0.1 · 2^-24 · lmax, within [5e-6, 1e-3].
 double g_inner_floor = 0.0, g_inner_factor = 0.5;
-// MIXED: 0 = restart the FP32 CG at every outer step (classic iterative refinement),
-// 1 = continue it, replacing its residual by the FP64 one (the Krylov space is kept)
-int g_mixed_continue = 0;
 
 double inner_floor(int lmax)
 {
@@ -512,49 +448,18 @@ akra_status bounded_wait(cudaEvent_t ev, std::chrono::steady_clock::time_point d
 // run CG for precision T on the plan-owned vectors (b already in slot 0); returns the per-RHS
 // states in host memory hst[R]
 template <typename T>
-static akra_status cg_iterate(akra_plan p, int R, CgBufs &b, cudaGraphExec_t exec, int maxiter,
-                              CgState *hst, std::chrono::steady_clock::time_point deadline);
-
-template <typename T>
 static akra_status cg_run(akra_plan p, int R, CgBufs &b, double tol, int maxiter, CgState *hst,
                           std::chrono::steady_clock::time_point deadline)
 {
     cudaGraphExec_t exec;
     AKRA_TRY(cg_graph<T>(p, R, b, &exec));
-    AKRA_TRY(cg_launch_init<T>(p, R, b, tol, maxiter, p->stream));
-    return cg_iterate<T>(p, R, b, exec, maxiter, hst, deadline);
-}
-
-// continue the FP32 CG after an FP64 residual: replace its residual (k_cg_replace), update the
-// direction, iterate; ptol (device, per RHS) holds the phase tolerances, < 0 for finished RHS
-static akra_status cg_continue32(akra_plan p, int R, CgBufs &b, const double *res0, const double *ptol,
-                                 int maxiter, CgState *hst, std::chrono::steady_clock::time_point deadline)
-{
-    cudaGraphExec_t exec;
-    AKRA_TRY(cg_graph<float>(p, R, b, &exec));
-    cudaStream_t cs = p->stream;
-    void **v = b.v32;
-    k_cg_replace<float><<<RED_NB, RED_NT, 0, cs>>>(p->lmax, p->ntri, (const double2 *)b.v64[2], res0, ptol,
-                                                   (float2 *)v[2], (float2 *)v[1], b.st[1], b.ctl[1],
-                                                   b.scratch, pw_ptr<float>(p), maxiter);
-    AKRA_CUDA_TRY(cudaGetLastError());
-    k_cg_update_p<float><<<RED_NB, RED_NT, 0, cs>>>(p->ntri, (const float2 *)v[2], (float2 *)v[3], b.st[1],
-                                                    b.ctl[1], pw_ptr<float>(p));
-    AKRA_CUDA_TRY(cudaGetLastError());
-    p->launches += 2;
-    return cg_iterate<float>(p, R, b, exec, maxiter, hst, deadline);
-}
-
-// launch captured iterations until every RHS is done (the state is already initialised)
-template <typename T>
-static akra_status cg_iterate(akra_plan p, int R, CgBufs &b, cudaGraphExec_t exec, int maxiter,
-                              CgState *hst, std::chrono::steady_clock::time_point deadline)
-{
     const long long per_iter =
         p->graphs[((long long)p->fields << 40) | ((long long)PrecIdx<T>::v << 32) | (long long)R]->kernels;
+    void **v = vecs<T>(b);
     CgState *st = b.st[PrecIdx<T>::v];
     CgCtl *ctl = b.ctl[PrecIdx<T>::v];
     cudaStream_t cs = p->stream;
+    AKRA_TRY(cg_launch_init<T>(p, R, b, tol, maxiter, cs));
     int *h_done = (int *)p->h_pinned;
     int launched = 0;
     int chunk = 2;
@@ -663,10 +568,6 @@ static akra_status solve_b(akra_plan p, akra_prec prec, const void *bsrc, void *
         AKRA_CUDA_TRY(cudaMemcpyAsync(hres.data(), b.res, sizeof(double) * 2 * R, cudaMemcpyDeviceToHost, cs));
         AKRA_CUDA_TRY(cudaEventRecord(p->ev_a, cs));
         AKRA_TRY(bounded_wait(p->ev_a, deadline));
-        // norms of the first residual: a continued FP32 CG keeps the units of its first system
-        double *res0 = b.res + 2 * kMaxRhsLocal, *ptol = b.res + 4 * kMaxRhsLocal;
-        AKRA_CUDA_TRY(cudaMemcpyAsync(res0, b.res, sizeof(double) * 2 * R, cudaMemcpyDeviceToDevice, cs));
-        std::vector<int> iters_before(R, 0);
         const int max_outer = 30;
         double worst = 0;
         for (int r = 0; r < R; r++) {
@@ -682,34 +583,22 @@ static akra_status solve_b(akra_plan p, akra_prec prec, const void *bsrc, void *
             }
             // inner tolerance: what this outer step must gain, but not below FP32 reach
             const double tin = std::max(inner_floor(p->lmax), std::min(0.1, g_inner_factor * tol / worst));
-            const bool cont = g_mixed_continue && outer > 0;
-            if (!cont) {
-                // restart: FP32 CG on r / ||r|| from zero
-                k_cast_scaled<<<RED_NB, RED_NT, 0, cs>>>(2 * p->ntri, R, (const double2 *)r64, b.res,
-                                                         (float2 *)b.v32[0]);
-                AKRA_CUDA_TRY(cudaGetLastError());
-                p->launches++;
-                AKRA_TRY(cg_run<float>(p, R, b, tin, inner_budget, hst.data(), deadline));
-            } else {
-                // continue: same target in the first residual's units (r0 = b, so relres itself)
-                std::vector<double> pt(R);
-                for (int r = 0; r < R; r++) pt[r] = relres[r] < tol ? -1.0 : tin * relres[r];
-                AKRA_CUDA_TRY(cudaMemcpyAsync(ptol, pt.data(), sizeof(double) * R, cudaMemcpyHostToDevice, cs));
-                AKRA_TRY(cg_continue32(p, R, b, res0, ptol, maxiter, hst.data(), deadline));
-            }
+            k_cast_scaled<<<RED_NB, RED_NT, 0, cs>>>(2 * p->ntri, R, (const double2 *)r64, b.res,
+                                                     (float2 *)b.v32[0]);
+            AKRA_CUDA_TRY(cudaGetLastError());
+            p->launches++;
+            AKRA_TRY(cg_run<float>(p, R, b, tin, inner_budget, hst.data(), deadline));
             int it = 0;
             for (int r = 0; r < R; r++) {
-                const int done_now = cont ? hst[r].iters - iters_before[r] : hst[r].iters;
-                it = std::max(it, done_now);
-                iters[r] += done_now;
-                iters_before[r] = hst[r].iters;
+                it = std::max(it, hst[r].iters);
+                iters[r] += hst[r].iters;
                 if (hst[r].status == AKRA_ENUMERIC) status[r] = AKRA_ENUMERIC;
             }
             total_iters += it;
             h32 += it;
             inner_budget -= it;
-            k_axpy_mixed<<<RED_NB, RED_NT, 0, cs>>>(2 * p->ntri, R, (const float2 *)b.v32[1],
-                                                    g_mixed_continue ? res0 : b.res, (double2 *)x64);
+            k_axpy_mixed<<<RED_NB, RED_NT, 0, cs>>>(2 * p->ntri, R, (const float2 *)b.v32[1], b.res,
+                                                    (double2 *)x64);
             AKRA_CUDA_TRY(cudaGetLastError());
             p->launches++;
             AKRA_TRY(true_residual<double>(p, R, b, b64, x64, t64, r64, hres.data(), deadline));
@@ -923,16 +812,6 @@ extern "C" akra_status akra_set_mixed_policy(double inner_floor, double inner_fa
     }
     g_inner_floor = inner_floor;
     g_inner_factor = inner_factor;
-    return AKRA_OK;
-}
-
-extern "C" akra_status akra_set_mixed_continue(int on)
-{
-    if (on != 0 && on != 1) {
-        set_error("akra_set_mixed_continue: on must be 0 or 1");
-        return AKRA_EINVAL;
-    }
-    g_mixed_continue = on;
     return AKRA_OK;
 }
 

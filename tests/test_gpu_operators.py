@@ -258,27 +258,6 @@ def test_cg_mixed_cap32_matches_oracle(cap32_ref):
     assert rel(x[0].cpu().numpy(), xref) < 1e-6
 
 
-@pytest.mark.parametrize("R", [1, 3])
-def test_cg_mixed_continued_matches_oracle(cap32_ref, R):
-    """Continued refinement (FP32 CG kept across outer steps, residual replaced by the FP64 one):
-    same solution as the oracle, converged in FP64, every RHS."""
-    wl, N, L, y, xref, _, _ = cap32_ref
-    p = A.akra_plan_create(N, L)
-    A.akra_plan_set_weights(p, torch.from_numpy(wl["ninv"]).to(DEV), 1e-3)
-    ys = np.stack([y * (1.0 + 0.5 * r) for r in range(R)])
-    A.akra_set_mixed_continue(True)
-    try:
-        x, info = A.akra_cg_solve(p, A.MIXED, torch.from_numpy(ys).to(DEV), tol=1e-9, maxiter=3000)
-    finally:
-        A.akra_set_mixed_continue(False)
-    assert info["status"] == 0 and info["relres"] < 1e-9 and info["outer"] >= 2, info
-    xs = x.cpu().numpy()
-    for r in range(R):
-        assert rel(xs[r], (1.0 + 0.5 * r) * xref) < 1e-6
-    with pytest.raises(A.AkraError):
-        A.akra_set_mixed_continue(2)
-
-
 def test_cg_fp32_cap32_close_to_oracle(cap32_ref):
     wl, N, L, y, xref, _, _ = cap32_ref
     p = A.akra_plan_create(N, L)
