@@ -18,8 +18,7 @@ Operator chain (Sec. II B, "The storage problem"):
 --×W-->  --exact transpose-->  (Hx) + λ_eff x`` (Eq. 14), solved by PCG
 (Sec. II B, "The inversion problem"; preconditioner Eq. 15).
 
-Readings where the paper is silent or inconsistent (each is also listed in
-DESIGN.md):
+Readings where the paper is silent or inconsistent:
   * KS sign: Eq. 3, γ_{±2,lm} = D_l κ_lm, i.e. a_E = -D_l κ_E and likewise for B.
   * W_p = ω M_p N^{-1}_p with ω = 4π/N_pix; λ_eff = λ · mean of N^{-1} over the
     unmasked pixels; preconditioner P = 1/(mean over all pixels of M N^{-1} + λ_eff).
