@@ -6,6 +6,8 @@
 //   * n a power of two: in-place radix-4/2 decimation in frequency (natural -> bit-reversed)
 //     for the backward DFT and decimation in time (bit-reversed -> natural) for the forward
 //     one, so W is applied to the bit-reversed pixel order and no permutation pass is needed;
+//     pairs of radix-4 stages run as one pass through shared memory (each thread keeps the
+//     16 elements of both stages in registers), so n = 8192 takes 4 passes instead of 7;
 //   * any other n (polar rings n = 4i): Bluestein's chirp-z form,
 //       X_k = conj(c_k) Σ_j [x_j conj(c_j)] c_{k-j},  c_j = e^{iπ j²/n},
 //     a cyclic convolution of length M = 2^⌈log2(2n-1)⌉ done by the same DIF/DIT pair, with
@@ -121,7 +123,7 @@ akra_status ring_fft32_build(akra_plan p)
 }
 
 // Order a ring list for the FP32 FFT launches: rings whose convolution length M is at most
-// fft32_msmall first (their launch reserves less shared memory, so two 1024-thread blocks
+// fft32_msmall first (their launch reserves less shared memory, so two blocks
 // fit on an SM), then those with M = fft32_mmax.  Writes the list to d_out (device).
 akra_status ring_fft32_order(akra_plan p, const std::vector<int> &rings, int *d_out, int *nsmall)
 {

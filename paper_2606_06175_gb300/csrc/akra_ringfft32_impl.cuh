@@ -5,7 +5,7 @@
 
 namespace akra {
 
-constexpr int F32_NT = 1024;
+constexpr int F32_NT = 512;
 constexpr int F32_MMAX = 8 * kMaxNside;   // largest convolution length (n <= 4 nside - 4)
 
 __device__ __forceinline__ float2 cm(float2 a, float2 b)
@@ -33,6 +33,36 @@ __device__ __forceinline__ float2 w_pow2(const float2 *__restrict__ tw2, int t, 
     return w;
 }
 
+// radix-4 DIF butterfly on (a0..a3) = x[t + k q] of a length-L stage, in place: the outputs go
+// where the in-place DIF keeps them (slot 1 holds the k = 2 output, slot 2 the k = 1 one),
+// twiddled by w1 = w^i, w2 = w^{2i}, w3 = w^{3i} of length L
+template <int S>
+__device__ __forceinline__ void dif4(float2 &a0, float2 &a1, float2 &a2, float2 &a3, float2 w1, float2 w2,
+                                     float2 w3)
+{
+    const float2 u0 = cadd(a0, a2), u1 = cadd(a1, a3), d0 = csub(a0, a2);
+    const float2 d1 = mul_si<S>(csub(a1, a3));
+    a0 = cadd(u0, u1);
+    a1 = cm(csub(u0, u1), w2);
+    a2 = cm(cadd(d0, d1), w1);
+    a3 = cm(csub(d0, d1), w3);
+}
+
+// radix-4 DIT butterfly (the inverse arrangement of dif4), w1 = w^i, w2 = w^{2i} of length L
+template <int S>
+__device__ __forceinline__ void dit4(float2 &p0, float2 &p1, float2 &p2, float2 &p3, float2 w1, float2 w2)
+{
+    float2 u = cm(p1, w2);
+    const float2 u0 = cadd(p0, u), u1 = csub(p0, u);
+    u = cm(p3, w2);
+    const float2 u2 = cadd(p2, u), u3 = csub(p2, u);
+    const float2 v2 = cm(u2, w1), v3 = mul_si<S>(cm(u3, w1));
+    p0 = cadd(u0, v2);
+    p2 = csub(u0, v2);
+    p1 = cadd(u1, v3);
+    p3 = csub(u1, v3);
+}
+
 // Shared-memory slot of element i: one float2 of padding after every 16, so that the radix-4
 // passes with element strides 1 and 4 (and every larger power of two) hit distinct banks.
 __host__ __device__ constexpr int f32_slots(int m) { return m + (m >> 4); }
@@ -53,20 +83,43 @@ __device__ void dif(float2 *x, int M, int logM, const float2 *__restrict__ tw2)
         __syncthreads();
         L = h;
     }
-    for (; L >= 4; L >>= 2) {
-        const int q = L >> 2;
-        for (int b = threadIdx.x; b < (M >> 2); b += blockDim.x) {
-            const int blk = b / q, i = b - blk * q;
+    // two radix-4 stages (lengths L and L/4) per pass: a thread holds the 16 elements t + j·L/16,
+    // which form four groups of the first stage (j mod 4 fixed) and, after it, four groups of the
+    // second (j div 4 fixed); results land where two separate passes would put them
+    for (; L >= 16; L >>= 4) {
+        const int q = L >> 4, lq = 31 - __clz(q);
+        for (int b = threadIdx.x; b < (M >> 4); b += blockDim.x) {
+            const int blk = b >> lq, i = b & (q - 1);
             const int t = blk * L + i;
-            const float2 a0 = x[pd(t)], a1 = x[pd(t + q)], a2 = x[pd(t + 2 * q)], a3 = x[pd(t + 3 * q)];
-            const float2 w1 = w_pow2<S>(tw2, i, L), w2 = w_pow2<S>(tw2, 2 * i, L),
-                         w3 = w_pow2<S>(tw2, 3 * i, L);
-            const float2 u0 = cadd(a0, a2), u1 = cadd(a1, a3), d0 = csub(a0, a2);
-            const float2 d1 = mul_si<S>(csub(a1, a3));
-            x[pd(t)] = cadd(u0, u1);
-            x[pd(t + q)] = cm(csub(u0, u1), w2);
-            x[pd(t + 2 * q)] = cm(cadd(d0, d1), w1);
-            x[pd(t + 3 * q)] = cm(csub(d0, d1), w3);
+            float2 v[16];
+#pragma unroll
+            for (int j = 0; j < 16; j++) v[j] = x[pd(t + j * q)];
+#pragma unroll
+            for (int j1 = 0; j1 < 4; j1++) {
+                const int i1 = i + j1 * q;
+                dif4<S>(v[j1], v[j1 + 4], v[j1 + 8], v[j1 + 12], w_pow2<S>(tw2, i1, L),
+                        w_pow2<S>(tw2, 2 * i1, L), w_pow2<S>(tw2, 3 * i1, L));
+            }
+            const int L2 = L >> 2;
+            const float2 w1 = w_pow2<S>(tw2, i, L2), w2 = w_pow2<S>(tw2, 2 * i, L2),
+                         w3 = w_pow2<S>(tw2, 3 * i, L2);
+#pragma unroll
+            for (int j2 = 0; j2 < 4; j2++) dif4<S>(v[4 * j2], v[4 * j2 + 1], v[4 * j2 + 2], v[4 * j2 + 3], w1, w2, w3);
+#pragma unroll
+            for (int j = 0; j < 16; j++) x[pd(t + j * q)] = v[j];
+        }
+        __syncthreads();
+    }
+    if (L == 4) {
+        for (int b = threadIdx.x; b < (M >> 2); b += blockDim.x) {
+            const int t = 4 * b;
+            float2 a0 = x[pd(t)], a1 = x[pd(t + 1)], a2 = x[pd(t + 2)], a3 = x[pd(t + 3)];
+            const float2 one = make_float2(1.f, 0.f);
+            dif4<S>(a0, a1, a2, a3, one, one, one);
+            x[pd(t)] = a0;
+            x[pd(t + 1)] = a1;
+            x[pd(t + 2)] = a2;
+            x[pd(t + 3)] = a3;
         }
         __syncthreads();
     }
@@ -77,22 +130,45 @@ template <int S>
 __device__ void dit(float2 *x, int M, int logM, const float2 *__restrict__ tw2)
 {
     const int Lmax = (logM & 1) ? (M >> 1) : M;
-    for (int L = 4; L <= Lmax; L <<= 2) {
+    int L = 4;
+    // two radix-4 stages (lengths L and 4L) per pass: a thread holds the 16 elements t + j·L/4 of
+    // one 4L block, four groups of the first stage (j div 4 fixed), then four of the second
+    // (j mod 4 fixed)
+    for (; 4 * L <= Lmax; L <<= 4) {
+        const int q = L >> 2, lq = 31 - __clz(q);
+        for (int b = threadIdx.x; b < (M >> 4); b += blockDim.x) {
+            const int blk = b >> lq, i = b & (q - 1);
+            const int t = blk * 4 * L + i;
+            float2 v[16];
+#pragma unroll
+            for (int j = 0; j < 16; j++) v[j] = x[pd(t + j * q)];
+            {
+                const float2 w1 = w_pow2<S>(tw2, i, L), w2 = w_pow2<S>(tw2, 2 * i, L);
+#pragma unroll
+                for (int j2 = 0; j2 < 4; j2++) dit4<S>(v[4 * j2], v[4 * j2 + 1], v[4 * j2 + 2], v[4 * j2 + 3], w1, w2);
+            }
+#pragma unroll
+            for (int j1 = 0; j1 < 4; j1++) {
+                const int i1 = i + j1 * q;
+                dit4<S>(v[j1], v[j1 + 4], v[j1 + 8], v[j1 + 12], w_pow2<S>(tw2, i1, 4 * L),
+                        w_pow2<S>(tw2, 2 * i1, 4 * L));
+            }
+#pragma unroll
+            for (int j = 0; j < 16; j++) x[pd(t + j * q)] = v[j];
+        }
+        __syncthreads();
+    }
+    if (L <= Lmax) {   // one radix-4 stage left (length L)
         const int q = L >> 2;
         for (int b = threadIdx.x; b < (M >> 2); b += blockDim.x) {
             const int blk = b / q, i = b - blk * q;
             const int t = blk * L + i;
-            const float2 p0 = x[pd(t)], p1 = x[pd(t + q)], p2 = x[pd(t + 2 * q)], p3 = x[pd(t + 3 * q)];
-            const float2 w1 = w_pow2<S>(tw2, i, L), w2 = w_pow2<S>(tw2, 2 * i, L);
-            float2 u = cm(p1, w2);
-            const float2 u0 = cadd(p0, u), u1 = csub(p0, u);
-            u = cm(p3, w2);
-            const float2 u2 = cadd(p2, u), u3 = csub(p2, u);
-            const float2 v2 = cm(u2, w1), v3 = mul_si<S>(cm(u3, w1));
-            x[pd(t)] = cadd(u0, v2);
-            x[pd(t + 2 * q)] = csub(u0, v2);
-            x[pd(t + q)] = cadd(u1, v3);
-            x[pd(t + 3 * q)] = csub(u1, v3);
+            float2 p0 = x[pd(t)], p1 = x[pd(t + q)], p2 = x[pd(t + 2 * q)], p3 = x[pd(t + 3 * q)];
+            dit4<S>(p0, p1, p2, p3, w_pow2<S>(tw2, i, L), w_pow2<S>(tw2, 2 * i, L));
+            x[pd(t)] = p0;
+            x[pd(t + q)] = p1;
+            x[pd(t + 2 * q)] = p2;
+            x[pd(t + 3 * q)] = p3;
         }
         __syncthreads();
     }
