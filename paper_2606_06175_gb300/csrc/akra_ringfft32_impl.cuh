@@ -33,6 +33,19 @@ __device__ __forceinline__ float2 w_pow2(const float2 *__restrict__ tw2, int t, 
     return w;
 }
 
+// e^{S 2πi m/16} for 0 <= m < 16 (m is a compile-time constant after unrolling):
+// cos(2πm/16) from cos 0, cos π/8, cos π/4, cos 3π/8, cos π/2 by symmetry, sin(2πm/16) =
+// cos(2π(m-4)/16)
+__device__ __forceinline__ constexpr float cos16(int m)
+{
+    constexpr float c[5] = {1.0f, 0.923879532511286756f, 0.707106781186547524f, 0.382683432365089772f, 0.0f};
+    return m <= 4 ? c[m] : m <= 8 ? -c[8 - m] : m <= 12 ? -c[m - 8] : c[16 - m];
+}
+template <int S> __device__ __forceinline__ float2 root16(int m)
+{
+    return make_float2(cos16(m & 15), S * cos16((m + 12) & 15));
+}
+
 // radix-4 DIF butterfly on (a0..a3) = x[t + k q] of a length-L stage, in place: the outputs go
 // where the in-place DIF keeps them (slot 1 holds the k = 2 output, slot 2 the k = 1 one),
 // twiddled by w1 = w^i, w2 = w^{2i}, w3 = w^{3i} of length L
@@ -94,11 +107,15 @@ __device__ void dif(float2 *x, int M, int logM, const float2 *__restrict__ tw2)
             float2 v[16];
 #pragma unroll
             for (int j = 0; j < 16; j++) v[j] = x[pd(t + j * q)];
+            {
+                // twiddles of group j1 (index i + j1·L/16): w^{k i} · e^{S 2πi k j1/16}
+                const float2 b1 = w_pow2<S>(tw2, i, L), b2 = w_pow2<S>(tw2, 2 * i, L),
+                             b3 = w_pow2<S>(tw2, 3 * i, L);
+                dif4<S>(v[0], v[4], v[8], v[12], b1, b2, b3);
 #pragma unroll
-            for (int j1 = 0; j1 < 4; j1++) {
-                const int i1 = i + j1 * q;
-                dif4<S>(v[j1], v[j1 + 4], v[j1 + 8], v[j1 + 12], w_pow2<S>(tw2, i1, L),
-                        w_pow2<S>(tw2, 2 * i1, L), w_pow2<S>(tw2, 3 * i1, L));
+                for (int j1 = 1; j1 < 4; j1++)
+                    dif4<S>(v[j1], v[j1 + 4], v[j1 + 8], v[j1 + 12], cm(b1, root16<S>(j1)),
+                            cm(b2, root16<S>(2 * j1)), cm(b3, root16<S>(3 * j1)));
             }
             const int L2 = L >> 2;
             const float2 w1 = w_pow2<S>(tw2, i, L2), w2 = w_pow2<S>(tw2, 2 * i, L2),
@@ -147,11 +164,13 @@ __device__ void dit(float2 *x, int M, int logM, const float2 *__restrict__ tw2)
 #pragma unroll
                 for (int j2 = 0; j2 < 4; j2++) dit4<S>(v[4 * j2], v[4 * j2 + 1], v[4 * j2 + 2], v[4 * j2 + 3], w1, w2);
             }
+            {
+                // twiddles of group j1 (index i + j1·L/4 of length 4L): w^{k i} · e^{S 2πi k j1/16}
+                const float2 b1 = w_pow2<S>(tw2, i, 4 * L), b2 = w_pow2<S>(tw2, 2 * i, 4 * L);
+                dit4<S>(v[0], v[4], v[8], v[12], b1, b2);
 #pragma unroll
-            for (int j1 = 0; j1 < 4; j1++) {
-                const int i1 = i + j1 * q;
-                dit4<S>(v[j1], v[j1 + 4], v[j1 + 8], v[j1 + 12], w_pow2<S>(tw2, i1, 4 * L),
-                        w_pow2<S>(tw2, 2 * i1, 4 * L));
+                for (int j1 = 1; j1 < 4; j1++)
+                    dit4<S>(v[j1], v[j1 + 4], v[j1 + 8], v[j1 + 12], cm(b1, root16<S>(j1)), cm(b2, root16<S>(2 * j1)));
             }
 #pragma unroll
             for (int j = 0; j < 16; j++) x[pd(t + j * q)] = v[j];
