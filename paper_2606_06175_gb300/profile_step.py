@@ -2,7 +2,13 @@
 (or one mixed solve) -- a small, self-contained command for Nsight Compute captures.
 
     python -m paper_2606_06175_gb300.profile_step --nside 1024 --lmax 2048 --prec f32 --reps 2
+
+`--cufft` instead times the library's FP32 ring-FFT stage (fold, backward DFT, ×W, forward
+DFT, unfold on every ring that holds a weighted pixel) next to cuFFT (through torch.fft) doing
+only the two DFTs and the ×W on the same rings, grouped by ring length; a timed comparison,
+cuFFT is not used by the library.
 """
+import json
 import argparse
 import os
 import sys
@@ -27,6 +33,8 @@ def main():
                     help="H applications of the flat-sky variant on an N x N grid instead")
     ap.add_argument("--shape", type=int, nargs=3, metavar=("P", "PA", "RG"),
                     help="force the Legendre tile shape of --prec (R = 1)")
+    ap.add_argument("--cufft", action="store_true",
+                    help="time the FP32 ring-FFT stage against cuFFT on the same rings")
     args = ap.parse_args()
     N, L = args.nside, args.lmax
     dev = torch.device("cuda", 0)
@@ -49,6 +57,9 @@ def main():
         A.akra_plan_set_shape(plan, prec, 1, *args.shape)
     kE = S.grf_alm(L, S.cl_kappa(L), sv["rng_alm"])
     x64 = torch.from_numpy(np.stack([kE, np.zeros_like(kE)])[None]).to(dev)
+    if args.cufft:
+        print(json.dumps(cufft_comparison(plan, sv["ninv"], N, dev)))
+        return
     if args.solve:
         y = A.akra_apply_A(plan, A.F64, x64)
         _, info = A.akra_cg_solve(plan, A.MIXED, y, tol=1e-6, maxiter=2000)
@@ -59,6 +70,56 @@ def main():
             A.akra_apply_H(plan, prec, x)
     torch.cuda.synchronize()
     print("ok", A.akra_plan_describe(plan)["kernel_launches"])
+
+
+def ring_table(N):
+    """HEALPix RING rings (i = 1 .. 4N-1): (first pixel, number of pixels)."""
+    npix = 12 * N * N
+    out = []
+    for i in range(1, 4 * N):
+        if i < N:
+            out.append((2 * i * (i - 1), 4 * i))
+        elif i <= 3 * N:
+            out.append((2 * N * (N - 1) + 4 * N * (i - N), 4 * N))
+        else:
+            k = 4 * N - i
+            out.append((npix - 2 * k * (k + 1), 4 * k))
+    return out
+
+
+def cufft_comparison(plan, ninv, N, dev, reps=5):
+    ours = A.akra_time_H_stages(plan, A.F32, 1, reps)["ring_fft"]
+    groups = {}
+    for first, n in ring_table(N):
+        if np.any(ninv[first:first + n] > 0):
+            groups.setdefault(n, []).append(first)
+    w = torch.from_numpy((4 * np.pi / ninv.size) * ninv).to(dev, torch.float32)
+    g = torch.Generator(device="cpu").manual_seed(7)
+    data = []
+    for n, firsts in sorted(groups.items()):
+        idx = (torch.tensor(firsts)[:, None] + torch.arange(n)[None, :]).to(dev)
+        x = torch.randn(len(firsts), n, generator=g, dtype=torch.complex64).to(dev)
+        data.append((n, x, w[idx]))
+
+    def run(sel):
+        for n, x, wg in sel:
+            y = torch.fft.ifft(x, norm="forward") * wg   # backward DFT (no 1/n), then ×W
+            torch.fft.fft(y)                            # forward DFT
+    belt = [d for d in data if d[0] == 4 * N]
+    out = {"nside": N, "active_rings": sum(d[1].shape[0] for d in data), "ring_lengths": len(data),
+           "belt_rings": sum(d[1].shape[0] for d in belt), "ring_fft_stage_ms": ours}
+    for key, sel in (("cufft_all_rings_ms", data), ("cufft_belt_rings_ms", belt)):
+        for _ in range(3):
+            run(sel)   # plans are created and cached here
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            run(sel)
+        e1.record()
+        torch.cuda.synchronize()
+        out[key] = e0.elapsed_time(e1) / reps
+    return out
 
 
 if __name__ == "__main__":
