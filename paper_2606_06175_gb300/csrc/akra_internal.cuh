@@ -132,7 +132,7 @@ struct Fft32Args {
     const float2 *bhat_all;
     const float2 *tw2;
     const float2 *tw_all;
-    const float *W;
+    const float *W;          // FP32 W in the FFT's pixel order (bit-reversed in power-of-two rings)
     int weighted;
     float2 *phi;
     const float *map_in;
@@ -213,6 +213,8 @@ struct akra_plan_s {
     double lambda = 0, lambda_eff = 0, precond = 1, omega = 0;
     double *d_W64 = nullptr;                 // [npix] ω M N^-1
     float *d_W32 = nullptr;
+    float *d_W32r = nullptr;                 // [npix] W in the FP32 ring FFT's pixel order
+                                             // (bit-reversed within power-of-two rings)
     int *d_active_rings = nullptr;           // rings with any W != 0
     int n_active_rings = 0;
     int *d_active_units = nullptr;           // units with an active ring

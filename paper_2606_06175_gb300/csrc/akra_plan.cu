@@ -268,10 +268,14 @@ __global__ void k_iota(int n, int *out)
 
 // per ring: W = ω M N^-1 in both precisions; count of masked pixels, Σ N^-1 over them,
 // and the number of invalid (negative or non-finite) entries
+// W32r holds the FP32 weights in the order the FP32 ring FFT visits the pixels: slot k of a
+// power-of-two ring (length 2^b) holds pixel brev_b(k), other rings are in pixel order.
 __global__ void k_weights(const RingInfo *rings, const double *ninv, double omega, double *W64,
-                          float *W32, double *ring_sum, double *ring_cnt, double *ring_bad)
+                          float *W32, float *W32r, double *ring_sum, double *ring_cnt, double *ring_bad)
 {
     const RingInfo ri = rings[blockIdx.x];
+    const bool pow2 = (ri.nphi & (ri.nphi - 1)) == 0;
+    const int logn = 31 - __clz(ri.nphi);
     double s = 0, c = 0, bad = 0;
     for (int j = threadIdx.x; j < ri.nphi; j += blockDim.x) {
         const double v = ninv[ri.first + j];
@@ -279,6 +283,7 @@ __global__ void k_weights(const RingInfo *rings, const double *ninv, double omeg
         const double w = (ok && v > 0) ? omega * v : 0.0;
         W64[ri.first + j] = w;
         W32[ri.first + j] = (float)w;
+        W32r[ri.first + (pow2 ? (int)(__brev((unsigned)j) >> (32 - logn)) : j)] = (float)w;
         if (!ok) bad += 1;
         if (ok && v > 0) {
             s += v;
@@ -476,6 +481,7 @@ static akra_status plan_build(akra_plan p)
     AKRA_TRY(dev_alloc(p, &p->d_ring_active, p->nring));
     AKRA_TRY(dev_alloc(p, &p->d_W64, sizeof(double) * p->npix));
     AKRA_TRY(dev_alloc(p, &p->d_W32, sizeof(float) * p->npix));
+    AKRA_TRY(dev_alloc(p, &p->d_W32r, sizeof(float) * p->npix));
     AKRA_TRY(dev_alloc(p, &p->d_pw64, sizeof(double) * p->ntri));
     AKRA_TRY(dev_alloc(p, &p->d_pw32, sizeof(float) * p->ntri));
 
@@ -563,7 +569,7 @@ extern "C" void akra_plan_destroy(akra_plan p)
     void *ptrs[] = {p->d_rings, p->d_units, p->d_factors, p->d_coef64, p->d_coef32, p->d_seedC,
                     p->d_D64, p->d_D32, p->d_tw64, p->d_tw32, p->d_all_rings, p->d_all_units,
                     p->d_active_rings, p->d_active_units, p->d_ring_active, p->d_W64, p->d_W32,
-                    p->phi.ptr, p->partial.ptr, p->cg.ptr, p->red.ptr, p->xsave.ptr, p->red_cl.ptr,
+                    p->d_W32r, p->phi.ptr, p->partial.ptr, p->cg.ptr, p->red.ptr, p->xsave.ptr, p->red_cl.ptr,
                     p->d_fft32_M,
                     p->d_fft32_off, p->d_fft32_tw2, p->d_fft32_bhat, p->d_seed32, p->d_seed64,
                     p->d_start32, p->d_start64, p->d_steps, p->d_pw64, p->d_pw32, p->d_ftw64,
@@ -631,7 +637,7 @@ extern "C" akra_status akra_plan_set_weights(akra_plan p, const double *d_ninv, 
         set_error("akra_plan_set_weights: scratch allocation failed");
         return AKRA_ENOMEM;
     }
-    k_weights<<<nr, 256, 0, st>>>(p->d_rings, d_ninv, p->omega, p->d_W64, p->d_W32, d_stats,
+    k_weights<<<nr, 256, 0, st>>>(p->d_rings, d_ninv, p->omega, p->d_W64, p->d_W32, p->d_W32r, d_stats,
                                   d_stats + nr, d_stats + 2 * nr);
     std::vector<double> h(3 * (size_t)nr);
     cudaError_t e1 = cudaGetLastError();

@@ -156,7 +156,7 @@ Fft32Args fft32_args(akra_plan p, bool weighted, const int *rings)
     a.bhat_all = p->d_fft32_bhat;
     a.tw2 = p->d_fft32_tw2;
     a.tw_all = p->d_tw32;
-    a.W = p->d_W32;
+    a.W = p->d_W32r;
     a.weighted = weighted ? 1 : 0;
     a.skip = p->cur_skip;
     return a;

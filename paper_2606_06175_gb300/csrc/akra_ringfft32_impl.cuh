@@ -7,6 +7,8 @@ namespace akra {
 
 constexpr int F32_NT = 512;
 constexpr int F32_MMAX = 8 * kMaxNside;   // largest convolution length (n <= 4 nside - 4)
+constexpr int F32_KPT = 4 * kMaxNside / F32_NT;   // ring pixels per thread at most
+static_assert(F32_KPT * F32_NT >= 4 * kMaxNside, "a ring must fit F32_KPT slots per thread");
 
 __device__ __forceinline__ float2 cm(float2 a, float2 b)
 {
@@ -268,15 +270,27 @@ __device__ __forceinline__ void ring_fft32_item(const Fft32Args &a, const int ri
     if (MODE != (int)FftMode::Adjoint) {
         // fold Φ(m) into n bins: F[k] = e^{iπσk/n} Σ_q (-1)^{σq} Φ(k + nq)
         if (n >= F32_NT) {
-            for (int k = tid; k < n; k += F32_NT) {
-                const int qlo = -((L + k) / n), qhi = fdiv(L - k, n);
-                float2 acc = make_float2(0.f, 0.f);
-                for (int q = qlo; q <= qhi; q++) {
-                    const float2 v = prow[k + n * q];
-                    if (sigma && (q & 1)) acc = csub(acc, v);
-                    else acc = cadd(acc, v);
+            // a thread's bins k = tid + u·F32_NT (u < F32_KPT), each summed over q in increasing
+            // order; the loads of one q are independent, so they are all in flight together
+            float2 acc[F32_KPT];
+#pragma unroll
+            for (int u = 0; u < F32_KPT; u++) acc[u] = make_float2(0.f, 0.f);
+            const int qmin = fdiv(-L, n), qmax = fdiv(L, n);
+            for (int q = qmin; q <= qmax; q++) {
+                const bool neg = sigma && (q & 1);
+#pragma unroll
+                for (int u = 0; u < F32_KPT; u++) {
+                    const int k = tid + u * F32_NT, m = k + n * q;
+                    if (k < n && m >= -L && m <= L) {
+                        const float2 v = prow[m];
+                        acc[u] = neg ? csub(acc[u], v) : cadd(acc[u], v);
+                    }
                 }
-                buf[pd(k)] = sigma ? cm(acc, tw[k]) : acc;
+            }
+#pragma unroll
+            for (int u = 0; u < F32_KPT; u++) {
+                const int k = tid + u * F32_NT;
+                if (k < n) buf[pd(k)] = sigma ? cm(acc[u], tw[k]) : acc[u];
             }
         } else {
             const int G = F32_NT / n, g = tid / n, k = tid - g * n;
@@ -308,7 +322,7 @@ __device__ __forceinline__ void ring_fft32_item(const Fft32Args &a, const int ri
                 const int j = pow2 ? (int)(__brev((unsigned)k) >> (32 - logn)) : k;
                 float2 v = buf[pd(k)];
                 if (weighted) {
-                    const float wj = W[first + j];
+                    const float wj = W[first + k];
                     v.x *= wj;
                     v.y *= wj;
                 }
@@ -317,11 +331,15 @@ __device__ __forceinline__ void ring_fft32_item(const Fft32Args &a, const int ri
             }
             return;
         }
-        for (int k = tid; k < n; k += F32_NT) {
-            const int j = pow2 ? (int)(__brev((unsigned)k) >> (32 - logn)) : k;
-            const float wj = W[first + j];
-            buf[pd(k)].x *= wj;
-            buf[pd(k)].y *= wj;
+        // ×W: slot k's weight is W[first + k] (stored in this slot order), loads all in flight
+#pragma unroll
+        for (int u = 0; u < F32_KPT; u++) {
+            const int k = tid + u * F32_NT;
+            if (k < n) {
+                const float wj = W[first + k];
+                buf[pd(k)].x *= wj;
+                buf[pd(k)].y *= wj;
+            }
         }
         __syncthreads();
     } else {
@@ -331,7 +349,7 @@ __device__ __forceinline__ void ring_fft32_item(const Fft32Args &a, const int ri
             const int j = pow2 ? (int)(__brev((unsigned)k) >> (32 - logn)) : k;
             float2 v = make_float2(u1[j], u2[j]);
             if (weighted) {
-                const float wj = W[first + j];
+                const float wj = W[first + k];
                 v.x *= wj;
                 v.y *= wj;
             }
