@@ -104,6 +104,31 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(self.rows)}
 
 
+def replica_noise(wl, rank):
+    """Shape noise of one rank's replica: rank 0 solves the workload's own realisation, rank r > 0
+    an independent one (seed 10000 + r), so replicas never repeat each other's data."""
+    import synthetic as S
+
+    if rank == 0:
+        return wl["noise"]
+    return S.shape_noise(wl["ninv"], np.random.default_rng(10_000 + rank))[0]
+
+
+def whole_job(elapsed, applies, world, device=None):
+    """Whole-job numbers of a replicated run: (slowest rank's time, H applications of all ranks).
+    Collectives on the default process group (NCCL on GPUs; any backend works)."""
+    if world == 1:
+        return elapsed, float(applies)
+    import torch
+    import torch.distributed as dist
+
+    tt = torch.tensor([elapsed], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    aa = torch.tensor([float(applies)], dtype=torch.float64, device=device)
+    dist.all_reduce(aa, op=dist.ReduceOp.SUM)
+    return float(tt), float(aa)
+
+
 def make_inputs(rank, dev):
     """des2048 workload (seeded), shear y = M (A x_true + n) formed with our FP64 forward operator."""
     import torch
@@ -117,9 +142,7 @@ def make_inputs(rank, dev):
     A.akra_plan_set_weights(plan, ninv, 1e-3)
     x_true = torch.from_numpy(np.stack(wl["x_true"])[None]).to(dev)
     y = A.akra_apply_A(plan, A.F64, x_true)
-    noise = wl["noise"]
-    if rank:
-        noise = S.shape_noise(wl["ninv"], np.random.default_rng(10_000 + rank))[0]
+    noise = replica_noise(wl, rank)
     y += torch.from_numpy(noise[None]).to(dev)
     y *= (ninv > 0).to(y.dtype)
     torch.cuda.synchronize()
@@ -273,17 +296,8 @@ def main():
     barrier()
     launches = A.akra_plan_describe(plan)["kernel_launches"] - launches0
     elapsed = ev0.elapsed_time(ev1) / 1e3
-    t_max = elapsed
     applies = sum(i["h_applies_f32"] + i["h_applies_f64"] for i in infos)
-    if world > 1:
-        tt = torch.tensor([elapsed], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt)
-        aa = torch.tensor([float(applies)], device=dev)
-        dist.all_reduce(aa)
-        applies_all = float(aa)
-    else:
-        applies_all = float(applies)
+    t_max, applies_all = whole_job(elapsed, applies, world, dev)
     value = applies_all / t_max
     ms_per_step = 1e3 * t_max / args.steps
 
