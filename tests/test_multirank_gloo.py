@@ -1,6 +1,7 @@
 """The bench's N > 1 path on CPU: world-size-2 `gloo` ranks (no GPU).  Each rank solves its own
 replica, so the only cross-rank steps are the timing/throughput reductions and the per-rank
 noise draw; the reference arm prints from rank 0 only."""
+import json
 import os
 import socket
 import sys
@@ -23,22 +24,22 @@ def _free_port():
         return s.getsockname()[1]
 
 
-def _rank_main(rank, world, port, out):
+def _rank_main(rank, world, port, outdir):
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
     dist.init_process_group("gloo", rank=rank, world_size=world)
     try:
         # rank r took 1 + r seconds for 10 (r + 1) H applications
-        out[rank] = bench.whole_job(1.0 + rank, 10 * (rank + 1), world, torch.device("cpu"))
+        res = bench.whole_job(1.0 + rank, 10 * (rank + 1), world, torch.device("cpu"))
+        with open(os.path.join(outdir, "%d.json" % rank), "w") as f:
+            json.dump(res, f)
     finally:
         dist.destroy_process_group()
 
 
-def test_whole_job_is_slowest_rank_time_and_all_ranks_applies():
+def test_whole_job_is_slowest_rank_time_and_all_ranks_applies(tmp_path):
     world = 2
-    with mp.Manager() as m:
-        out = m.dict()
-        mp.spawn(_rank_main, args=(world, _free_port(), out), nprocs=world, join=True)
-        res = dict(out)
+    mp.spawn(_rank_main, args=(world, _free_port(), str(tmp_path)), nprocs=world, join=True)
+    res = [tuple(json.load(open(tmp_path / ("%d.json" % r)))) for r in range(world)]
     assert res[0] == res[1] == (2.0, 30.0)
 
 
