@@ -376,3 +376,20 @@ def test_error_statuses():
     yn[0, 0, 0] = float("nan")
     _, info = A.akra_cg_solve(p, A.F64, yn, tol=1e-8, maxiter=50)
     assert info["status"] == 5                                    # ENUMERIC
+
+
+# ---------------------------------------------------------------------------
+# degenerate input: an empty footprint (every N^-1 zero)
+# ---------------------------------------------------------------------------
+def test_empty_footprint_gives_zero_operator_and_zero_solution():
+    N, L = 8, 12
+    p = A.akra_plan_create(N, L)
+    A.akra_plan_set_weights(p, torch.zeros((p.npix,), dtype=torch.float64, device=DEV), 1e-3)
+    d = A.akra_plan_describe(p)
+    assert d["n_active_rings"] == 0 and d["n_active_units"] == 0 and d["lambda_eff"] == 0.0
+    x = torch.randn((1, 2, p.ntri), dtype=torch.complex128, device=DEV)
+    assert torch.count_nonzero(A.akra_apply_H(p, A.F64, x)) == 0
+    shear = torch.randn((1, 2, p.npix), dtype=torch.float64, device=DEV)
+    for prec in (A.F64, A.MIXED):
+        xs, info = A.akra_cg_solve(p, prec, shear, tol=1e-6, maxiter=50)
+        assert info["status"] == 0 and torch.count_nonzero(xs) == 0
