@@ -124,7 +124,8 @@ akra_status akra_plan_describe(akra_plan plan, akra_plan_desc *out);
 /* Set the pixel weights from d_ninv [npix] (double, N^-1_p >= 0, 0 off the mask; the mask
  * is M_p = [N^-1_p > 0]).  Stores W_p = ω M_p N^-1_p (ω = 4π/npix) in FP64 and FP32,
  * λ_eff = lambda · mean_{M}(N^-1) (Eq. 14) and P = 1/(mean_all(M N^-1) + λ_eff) (Eq. 15),
- * and the list of rings with any nonzero weight (the only rings H needs).
+ * and the list of rings with any nonzero weight (the only rings H needs).  An all-zero d_ninv
+ * (empty footprint) is accepted: no ring is active, λ_eff = 0, H = 0 and solves return x = 0.
  * Blocking (reads the statistics back).  Errors: EINVAL (NULL, lambda < 0, negative or
  * non-finite N^-1), ECUDA. */
 akra_status akra_plan_set_weights(akra_plan plan, const double *d_ninv, double lambda,
