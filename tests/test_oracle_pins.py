@@ -120,6 +120,22 @@ def test_parity_relation():
             assert np.max(np.abs(a - sg * b)) < 1e-12
 
 
+@pytest.mark.parametrize("s", [2, -2, 0])
+def test_addition_theorem_sum_over_m(s):
+    """Spin-weighted addition theorem at coincident points: Σ_{m=-l..l} |sY_lm(θ)|² = (2l+1)/4π
+    for l >= |s| and every θ, which fixes the normalisation of all m at once, at any latitude
+    (including rings next to a pole)."""
+    L = 1000
+    ref = (2 * np.arange(L + 1) + 1) / (4 * math.pi)
+    for th in (0.004, 0.4, 1.3, math.pi / 2, 2.9):
+        acc = np.zeros(L + 1)
+        for m in range(-L, L + 1):
+            acc += O.spin_lambda(s, L, m, th) ** 2
+        l0 = abs(s)
+        assert np.max(np.abs(acc[l0:] - ref[l0:]) / ref[l0:]) < 1e-10, (s, th)
+        assert np.all(acc[:l0] == 0)
+
+
 @pytest.mark.parametrize("s", [2, -2])
 def test_orthonormality_at_high_l(s):
     """∫ sλ_lm sλ_l'm 2π d(cosθ) = δ_ll' (exact with Gauss-Legendre: the product is a
