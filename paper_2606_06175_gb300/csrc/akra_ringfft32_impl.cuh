@@ -375,7 +375,7 @@ __device__ __forceinline__ void ring_fft32_item(const Fft32Args &a, const int ri
 
 
 template <int MODE>
-__global__ void __launch_bounds__(F32_NT) k_ring_fft32(Fft32Args a)
+__global__ void __launch_bounds__(F32_NT, 2) k_ring_fft32(Fft32Args a)
 {
     if (a.skip && *a.skip) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
