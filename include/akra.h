@@ -304,7 +304,9 @@ akra_status akra_cl_spectra(akra_plan plan, akra_prec prec, const void *d_a, con
  * and 0 < inner_factor <= 1. */
 akra_status akra_set_mixed_policy(double inner_floor, double inner_factor);
 
-/* Host-side wall-clock budget (seconds, > 0) for blocking solves; default 3600. */
+/* Host-side wall-clock budget (seconds, > 0) for blocking solves; default 3600.  Process-wide
+ * (any thread may set it; solves that start afterwards use the new value).  A solve that runs
+ * out returns ETIMEOUT with the context still usable.  Errors: EINVAL unless seconds > 0. */
 akra_status akra_set_timeout(double seconds);
 
 /* Pick the Legendre tile shapes for this plan, precision and RHS count by timing the

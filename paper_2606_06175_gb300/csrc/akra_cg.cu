@@ -415,15 +415,16 @@ static akra_status cg_graph(akra_plan p, int R, CgBufs &b, cudaGraphExec_t *out)
     return AKRA_OK;
 }
 
-double g_timeout_s = 3600.0;
+std::atomic<double> g_timeout_s{3600.0};
 // MIXED inner tolerance: max(floor, min(0.1, factor · tol / current FP64 residual)).
 // floor <= 0 selects the automatic floor, the FP32 operator's own accuracy (below it the FP32
 // CG gains nothing on the FP64 residual): 0.1 · 2^-24 · lmax, within [5e-6, 1e-3].
-double g_inner_floor = 0.0, g_inner_factor = 0.5;
+std::atomic<double> g_inner_floor{0.0}, g_inner_factor{0.5};
 
 double inner_floor(int lmax)
 {
-    if (g_inner_floor > 0) return g_inner_floor;
+    const double f = g_inner_floor.load();
+    if (f > 0) return f;
     return std::min(1e-3, std::max(5e-6, 0.1 * 0x1p-24 * (double)lmax));
 }
 

@@ -1,6 +1,7 @@
 // akra_cg_impl.cuh -- CG state, workspace layout and the launchers shared by the per-plan
 // solver (akra_cg.cu) and the multi-instance solver (akra_batch.cu).
 #pragma once
+#include <atomic>
 #include <chrono>
 
 #include "akra_internal.cuh"
@@ -52,8 +53,9 @@ template <> struct PrecIdx<float> { static constexpr int v = 1; };
 template <typename T>
 inline void **vecs(CgBufs &b) { return PrecIdx<T>::v == 0 ? b.v64 : b.v32; }
 
-extern double g_timeout_s;
-extern double g_inner_floor, g_inner_factor;
+// process-wide settings (set from any thread; a solve reads them when it starts a step)
+extern std::atomic<double> g_timeout_s;
+extern std::atomic<double> g_inner_floor, g_inner_factor;
 double inner_floor(int lmax);
 akra_status cg_reserve(akra_plan p, int R, CgBufs &b);
 akra_status bounded_wait(cudaEvent_t ev, std::chrono::steady_clock::time_point deadline);
