@@ -215,6 +215,67 @@ def test_eb_convention_single_modes():
     assert np.max(np.abs((g1 + 1j * g2) - (-1j * Y))) < 1e-13
 
 
+def _single_mode_error(forward, N=4, L=4):
+    """Largest deviation of forward(κ) from the Eq. 3 / Eq. 2 shear of single κ modes.
+
+    Eq. 3 gives γ_{±2,lm} = D_l κ_lm with κ = κ_E + i κ_B, and the real field has
+    κ_{l,-m} = (-1)^m conj(κ_lm), so a single stored mode c at (l, m > 0) must give
+    γ1 + iγ2 = D_l f [c 2Y_lm + (-1)^m conj(c) 2Y_{l,-m}] with f = 1 for E and f = i for B
+    (at m = 0 only the first term, c real).  2Y from the Goldberg formula (mpmath)."""
+    nt = O.ntri(L)
+    th, ph = O.pixel_angles(N)
+    D = O.ks_kernel(L)
+    worst = 0.0
+    for l, m in ((2, 0), (2, 1), (3, 2), (4, 3), (4, 4)):
+        Yp = np.array([O.goldberg_sYlm(2, l, m, t, p) for t, p in zip(th, ph)])
+        Ym = np.array([O.goldberg_sYlm(2, l, -m, t, p) for t, p in zip(th, ph)])
+        c = 0.7 - 0.3j if m > 0 else 0.7 + 0j
+        for field, f in ((0, 1.0), (1, 1j)):
+            kE = np.zeros(nt, complex)
+            kB = np.zeros(nt, complex)
+            (kE if field == 0 else kB)[O.tri_index(L, l, m)] = c
+            g1, g2 = forward(N, L, kE, kB)
+            expect = D[l] * f * (c * Yp + ((-1) ** m * np.conj(c) * Ym if m > 0 else 0))
+            worst = max(worst, float(np.max(np.abs(g1 + 1j * g2 - expect))))
+    return worst
+
+
+def test_forward_A_single_modes_follow_eq3_sign():
+    """Pins the KS sign of forward_A (and so adjoint_A, its transpose): single κ_E and κ_B
+    modes produce D_l κ_lm 2Y_lm + mirror, not its negative (the Eq. 3 reading)."""
+    assert _single_mode_error(O.forward_A) < 1e-13
+
+
+def test_planted_forward_A_sign_flip_is_caught_by_single_modes():
+    flipped = lambda N, L, kE, kB: tuple(-g for g in O.forward_A(N, L, kE, kB))
+    assert _single_mode_error(flipped) > 0.1
+
+
+def _uniform_sky_precond_error(precond_fn, N=16, L=16):
+    """max |P_i diag(H_λ)_i - 1| over the real-dof basis on a uniform full sky (M ≡ 1, N^-1 =
+    100, λ = 1e-3).  There H_λ is diagonal up to HEALPix quadrature error (App. A), with
+    <N^-1> D_l^2 + λ_eff on the l >= 2 modes and exactly λ_eff on l < 2, which A does not see;
+    the per-l preconditioner is defined as the inverse of that diagonal."""
+    w = O.Weights(N, np.full(12 * N * N, 100.0), lam=1e-3)
+    H, vecs = O.dense_H(N, L, w)
+    P = precond_fn(L, w)
+    idx = np.array([(e if e.any() else b).nonzero()[0][0] for e, b in vecs])
+    return float(np.max(np.abs(P[idx] * np.diag(H) - 1.0)))
+
+
+def test_per_l_preconditioner_inverts_the_uniform_sky_diagonal_of_dense_H():
+    assert _uniform_sky_precond_error(O.per_l_preconditioner) < 1e-2
+
+
+def test_planted_per_l_preconditioner_with_abs_D_is_caught():
+    def bad(L, w):
+        ls, _ = O.lm_arrays(L)
+        d = w.mean_mninv * np.abs(O.ks_kernel(L))[ls] + w.lam_eff
+        return 1.0 / d
+
+    assert _uniform_sky_precond_error(bad) > 0.1
+
+
 @pytest.mark.parametrize("nside,lmax", [(8, 20), (16, 40), (8, 31)])
 def test_adjoint_identity(nside, lmax):
     rng = np.random.default_rng(lmax)
