@@ -138,12 +138,14 @@ akra_status akra_synth_spin2(akra_plan plan, akra_prec prec, const void *d_alm, 
                              int R, void *stream);
 
 /* akra_synth_spin2 without any device allocation.  The paper has no counterpart: this is
- * for callers that cannot allocate at the point of the call -- inside a stream capture, under
- * a memory pool or budget that forbids new allocations, or in a loop where the implicit
- * synchronisation of cudaMalloc is not acceptable.  Same arguments, layouts and result as
- * akra_synth_spin2 (the same kernels run); the phase-array scratch is a fixed 32 MiB
- * device array inside the library (held by every GPU that loads the library until the
- * process exits) instead of a plan workspace.  The plan itself must already exist.
+ * for callers that cannot allocate device memory at the point of the call -- code running
+ * under a device-memory budget or inside a memory pool that must not grow, a process where
+ * another component has already reserved the device memory, or a latency-critical loop where
+ * cudaMalloc's implicit device synchronisation is not acceptable.  Same arguments, layouts and
+ * result as akra_synth_spin2 (the same kernels run); the phase-array scratch is a fixed
+ * 32 MiB device array inside the library (held by every GPU that loads the library until the
+ * process exits) instead of a plan workspace.  The plan must already exist, and its device
+ * must be the current device (EINVAL otherwise).
  * Limit: R * (4 nside - 1) * (2 lmax + 1) * sizeof(complex) <= 32 MiB (for R = 1: FP64 up to
  * about nside 256 / lmax 512, FP32 up to nside 512 / lmax 1024); larger sizes return
  * EINVAL with a message.  The first call on each device looks up the scratch address
@@ -185,7 +187,12 @@ akra_status akra_apply_H(akra_plan plan, akra_prec prec, const void *d_x, void *
  * FP64, inner CG in FP32 (iterative refinement).  The loop runs on the device (one CUDA
  * graph per iteration block); the host only polls a device status.  Blocking; info may be
  * NULL.  Returns the worst per-RHS status: OK, ENOCONV, ENUMERIC, ETIMEOUT (wall-clock
- * budget from akra_set_timeout), or an argument/CUDA error. */
+ * budget from akra_set_timeout), or an argument/CUDA error.  On every return, including
+ * ETIMEOUT and errors after work was queued, `stream` is ordered after all work the call
+ * queued, so d_shear and d_x may be freed or reused in stream order.  After ETIMEOUT the
+ * contents of d_x are unspecified and that work can still be running on the device (up to
+ * 16 launched CG iterations, and kernels or copies still reading d_shear): synchronise
+ * `stream` before the host reads or frees those buffers outside stream order. */
 akra_status akra_cg_solve(akra_plan plan, akra_prec prec, const void *d_shear, void *d_x,
                           int R, double tol, int maxiter, akra_cg_info *info, void *stream);
 
@@ -300,13 +307,17 @@ akra_status akra_cl_spectra(akra_plan plan, akra_prec prec, const void *d_a, con
  * about (FP32 tolerance + FP32 operator error) × the previous one, so iterating the FP32 CG
  * below the FP32 operator's relative error (~0.1-0.2 · 2^-24 · lmax) gains nothing.
  * inner_floor = 0 (default) selects that floor, 0.1 · 2^-24 · lmax within [5e-6, 1e-3];
- * inner_factor defaults to 0.5.  Process-wide.  Errors: EINVAL unless 0 <= inner_floor < 0.1
- * and 0 < inner_factor <= 1. */
+ * inner_factor defaults to 0.5.  Process-wide: the pair is stored together (under a lock) and
+ * a solve reads it once per outer step, so it never combines the floor of one call with the
+ * factor of another; a solve already running picks up a new pair at its next outer step.
+ * Errors: EINVAL unless 0 <= inner_floor < 0.1 and 0 < inner_factor <= 1. */
 akra_status akra_set_mixed_policy(double inner_floor, double inner_factor);
 
-/* Host-side wall-clock budget (seconds, > 0) for blocking solves; default 3600.  Process-wide
+/* Host-side wall-clock budget (seconds) for blocking solves; default 3600.  Process-wide
  * (any thread may set it; solves that start afterwards use the new value).  A solve that runs
- * out returns ETIMEOUT with the context still usable.  Errors: EINVAL unless seconds > 0. */
+ * out returns ETIMEOUT with the context still usable; the work it had already queued may
+ * still be running, with the caller's stream ordered after it (see akra_cg_solve).
+ * Errors: EINVAL unless seconds is finite and 0 < seconds <= 1e9. */
 akra_status akra_set_timeout(double seconds);
 
 /* Pick the Legendre tile shapes for this plan, precision and RHS count by timing the

@@ -471,14 +471,14 @@ extern "C" akra_status akra_batch_cg_solve(akra_batch b, akra_prec prec, const v
         set_error("akra_batch_cg_solve: invalid argument (precision must be AKRA_MIXED or AKRA_F32)");
         return AKRA_EINVAL;
     }
-    const auto deadline = std::chrono::steady_clock::now() +
-                          std::chrono::microseconds((long long)(g_timeout_s * 1e6));
+    const auto deadline = solve_deadline();
     cudaStream_t user = (cudaStream_t)stream;
     const int n = b->ninst;
     AKRA_TRY(batch_reserve(b));
     std::vector<CgBufs> cb(n);
     for (int i = 0; i < n; i++) AKRA_TRY(cg_reserve(b->plans[i], b->R[i], cb[i]));
     AKRA_TRY(join(b, user));
+    StreamJoinGuard leave_guard{b->stream, user, b->ev};
     cudaStream_t st = b->stream;
     for (int i = 0; i < n; i++) {
         AKRA_CUDA_TRY(cudaMemsetAsync(cb[i].ctl[0], 0, sizeof(CgCtl), st));
@@ -531,6 +531,7 @@ extern "C" akra_status akra_batch_cg_solve(akra_batch b, akra_prec prec, const v
         }
         int budget = maxiter;
         for (int round = 0; round < 30; round++) {
+            const MixedPolicy mp = mixed_policy();
             std::vector<char> act(n, 0);
             std::vector<double> tl(n, tol);
             bool any = false;
@@ -541,7 +542,7 @@ extern "C" akra_status akra_batch_cg_solve(akra_batch b, akra_prec prec, const v
                 if (w >= tol && !bad) {
                     act[i] = 1;
                     any = true;
-                    tl[i] = std::max(inner_floor(b->plans[i]->lmax), std::min(0.1, g_inner_factor * tol / w));
+                    tl[i] = inner_tol(mp, b->plans[i]->lmax, tol, w);
                 }
             }
             if (!any || budget <= 0) break;

@@ -12,6 +12,7 @@
 // Dot products use the real-dof metric: <x,y> = Σ_l [x_l0 y_l0 + 2 Re Σ_{m>0} x conj(y)].
 #include <algorithm>
 #include <chrono>
+#include <mutex>
 #include <thread>
 
 #include "akra_cg_impl.cuh"
@@ -415,17 +416,43 @@ static akra_status cg_graph(akra_plan p, int R, CgBufs &b, cudaGraphExec_t *out)
     return AKRA_OK;
 }
 
-std::atomic<double> g_timeout_s{3600.0};
+// process-wide solver settings
+static std::mutex g_settings_mu;
+static double g_timeout_s = 3600.0;
+static MixedPolicy g_mixed{0.0, 0.5};
+constexpr double kMaxTimeout = 1e9;   // seconds (about 32 years)
+
+MixedPolicy mixed_policy()
+{
+    std::lock_guard<std::mutex> lock(g_settings_mu);
+    return g_mixed;
+}
+
+void set_mixed_policy(MixedPolicy mp)
+{
+    std::lock_guard<std::mutex> lock(g_settings_mu);
+    g_mixed = mp;
+}
+
+std::chrono::steady_clock::time_point solve_deadline()
+{
+    double s;
+    {
+        std::lock_guard<std::mutex> lock(g_settings_mu);
+        s = g_timeout_s;
+    }
+    // s is finite and in (0, 1e9] (akra_set_timeout), so the microsecond count fits
+    return std::chrono::steady_clock::now() + std::chrono::microseconds((long long)(s * 1e6));
+}
+
 // MIXED inner tolerance: max(floor, min(0.1, factor · tol / current FP64 residual)).
 // floor <= 0 selects the automatic floor, the FP32 operator's own accuracy (below it the FP32
 // CG gains nothing on the FP64 residual): 0.1 · 2^-24 · lmax, within [5e-6, 1e-3].
-std::atomic<double> g_inner_floor{0.0}, g_inner_factor{0.5};
-
-double inner_floor(int lmax)
+double inner_tol(const MixedPolicy &mp, int lmax, double tol, double worst)
 {
-    const double f = g_inner_floor.load();
-    if (f > 0) return f;
-    return std::min(1e-3, std::max(5e-6, 0.1 * 0x1p-24 * (double)lmax));
+    const double fl = mp.floor > 0 ? mp.floor
+                                   : std::min(1e-3, std::max(5e-6, 0.1 * 0x1p-24 * (double)lmax));
+    return std::max(fl, std::min(0.1, mp.factor * tol / worst));
 }
 
 // wait for the event with a wall-clock budget (no unbounded device wait)
@@ -520,8 +547,7 @@ static akra_status solve_b(akra_plan p, akra_prec prec, const void *bsrc, void *
                            int maxiter, akra_cg_info *info, cudaStream_t user, bool b_in_place,
                            CgBufs &b, int h64_already)
 {
-    const auto t0 = std::chrono::steady_clock::now();
-    const auto deadline = t0 + std::chrono::microseconds((long long)(g_timeout_s * 1e6));
+    const auto deadline = solve_deadline();
     cudaStream_t cs = p->stream;
     const size_t V64 = (size_t)R * 2 * p->ntri * sizeof(double2);
     const size_t V32 = (size_t)R * 2 * p->ntri * sizeof(float2);
@@ -583,7 +609,7 @@ static akra_status solve_b(akra_plan p, akra_prec prec, const void *bsrc, void *
                 break;
             }
             // inner tolerance: what this outer step must gain, but not below FP32 reach
-            const double tin = std::max(inner_floor(p->lmax), std::min(0.1, g_inner_factor * tol / worst));
+            const double tin = inner_tol(mixed_policy(), p->lmax, tol, worst);
             k_cast_scaled<<<RED_NB, RED_NT, 0, cs>>>(2 * p->ntri, R, (const double2 *)r64, b.res,
                                                      (float2 *)b.v32[0]);
             AKRA_CUDA_TRY(cudaGetLastError());
@@ -811,17 +837,17 @@ extern "C" akra_status akra_set_mixed_policy(double inner_floor, double inner_fa
         set_error("akra_set_mixed_policy: need 0 <= inner_floor < 0.1 and 0 < inner_factor <= 1");
         return AKRA_EINVAL;
     }
-    g_inner_floor = inner_floor;
-    g_inner_factor = inner_factor;
+    set_mixed_policy(MixedPolicy{inner_floor, inner_factor});
     return AKRA_OK;
 }
 
 extern "C" akra_status akra_set_timeout(double seconds)
 {
-    if (!(seconds > 0)) {
-        set_error("akra_set_timeout: seconds must be > 0");
+    if (!(seconds > 0) || !(seconds <= kMaxTimeout)) {   // also rejects NaN and +inf
+        set_error("akra_set_timeout: seconds must be finite, > 0 and <= 1e9");
         return AKRA_EINVAL;
     }
+    std::lock_guard<std::mutex> lock(g_settings_mu);
     g_timeout_s = seconds;
     return AKRA_OK;
 }
@@ -834,6 +860,7 @@ extern "C" akra_status akra_cg_solve_b(akra_plan p, akra_prec prec, const void *
     CgBufs b;
     AKRA_TRY(cg_reserve(p, R, b));
     AKRA_TRY(join_user(p, user, b));
+    StreamJoinGuard leave{p->stream, user, p->ev_b};
     return solve_b(p, prec, d_b, d_x, R, tol, maxiter, info, user, false, b, 0);
 }
 
@@ -845,6 +872,7 @@ extern "C" akra_status akra_cg_solve(akra_plan p, akra_prec prec, const void *d_
     CgBufs b;
     AKRA_TRY(cg_reserve(p, R, b));
     AKRA_TRY(join_user(p, user, b));
+    StreamJoinGuard leave{p->stream, user, p->ev_b};
     // b = A^T W y, in FP64 unless the whole solve is FP32
     akra_status s;
     int h64 = 0;
@@ -870,6 +898,7 @@ extern "C" akra_status akra_cg_solve_adjoint(akra_plan p, akra_prec prec, const 
     CgBufs b;
     AKRA_TRY(cg_reserve(p, R, b));
     AKRA_TRY(join_user(p, user, b));
+    StreamJoinGuard leave{p->stream, user, p->ev_b};
     // right-hand side G^{-1} g in the solve's own precision region
     const bool dbl = prec != AKRA_F32;
     AKRA_TRY(metric_inverse(p, dbl, d_g, dbl ? b.v64[0] : b.v32[0], R, p->stream));
@@ -890,6 +919,7 @@ extern "C" akra_status akra_cg_solve_fields(akra_plan p, akra_prec prec, akra_fi
     CgBufs b;
     AKRA_TRY(cg_reserve(p, R, b));
     AKRA_TRY(join_user(p, user, b));
+    StreamJoinGuard leave{p->stream, user, p->ev_b};
     cudaStream_t cs = p->stream;
     const bool dbl = prec != AKRA_F32;
     const size_t elem = dbl ? sizeof(double2) : sizeof(float2);

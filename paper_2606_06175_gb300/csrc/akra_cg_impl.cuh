@@ -1,7 +1,6 @@
 // akra_cg_impl.cuh -- CG state, workspace layout and the launchers shared by the per-plan
 // solver (akra_cg.cu) and the multi-instance solver (akra_batch.cu).
 #pragma once
-#include <atomic>
 #include <chrono>
 
 #include "akra_internal.cuh"
@@ -53,10 +52,32 @@ template <> struct PrecIdx<float> { static constexpr int v = 1; };
 template <typename T>
 inline void **vecs(CgBufs &b) { return PrecIdx<T>::v == 0 ? b.v64 : b.v32; }
 
-// process-wide settings (set from any thread; a solve reads them when it starts a step)
-extern std::atomic<double> g_timeout_s;
-extern std::atomic<double> g_inner_floor, g_inner_factor;
-double inner_floor(int lmax);
+// process-wide settings (set from any thread).  The mixed-precision policy is one pair,
+// written and read under a lock, so a solve never sees a floor from one call of
+// akra_set_mixed_policy with the factor of another; a solve reads it once per outer step.
+struct MixedPolicy {
+    double floor;    // <= 0: the automatic floor (the FP32 operator's own accuracy)
+    double factor;
+};
+MixedPolicy mixed_policy();
+void set_mixed_policy(MixedPolicy mp);
+// inner FP32 tolerance of an outer step: max(floor, min(0.1, factor tol / worst))
+double inner_tol(const MixedPolicy &mp, int lmax, double tol, double worst);
+// the wall-clock deadline of a blocking solve that starts now (budget of akra_set_timeout)
+std::chrono::steady_clock::time_point solve_deadline();
+
+// Orders the caller's stream after everything queued so far on an internal stream, on every
+// return path (normal, error or ETIMEOUT) of a blocking call that queued work there: the
+// caller may then free or reuse its buffers in stream order, even while copies or CG
+// iterations launched before an early return are still running.
+struct StreamJoinGuard {
+    cudaStream_t from, to;
+    cudaEvent_t ev;
+    ~StreamJoinGuard()
+    {
+        if (cudaEventRecord(ev, from) == cudaSuccess) cudaStreamWaitEvent(to, ev, 0);
+    }
+};
 akra_status cg_reserve(akra_plan p, int R, CgBufs &b);
 akra_status bounded_wait(cudaEvent_t ev, std::chrono::steady_clock::time_point deadline);
 // x = 0, r = b (slot 0), p = P r, state and ctl initialised (precision T region)

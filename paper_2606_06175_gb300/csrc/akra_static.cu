@@ -2,10 +2,10 @@
 //
 // akra_synth_spin2 keeps its phase array Φ in a plan workspace that it grows with
 // cudaMalloc on first use (or when R grows).  Some callers cannot allocate at the point
-// where they need a synthesis: code running while a stream is being captured into a CUDA
-// graph (a cudaMalloc there breaks or invalidates the capture), code that runs under a
-// memory pool or budget that forbids new device allocations, and latency-critical loops
-// where a cudaMalloc (an implicit device synchronisation) is not acceptable.  This entry
+// where they need a synthesis: code running under a device-memory budget or inside a
+// memory pool that must not grow, a process where another component (a framework's caching
+// allocator, say) has already reserved the device memory, and latency-critical loops where
+// a cudaMalloc, with its implicit device synchronisation, is not acceptable.  This entry
 // point runs the same two kernels (Legendre synthesis, ring FFT) but puts Φ in a fixed
 // file-scope device array instead, so a call allocates nothing.
 #include <mutex>
@@ -87,6 +87,15 @@ extern "C" akra_status akra_synth_spin2_static(akra_plan p, akra_prec prec, cons
     }
     if (R < 1 || R > 65535) {
         set_error("akra_synth_spin2_static: R = %d outside [1, 65535]", R);
+        return AKRA_EINVAL;
+    }
+    // the plan's tables live on the device it was created on; the scratch looked up below is
+    // the current device's, so the two must agree
+    int dev = -1;
+    AKRA_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev != p->device) {
+        set_error("akra_synth_spin2_static: the current device is %d but the plan was created on "
+                  "device %d; make the plan's device current first", dev, p->device);
         return AKRA_EINVAL;
     }
     cudaStream_t st = (cudaStream_t)stream;

@@ -1,7 +1,7 @@
 """Profiling driver: build a DES-like problem at (nside, lmax) and run `reps` H applications
 (or one mixed solve) -- a small, self-contained command for Nsight Compute captures.
 
-    python -m paper_2606_06175_gb300.profile_step --nside 1024 --lmax 2048 --prec f32 --reps 2
+    python profile_step.py --nside 1024 --lmax 2048 --prec f32 --reps 2
 
 `--cufft` instead times the library's FP32 ring-FFT stage (fold, backward DFT, ×W, forward
 DFT, unfold on every ring that holds a weighted pixel) next to cuFFT (through torch.fft) doing
@@ -16,7 +16,7 @@ import sys
 import numpy as np
 import torch
 
-sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
 
 import synthetic as S  # noqa: E402
 from paper_2606_06175_gb300 import akra as A  # noqa: E402

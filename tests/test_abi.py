@@ -63,3 +63,15 @@ def test_null_arguments_are_rejected(lib):
     assert lib.akra_plan_describe(None, None) == 1
     lib.akra_plan_destroy(None)   # no-op
     assert b"NULL" in lib.akra_last_error() or len(lib.akra_last_error()) > 0
+
+
+def test_set_timeout_rejects_non_finite_and_huge_budgets(lib):
+    """The budget becomes a microsecond count: NaN, +inf and values beyond 1e9 s would overflow
+    that conversion, so they are rejected, as are values <= 0."""
+    import ctypes
+
+    lib.akra_set_timeout.argtypes = [ctypes.c_double]
+    for v in (float("inf"), float("nan"), 1e300, 1.0000001e9, 0.0, -1.0, float("-inf")):
+        assert lib.akra_set_timeout(v) == 1, v
+    assert lib.akra_set_timeout(1e9) == 0
+    assert lib.akra_set_timeout(3600.0) == 0     # back to the default

@@ -378,6 +378,44 @@ def test_error_statuses():
     assert info["status"] == 5                                    # ENUMERIC
 
 
+def test_timeout_leaves_the_callers_stream_ordered_after_queued_work():
+    """After ETIMEOUT the solve's already launched iterations may still run; the caller's stream
+    must wait for them, so buffers can be freed and reused in stream order with no device-wide
+    synchronize.  Checked on a problem whose iterations take milliseconds: right after the
+    ETIMEOUT return the caller's stream is still busy, and a fresh solve on reused memory
+    gives the same solution as before."""
+    N, L = 512, 1024
+    p = A.akra_plan_create(N, L)
+    sv = S.survey(N, "des", 1002)
+    A.akra_plan_set_weights(p, torch.from_numpy(sv["ninv"]).to(DEV), 1e-3)
+    g = torch.Generator(device=DEV).manual_seed(5)
+    y = torch.randn((1, 2, p.npix), dtype=torch.float64, device=DEV, generator=g)
+    y *= torch.from_numpy(sv["mask"]).to(DEV)
+    xref, info = A.akra_cg_solve(p, A.F64, y, tol=1e-4, maxiter=500)   # also captures the graph
+    assert info["status"] == 0
+    torch.cuda.synchronize()
+    x = torch.zeros_like(xref)
+    A.akra_set_timeout(0.05)
+    try:
+        with pytest.raises(A.AkraError) as ei:
+            A.akra_cg_solve(p, A.F64, y, x, tol=1e-14, maxiter=100000)
+        assert ei.value.status == 6
+        busy = not torch.cuda.current_stream().query()
+    finally:
+        A.akra_set_timeout(3600.0)
+    assert busy, "the caller's stream is not ordered after the abandoned iterations"
+    # free the solve's buffers and reuse the memory in stream order, without synchronising
+    yc = y.clone()
+    del x, y
+    y2 = torch.empty_like(yc)
+    y2.copy_(yc)
+    x2 = torch.full_like(xref, float("nan"))
+    x2, info = A.akra_cg_solve(p, A.F64, y2, x2, tol=1e-4, maxiter=500)
+    torch.cuda.synchronize()
+    assert info["status"] == 0
+    assert float(torch.linalg.vector_norm(x2 - xref) / torch.linalg.vector_norm(xref)) < 1e-12
+
+
 # ---------------------------------------------------------------------------
 # degenerate input: an empty footprint (every N^-1 zero)
 # ---------------------------------------------------------------------------

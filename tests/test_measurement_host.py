@@ -3,7 +3,7 @@ ring-FFT / cuFFT comparison groups rings by."""
 import numpy as np
 
 import synthetic as S
-from paper_2606_06175_gb300.profile_step import ring_table
+from profile_step import ring_table
 
 
 def test_ring_table_tiles_the_sphere_ring_by_ring():
