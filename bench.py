@@ -333,7 +333,7 @@ def differentiation_block(A, dev):
             torch.cuda.synchronize()
             dt = time.perf_counter() - t0
         grads[name] = (yt.grad.double(), nt.grad.double())
-        out[name] = {"forward_backward_s": dt, "loss": float(loss)}
+        out[name] = {"forward_backward_s": dt, "loss": float(loss.detach())}
     out["rel_diff_mixed_vs_fp64_grad_y"] = rel_err(grads["mixed"][0], grads["fp64"][0])
     out["rel_diff_mixed_vs_fp64_grad_ninv"] = rel_err(grads["mixed"][1], grads["fp64"][1])
     out["workload"] = "grad512: Nside 512, lmax 1024, DES-like footprint, seed 1005, tol 1e-6"

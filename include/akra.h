@@ -121,6 +121,25 @@ const char *akra_version(void);
 /* Fill *out with the plan's sizes and weight statistics.  Blocking. */
 akra_status akra_plan_describe(akra_plan plan, akra_plan_desc *out);
 
+/* Bounds-check record of the debug build (libakra_debug.so, compiled with -DAKRA_DEBUG; the
+ * paper has no counterpart).  In that build the index of every global-memory access of the
+ * operator kernels (Legendre synthesis and adjoint, epilogue, ring FFTs) is checked against its
+ * array's extent; an index outside it is replaced by 0 (no access leaves its array, no kernel
+ * traps) and counted.  This call synchronises the device, returns the number of violations
+ * since the last call in *count, with the call site, index and extent of the first one, and
+ * clears the record.  In the release build *count = -1 (no checks compiled in).  site, index
+ * and bound may be NULL.  Errors: EINVAL (count NULL), ECUDA. */
+akra_status akra_debug_violations(long long *count, int *site, long long *index, long long *bound);
+
+/* Testing aid (a substitute for a memory checker; the paper has no counterpart): set every
+ * byte of every device workspace the plan currently holds -- phase array, adjoint partial
+ * sums, CG vectors and reduction scratch, field and spectra scratch -- to `byte`.  With 0xFF
+ * each FP32 and FP64 entry becomes a NaN, so an operator or solve that reads a workspace entry
+ * it did not write first returns non-finite results.  Workspaces keep their addresses, so
+ * captured CG graphs stay valid.  Asynchronous on `stream`.  Errors: EINVAL (NULL plan, byte
+ * outside [0, 255]), ECUDA. */
+akra_status akra_plan_fill_workspaces(akra_plan plan, int byte, void *stream);
+
 /* Set the pixel weights from d_ninv [npix] (double, N^-1_p >= 0, 0 off the mask; the mask
  * is M_p = [N^-1_p > 0]).  Stores W_p = ω M_p N^-1_p (ω = 4π/npix) in FP64 and FP32,
  * λ_eff = lambda · mean_{M}(N^-1) (Eq. 14) and P = 1/(mean_all(M N^-1) + λ_eff) (Eq. 15),

@@ -55,13 +55,16 @@ EXPORTS = ["akra_plan_create", "akra_plan_destroy", "akra_last_error", "akra_ver
            "akra_batch_apply_H", "akra_batch_cg_solve", "akra_batch_describe",
            "akra_plan_get_shape", "akra_plan_set_shape", "akra_set_mixed_policy", "akra_fma_rate",
            "akra_cg_solve_fields", "akra_shuffle_shear", "akra_cl_spectra",
-           "akra_plan_set_preconditioner", "akra_flat_plan_create"]
+           "akra_plan_set_preconditioner", "akra_flat_plan_create", "akra_plan_fill_workspaces",
+           "akra_debug_violations"]
 
 _lib_handle = None
 
 
 def library_path() -> str:
-    return _build.OUT
+    """libakra.so in the package directory, or the file named by AKRA_LIBRARY (e.g. the
+    bounds-checked debug build libakra_debug.so)."""
+    return os.environ.get("AKRA_LIBRARY") or _build.OUT
 
 
 def load(build_if_missing: bool = False):
@@ -71,8 +74,8 @@ def load(build_if_missing: bool = False):
         return _lib_handle
     path = library_path()
     if not os.path.exists(path):
-        if not build_if_missing:
-            raise RuntimeError("libakra.so is not built (run paper_2606_06175_gb300/build.py)")
+        if not build_if_missing or path != _build.OUT:
+            raise RuntimeError("%s is not built (run paper_2606_06175_gb300/build.py)" % path)
         _build.build()
     lib = ctypes.CDLL(path)
     vp, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
@@ -95,6 +98,9 @@ def load(build_if_missing: bool = False):
         "akra_set_timeout": ([d], i),
         "akra_set_mixed_policy": ([d, d], i),
         "akra_plan_set_preconditioner": ([vp, i], i),
+        "akra_plan_fill_workspaces": ([vp, i, vp], i),
+        "akra_debug_violations": ([ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(i),
+                                   ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)], i),
         "akra_shuffle_shear": ([vp, i, vp, vp, vp, i, vp], i),
         "akra_cl_spectra": ([vp, i, vp, vp, i, i, ctypes.POINTER(d), vp, vp], i),
         "akra_fma_rate": ([i, ctypes.POINTER(d)], i),
@@ -214,6 +220,21 @@ def akra_plan_describe(plan: Plan) -> dict:
     d = PlanDesc()
     _check(load().akra_plan_describe(plan.handle, ctypes.byref(d)))
     return {f: getattr(d, f) for f, _ in PlanDesc._fields_}
+
+
+def akra_debug_violations() -> dict:
+    """Out-of-bounds accesses recorded by the debug build since the last call (count -1: the
+    release build, which has no checks); clears the record."""
+    c, si = ctypes.c_longlong(), ctypes.c_int()
+    ix, bd = ctypes.c_longlong(), ctypes.c_longlong()
+    _check(load().akra_debug_violations(ctypes.byref(c), ctypes.byref(si), ctypes.byref(ix), ctypes.byref(bd)))
+    return {"count": c.value, "site": si.value, "index": ix.value, "bound": bd.value}
+
+
+def akra_plan_fill_workspaces(plan: Plan, byte: int = 0xFF, stream=None):
+    """Fill every workspace the plan holds with `byte` (0xFF: NaN in FP32 and FP64), so that a
+    later read of an entry no kernel wrote shows up as a non-finite result (testing aid)."""
+    _check(load().akra_plan_fill_workspaces(plan.handle, int(byte), _stream(stream)))
 
 
 def akra_plan_set_weights(plan: Plan, ninv: torch.Tensor, lam: float = 1e-3, stream=None):

@@ -302,6 +302,8 @@ static akra_status batch_cg32(akra_batch b, std::vector<CgBufs> &cb, const std::
     return bounded_wait(b->ev, deadline);
 }
 
+AKRA_DEBUG_COLLECTOR(batch)
+
 }  // namespace akra
 
 using namespace akra;

@@ -36,6 +36,63 @@ void set_error(const char *fmt, ...);
     } while (0)
 
 // ---------------------------------------------------------------------------
+// bounds-checked build (-DAKRA_DEBUG, built as libakra_debug.so): the index of every
+// global-memory access of the operator kernels (Legendre items, epilogue, ring FFTs) is checked
+// against its array's extent.  An index outside [0, bound) is replaced by 0, so no access
+// leaves its array, and the first violation (call site, index, bound) is recorded in a device
+// record of the translation unit; akra_debug_violations() collects and clears the records.
+// No kernel traps: the call's results are wrong and the host is told.  The release build
+// compiles the plain index.
+// ---------------------------------------------------------------------------
+struct DebugRecord {
+    unsigned long long count;   // out-of-bounds accesses seen
+    long long index, bound;     // the first one
+    int site;                   // its call site (DebugSite)
+    int pad;
+};
+enum DebugSite {
+    kDbgUnits = 1, kDbgUnitInfo, kDbgStart, kDbgSeeds, kDbgCoef, kDbgAlm, kDbgKsFactor,
+    kDbgPhiWrite, kDbgPhiRead, kDbgPartialWrite, kDbgPartialRead, kDbgAlmOut, kDbgRingActive,
+    kDbgFftPhi, kDbgFftMapIn, kDbgFftMapOut, kDbgFftWeight, kDbgFftRing
+};
+#ifdef AKRA_DEBUG
+static __device__ DebugRecord g_akra_dbg;   // one per translation unit
+__device__ __forceinline__ long long dbg_index(long long i, long long bound, int site)
+{
+    if (i >= 0 && i < bound) return i;
+    if (atomicAdd(&g_akra_dbg.count, 1ull) == 0ull) {
+        g_akra_dbg.index = i;
+        g_akra_dbg.bound = bound;
+        g_akra_dbg.site = site;
+    }
+    return 0;
+}
+#define AKRA_IX(i, bound, site) ::akra::dbg_index((long long)(i), (long long)(bound), (site))
+#define AKRA_DEBUG_COLLECTOR(tu)                                                           \
+    akra_status debug_collect_##tu(DebugRecord *acc)                                       \
+    {                                                                                      \
+        DebugRecord r{}, zero{};                                                           \
+        AKRA_CUDA_TRY(cudaMemcpyFromSymbol(&r, g_akra_dbg, sizeof(r)));                    \
+        AKRA_CUDA_TRY(cudaMemcpyToSymbol(g_akra_dbg, &zero, sizeof(zero)));                \
+        if (r.count && !acc->count) {                                                      \
+            acc->index = r.index;                                                          \
+            acc->bound = r.bound;                                                          \
+            acc->site = r.site;                                                            \
+        }                                                                                  \
+        acc->count += r.count;                                                             \
+        return AKRA_OK;                                                                    \
+    }
+#else
+#define AKRA_IX(i, bound, site) (i)
+#define AKRA_DEBUG_COLLECTOR(tu) \
+    akra_status debug_collect_##tu(DebugRecord *) { return AKRA_OK; }
+#endif
+akra_status debug_collect_legendre(DebugRecord *acc);
+akra_status debug_collect_batch(DebugRecord *acc);
+akra_status debug_collect_ringfft(DebugRecord *acc);
+akra_status debug_collect_ringfft32(DebugRecord *acc);
+
+// ---------------------------------------------------------------------------
 // small vector types
 // ---------------------------------------------------------------------------
 template <typename T> struct Cx;

@@ -34,24 +34,28 @@ __global__ void k_adj_epilogue(int L, long long ntri, int nchunks, int R,
     using C2 = cx_t<T>;
     const int m = blockIdx.x, r = blockIdx.y;
     const long long mbase = (long long)m * (2 * L + 1 - m) / 2;
+    const long long qbound = (long long)nchunks * R * ntri * 4;   // extent of the partial sums
+    const long long abound = (long long)R * 2 * ntri;             // extent of x and out
+    (void)qbound;
+    (void)abound;
     for (int l = m + threadIdx.x; l <= L; l += blockDim.x) {
         const long long idx = mbase + l;
         T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
         if (l >= 2) {
             for (int c = 0; c < nchunks; c++) {
-                const T *pp = partial + (((size_t)c * R + r) * ntri + idx) * 4;
-                a0 += pp[0];
-                a1 += pp[1];
-                a2 += pp[2];
-                a3 += pp[3];
+                const long long pq = (((size_t)c * R + r) * ntri + idx) * 4;
+                a0 += partial[AKRA_IX(pq + 0, qbound, kDbgPartialRead)];
+                a1 += partial[AKRA_IX(pq + 1, qbound, kDbgPartialRead)];
+                a2 += partial[AKRA_IX(pq + 2, qbound, kDbgPartialRead)];
+                a3 += partial[AKRA_IX(pq + 3, qbound, kDbgPartialRead)];
             }
         }
-        const T h = (fl ? fl[l] : T(-1)) * T(0.5);
+        const T h = (fl ? fl[AKRA_IX(l, L + 1, kDbgKsFactor)] : T(-1)) * T(0.5);
         C2 E{h * a0, h * a1};
         C2 B{h * a3, -h * a2};
         if (xreg) {
-            C2 xe = xreg[((size_t)r * 2 + 0) * ntri + idx];
-            C2 xb = xreg[((size_t)r * 2 + 1) * ntri + idx];
+            C2 xe = xreg[AKRA_IX(((size_t)r * 2 + 0) * ntri + idx, abound, kDbgAlm)];
+            C2 xb = xreg[AKRA_IX(((size_t)r * 2 + 1) * ntri + idx, abound, kDbgAlm)];
             E.x += lam * xe.x;
             E.y += lam * xe.y;
             B.x += lam * xb.x;
@@ -61,8 +65,8 @@ __global__ void k_adj_epilogue(int L, long long ntri, int nchunks, int R,
         // a field outside the solve's field set is held at zero (its block row is dropped)
         if (!(fields & 1)) E = C2{0, 0};
         if (!(fields & 2)) B = C2{0, 0};
-        out[((size_t)r * 2 + 0) * ntri + idx] = E;
-        out[((size_t)r * 2 + 1) * ntri + idx] = B;
+        out[AKRA_IX(((size_t)r * 2 + 0) * ntri + idx, abound, kDbgAlmOut)] = E;
+        out[AKRA_IX(((size_t)r * 2 + 1) * ntri + idx, abound, kDbgAlmOut)] = B;
     }
 }
 
@@ -205,5 +209,7 @@ template akra_status adjoint_epilogue<float>(akra_plan, LegMode, const void *, i
                                              double, void *, int, cudaStream_t, int);
 template akra_status adjoint_epilogue<double>(akra_plan, LegMode, const void *, int, const void *,
                                               double, void *, int, cudaStream_t, int);
+
+AKRA_DEBUG_COLLECTOR(legendre)
 
 }  // namespace akra

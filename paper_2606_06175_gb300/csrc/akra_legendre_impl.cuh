@@ -2,6 +2,8 @@
 // of ring pairs, one group of RHS) shared by the per-plan launches (akra_legendre.cu) and the
 // persistent multi-instance launches (akra_batch.cu).  See akra_legendre.cu for the method.
 #pragma once
+#include <type_traits>
+
 #include "akra_internal.cuh"
 
 namespace akra {
@@ -27,22 +29,29 @@ __device__ __forceinline__ int block_min_start(int v)
 // current values): load the state of every pair whose recurrence starts here
 template <typename V4, typename T, int P>
 __device__ __forceinline__ void start_pairs(const V4 *__restrict__ seeds, const int2 *__restrict__ start,
-                                            size_t base, int lt, const int (&uid)[P],
+                                            size_t base, long long tbound, int lt, const int (&uid)[P],
                                             const int (&gs)[P], T (&vp)[P], T (&vm)[P],
                                             T (&vpo)[P], T (&vmo)[P], int (&e)[P])
 {
+    (void)tbound;
 #pragma unroll
     for (int k = 0; k < P; k++) {
         if (gs[k] == lt) {
-            const V4 s = seeds[base + uid[k]];
+            const V4 s = seeds[AKRA_IX(base + uid[k], tbound, kDbgSeeds)];
             vp[k] = s.x;
             vm[k] = s.y;
             vpo[k] = s.z;
             vmo[k] = s.w;
-            e[k] = start[base + uid[k]].y;
+            e[k] = start[AKRA_IX(base + uid[k], tbound, kDbgStart)].y;
         }
     }
 }
+
+}  // namespace akra
+
+#include "akra_legendre_f32x2.cuh"   // FP32 items with paired FMAs (use TL, block_min_start)
+
+namespace akra {
 
 // ---------------------------------------------------------------------------
 // synthesis: Φ(ring, ±m) for every ring of the listed units
@@ -67,6 +76,7 @@ __device__ __forceinline__ void leg_synth_item(const LegArgs<T> &a, const int m,
     const int l0 = m > 2 ? m : 2;
     const int tid = threadIdx.x;
     const long long mbase = (long long)m * (2 * L + 1 - m) / 2;
+    const long long tbound = (long long)(L + 1) * nunit_all;   // extent of the start tables
 
     // every pair's recurrence starts at its grid point gs (state loaded there); until then
     // its state is zero, which the recurrence keeps and the contraction ignores
@@ -77,14 +87,14 @@ __device__ __forceinline__ void leg_synth_item(const LegArgs<T> &a, const int m,
 #pragma unroll
     for (int k = 0; k < P; k++) {
         const int iu = (chunk * P + k) * NT + tid;
-        uid[k] = iu < nunits ? (units ? units[iu] : iu) : -1;
+        uid[k] = iu < nunits ? (units ? units[AKRA_IX(iu, nunits, kDbgUnits)] : iu) : -1;
         x[k] = 0;
         vp[k] = vm[k] = vpo[k] = vmo[k] = 0;
         e[k] = 0;
         gs[k] = kNeverLive;
         if (uid[k] >= 0) {
-            x[k] = (T)uinfo[uid[k]].x;
-            gs[k] = start[(size_t)m * nunit_all + uid[k]].x;
+            x[k] = (T)uinfo[AKRA_IX(uid[k], nunit_all, kDbgUnitInfo)].x;
+            gs[k] = start[AKRA_IX((size_t)m * nunit_all + uid[k], tbound, kDbgStart)].x;
         }
         my_first = min(my_first, gs[k]);
 #pragma unroll
@@ -100,8 +110,8 @@ __device__ __forceinline__ void leg_synth_item(const LegArgs<T> &a, const int m,
         // recurrence coefficients of two consecutive steps per entry: {A'_l, c'_l, A'_l+1, c'_l+1}
         for (int i = tid; i < TL / 2; i += NT) {
             const int l = lt + 2 * i;
-            const V4 c0 = (l <= L) ? coef[mbase + l] : V4{0, 0, 0, 0};
-            const V4 c1 = (l + 1 <= L) ? coef[mbase + l + 1] : V4{0, 0, 0, 0};
+            const V4 c0 = (l <= L) ? coef[AKRA_IX(mbase + l, ntri, kDbgCoef)] : V4{0, 0, 0, 0};
+            const V4 c1 = (l + 1 <= L) ? coef[AKRA_IX(mbase + l + 1, ntri, kDbgCoef)] : V4{0, 0, 0, 0};
             s_coef[i] = V4{c0.x, c0.y, c1.x, c1.y};
         }
         for (int i = tid; i < TL * RG; i += NT) {
@@ -109,10 +119,12 @@ __device__ __forceinline__ void leg_synth_item(const LegArgs<T> &a, const int m,
             const int l = lt + li, r = r0 + rr;
             V4 v{0, 0, 0, 0};
             if (l <= L && r < R) {
-                C2 E = alm[((size_t)r * 2 + 0) * ntri + mbase + l];
-                C2 B = alm[((size_t)r * 2 + 1) * ntri + mbase + l];
+                const long long abound = (long long)R * 2 * ntri;
+                C2 E = alm[AKRA_IX(((size_t)r * 2 + 0) * ntri + mbase + l, abound, kDbgAlm)];
+                C2 B = alm[AKRA_IX(((size_t)r * 2 + 1) * ntri + mbase + l, abound, kDbgAlm)];
                 // KS (or -1) factor times the monic scale σ_l: λ_l = σ_l μ_l
-                const T f = (fl ? fl[l] : T(-1)) * coef[mbase + l].z;
+                const T f = (fl ? fl[AKRA_IX(l, L + 1, kDbgKsFactor)] : T(-1)) *
+                            coef[AKRA_IX(mbase + l, ntri, kDbgCoef)].z;
                 if (m == 0) E.y = B.y = 0;
                 // c = f (E + iB), d = f (E - iB)
                 v = V4{f * (E.x - B.y), f * (E.y + B.x), f * (E.x + B.y), f * (E.y - B.x)};
@@ -121,7 +133,7 @@ __device__ __forceinline__ void leg_synth_item(const LegArgs<T> &a, const int m,
         }
         __syncthreads();
         const int nl = min(TL, L - lt + 1);
-        start_pairs(seeds, start, (size_t)m * nunit_all, lt, uid, gs, vp, vm, vpo, vmo, e);
+        start_pairs(seeds, start, (size_t)m * nunit_all, tbound, lt, uid, gs, vp, vm, vpo, vmo, e);
         if (warp_first > lt + TL - 1) continue;   // none of this warp's pairs has started yet
         bool live = true;
 #pragma unroll
@@ -194,10 +206,12 @@ __device__ __forceinline__ void leg_synth_item(const LegArgs<T> &a, const int m,
     // combine parities into the north and south rings and write Φ(±m)
     const bool swap = ((l0 + m) & 1) != 0;   // slot A holds odd (l+m) when l0+m is odd
     const size_t row = 2 * (size_t)L + 1;
+    const long long pbound = (long long)R * nring * row;   // extent of Φ
+    (void)pbound;
 #pragma unroll
     for (int k = 0; k < P; k++) {
         if (uid[k] < 0) continue;
-        const UnitInfo ui = uinfo[uid[k]];
+        const UnitInfo ui = uinfo[AKRA_IX(uid[k], nunit_all, kDbgUnitInfo)];
 #pragma unroll
         for (int rr = 0; rr < RG; rr++) {
             const int r = r0 + rr;
@@ -214,14 +228,14 @@ __device__ __forceinline__ void leg_synth_item(const LegArgs<T> &a, const int m,
             for (int side = 0; side < 2; side++) {
                 const int ring = side == 0 ? ui.ring_n : ui.ring_s;
                 if (ring < 0) continue;
-                if (ring_active && !ring_active[ring]) continue;
+                if (ring_active && !ring_active[AKRA_IX(ring, nring, kDbgRingActive)]) continue;
                 const int o = side == 0 ? 0 : 4;
                 const T sg = side == 0 ? T(1) : T(-1);
                 const T fr = se[o + 0] + sg * so[o + 0], fi = se[o + 1] + sg * so[o + 1];
                 const T gr = se[o + 2] + sg * so[o + 2], gi = se[o + 3] + sg * so[o + 3];
-                C2 *prow = phi + ((size_t)r * nring + ring) * row + L;
-                prow[m] = C2{fr, fi};
-                if (m > 0) prow[-m] = C2{gr, -gi};
+                const size_t pb = ((size_t)r * nring + ring) * row + L;   // Φ(ring, m = 0)
+                phi[AKRA_IX(pb + m, pbound, kDbgPhiWrite)] = C2{fr, fi};
+                if (m > 0) phi[AKRA_IX(pb - m, pbound, kDbgPhiWrite)] = C2{gr, -gi};
             }
         }
     }
@@ -235,14 +249,27 @@ __device__ __forceinline__ void leg_synth_item(const LegArgs<T> &a, const int m,
 //     (l+m) even: E += 2λ U1 + (-2)λ U2,  B += 2λ U3 + (-2)λ U4
 //     (l+m) odd : E += 2λ U3 - (-2)λ U4,  B += 2λ U1 - (-2)λ U2
 // ---------------------------------------------------------------------------
+// one synthesis work item: FP32 with paired FMAs, FP64 scalar
+template <typename T, int P, int RG, int NT>
+__device__ __forceinline__ void synth_item(const LegArgs<T> &a, int m, int chunk, int r0)
+{
+    if constexpr (std::is_same<T, float>::value) {
+        __shared__ float4 s_cf[TL];
+        __shared__ float4 s_a2[TL][RG][2];
+        leg_synth_item_f2<P, RG, NT>(a, m, chunk, r0, s_cf, s_a2);
+    } else {
+        __shared__ v4_t<T> s_coef[TL];
+        __shared__ v4_t<T> s_alm[TL][RG];
+        leg_synth_item<T, P, RG, NT>(a, m, chunk, r0, s_coef, s_alm);
+    }
+}
+
 template <typename T, int P, int RG, int NT>
 __global__ void __launch_bounds__(NT) k_leg_synth(LegArgs<T> a)
 {
-    __shared__ v4_t<T> s_coef[TL];
-    __shared__ v4_t<T> s_alm[TL][RG];
     if (a.skip && *a.skip) return;
     const int m = blockIdx.x / a.nchunks;
-    leg_synth_item<T, P, RG, NT>(a, m, blockIdx.x - m * a.nchunks, blockIdx.y * RG, s_coef, s_alm);
+    synth_item<T, P, RG, NT>(a, m, blockIdx.x - m * a.nchunks, blockIdx.y * RG);
 }
 
 // persistent form: blocks take (instance, m, chunk, RHS group) items from a queue ordered by cost
@@ -251,8 +278,6 @@ __global__ void __launch_bounds__(NT)
 k_leg_synth_queue(const LegArgs<T> *__restrict__ insts, const int4 *__restrict__ items, int nitems,
                   int *counter)
 {
-    __shared__ v4_t<T> s_coef[TL];
-    __shared__ v4_t<T> s_alm[TL][RG];
     __shared__ int s_it;
     for (;;) {
         if (threadIdx.x == 0) s_it = atomicAdd(counter, 1);
@@ -263,7 +288,7 @@ k_leg_synth_queue(const LegArgs<T> *__restrict__ insts, const int4 *__restrict__
         const int4 w = items[it];
         const LegArgs<T> a = insts[w.x];
         if (a.skip && *a.skip) continue;
-        leg_synth_item<T, P, RG, NT>(a, w.y, w.z, w.w * RG, s_coef, s_alm);
+        synth_item<T, P, RG, NT>(a, w.y, w.z, w.w * RG);
     }
 }
 
@@ -304,6 +329,11 @@ __device__ __forceinline__ void leg_adjoint_item(
     const long long mbase = (long long)m * (2 * L + 1 - m) / 2;
     const size_t row = 2 * (size_t)L + 1;
     const bool swap = ((l0 + m) & 1) != 0;
+    const long long tbound = (long long)(L + 1) * nunit_all;        // extent of the start tables
+    const long long pbound = (long long)R * nring * row;            // extent of Φ'
+    const long long qbound = (long long)a.nchunks * R * ntri * 4;   // extent of the partial sums
+    (void)pbound;
+    (void)qbound;
 
     T x[P], vp[P], vm[P], vpo[P], vmo[P];
     int e[P], uid[P], gs[P];
@@ -316,7 +346,7 @@ __device__ __forceinline__ void leg_adjoint_item(
     for (int k = 0; k < P; k++) {
         // each warp holds 32 P consecutive pairs (close in latitude, so close in start point)
         const int iu = chunk * P * NT + warp * 32 * P + k * 32 + lane;
-        const int u = iu < nunits ? (units ? units[iu] : iu) : -1;
+        const int u = iu < nunits ? (units ? units[AKRA_IX(iu, nunits, kDbgUnits)] : iu) : -1;
         uid[k] = u;
         x[k] = 0;
         vp[k] = vm[k] = vpo[k] = vmo[k] = 0;
@@ -325,9 +355,9 @@ __device__ __forceinline__ void leg_adjoint_item(
         UnitInfo ui;
         ui.ring_n = ui.ring_s = -1;
         if (u >= 0) {
-            ui = uinfo[u];
+            ui = uinfo[AKRA_IX(u, nunit_all, kDbgUnitInfo)];
             x[k] = (T)ui.x;
-            gs[k] = start[(size_t)m * nunit_all + u].x;
+            gs[k] = start[AKRA_IX((size_t)m * nunit_all + u, tbound, kDbgStart)].x;
         }
         my_first = min(my_first, gs[k]);
 #pragma unroll
@@ -340,9 +370,10 @@ __device__ __forceinline__ void leg_adjoint_item(
                 Pv[side] = C2{0, 0};
                 Qv[side] = C2{0, 0};
                 if (ring < 0 || r >= R) continue;
-                if (ring_active && !ring_active[ring]) continue;
-                const C2 *prow = phi + ((size_t)r * nring + ring) * row + L;
-                const C2 g = prow[m], gm = prow[-m];
+                if (ring_active && !ring_active[AKRA_IX(ring, nring, kDbgRingActive)]) continue;
+                const size_t pb = ((size_t)r * nring + ring) * row + L;   // Φ'(ring, m = 0)
+                const C2 g = phi[AKRA_IX(pb + m, pbound, kDbgPhiRead)];
+                const C2 gm = phi[AKRA_IX(pb - m, pbound, kDbgPhiRead)];
                 Pv[side] = g;
                 Qv[side] = C2{gm.x, -gm.y};
             }
@@ -364,17 +395,19 @@ __device__ __forceinline__ void leg_adjoint_item(
     for (int i = tid; i < (min(l_first, L + 1) - l0) * RG * 4; i += NT) {
         const int step = i / (RG * 4), rem = i - step * RG * 4, rr = rem >> 2, q = rem & 3;
         const int r = r0 + rr;
-        if (r < R) partial[(((size_t)chunk * R + r) * ntri + mbase + l0 + step) * 4 + q] = T(0);
+        if (r < R)
+            partial[AKRA_IX((((size_t)chunk * R + r) * ntri + mbase + l0 + step) * 4 + q, qbound,
+                            kDbgPartialWrite)] = T(0);
     }
     for (int lt = l_first; lt <= L; lt += TLA) {
         __syncthreads();
         for (int i = tid; i < TLA; i += NT) {
             const int l = lt + i;
-            s_coef[i] = (l <= L) ? coef[mbase + l] : V4{0, 0, 0, 0};
+            s_coef[i] = (l <= L) ? coef[AKRA_IX(mbase + l, ntri, kDbgCoef)] : V4{0, 0, 0, 0};
         }
         __syncthreads();
         const int nl = min(TLA, L - lt + 1);
-        start_pairs(seeds, start, (size_t)m * nunit_all, lt, uid, gs, vp, vm, vpo, vmo, e);
+        start_pairs(seeds, start, (size_t)m * nunit_all, tbound, lt, uid, gs, vp, vm, vpo, vmo, e);
         if (warp_first > lt + TLA - 1) {
             // none of this warp's pairs has started yet: its rows of the tile sum are zero
             T *zr = &s_red[warp][0][0][0];
@@ -471,20 +504,36 @@ __device__ __forceinline__ void leg_adjoint_item(
 #pragma unroll
             for (int w = 0; w < NW; w++) sv += s_red[w][step][rr][q];
             // the recurrence ran on μ_l = λ_l / σ_l
-            partial[(((size_t)chunk * R + r) * ntri + mbase + lt + step) * 4 + q] = sv * s_coef[step].z;
+            partial[AKRA_IX((((size_t)chunk * R + r) * ntri + mbase + lt + step) * 4 + q, qbound,
+                            kDbgPartialWrite)] = sv * s_coef[step].z;
         }
+    }
+}
+
+// one adjoint work item: FP32 with paired FMAs, FP64 scalar
+template <typename T, int P, int RG, int NT>
+__device__ __forceinline__ void adjoint_item(const LegArgs<T> &a, int m, int chunk, int r0)
+{
+    if constexpr (std::is_same<T, float>::value) {
+        __shared__ float4 s_cf[TL];
+        __shared__ float s_sig[TL];
+        __shared__ float s_red[NT / 32][TL][RG][4];
+        __shared__ __align__(16) float s_tr[NT / 32][32][36];
+        leg_adjoint_item_f2<P, RG, NT>(a, m, chunk, r0, s_cf, s_sig, s_red, s_tr);
+    } else {
+        __shared__ v4_t<T> s_coef[AdjTile<T, RG>::v];
+        __shared__ T s_red[NT / 32][AdjTile<T, RG>::v][RG][4];
+        __shared__ __align__(16) T s_tr[NT / 32][32][TrStride<T>::v];
+        leg_adjoint_item<T, P, RG, NT>(a, m, chunk, r0, s_coef, s_red, s_tr);
     }
 }
 
 template <typename T, int P, int RG, int NT>
 __global__ void __launch_bounds__(NT) k_leg_adjoint(LegArgs<T> a)
 {
-    __shared__ v4_t<T> s_coef[AdjTile<T, RG>::v];
-    __shared__ T s_red[NT / 32][AdjTile<T, RG>::v][RG][4];
-    __shared__ __align__(16) T s_tr[NT / 32][32][TrStride<T>::v];
     if (a.skip && *a.skip) return;
     const int m = blockIdx.x / a.nchunks;
-    leg_adjoint_item<T, P, RG, NT>(a, m, blockIdx.x - m * a.nchunks, blockIdx.y * RG, s_coef, s_red, s_tr);
+    adjoint_item<T, P, RG, NT>(a, m, blockIdx.x - m * a.nchunks, blockIdx.y * RG);
 }
 
 template <typename T, int P, int RG, int NT>
@@ -492,9 +541,6 @@ __global__ void __launch_bounds__(NT)
 k_leg_adjoint_queue(const LegArgs<T> *__restrict__ insts, const int4 *__restrict__ items, int nitems,
                     int *counter)
 {
-    __shared__ v4_t<T> s_coef[AdjTile<T, RG>::v];
-    __shared__ T s_red[NT / 32][AdjTile<T, RG>::v][RG][4];
-    __shared__ __align__(16) T s_tr[NT / 32][32][TrStride<T>::v];
     __shared__ int s_it;
     for (;;) {
         if (threadIdx.x == 0) s_it = atomicAdd(counter, 1);
@@ -505,7 +551,7 @@ k_leg_adjoint_queue(const LegArgs<T> *__restrict__ insts, const int4 *__restrict
         const int4 w = items[it];
         const LegArgs<T> a = insts[w.x];
         if (a.skip && *a.skip) continue;
-        leg_adjoint_item<T, P, RG, NT>(a, w.y, w.z, w.w * RG, s_coef, s_red, s_tr);
+        adjoint_item<T, P, RG, NT>(a, w.y, w.z, w.w * RG);
     }
 }
 

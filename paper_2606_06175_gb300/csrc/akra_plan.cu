@@ -583,6 +583,46 @@ extern "C" void akra_plan_destroy(akra_plan p)
     delete p;
 }
 
+extern "C" akra_status akra_debug_violations(long long *count, int *site, long long *index,
+                                             long long *bound)
+{
+    if (!count) {
+        set_error("akra_debug_violations: NULL count");
+        return AKRA_EINVAL;
+    }
+#ifdef AKRA_DEBUG
+    DebugRecord acc{};
+    AKRA_CUDA_TRY(cudaDeviceSynchronize());
+    AKRA_TRY(debug_collect_legendre(&acc));
+    AKRA_TRY(debug_collect_batch(&acc));
+    AKRA_TRY(debug_collect_ringfft(&acc));
+    AKRA_TRY(debug_collect_ringfft32(&acc));
+    *count = (long long)acc.count;
+    if (site) *site = acc.site;
+    if (index) *index = acc.index;
+    if (bound) *bound = acc.bound;
+#else
+    *count = -1;   // release build: no checks compiled in
+    if (site) *site = 0;
+    if (index) *index = 0;
+    if (bound) *bound = 0;
+#endif
+    return AKRA_OK;
+}
+
+extern "C" akra_status akra_plan_fill_workspaces(akra_plan p, int byte, void *stream)
+{
+    if (!p || byte < 0 || byte > 255) {
+        set_error("akra_plan_fill_workspaces: NULL plan or byte outside [0, 255]");
+        return AKRA_EINVAL;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    akra::Workspace *ws[] = {&p->phi, &p->partial, &p->cg, &p->red, &p->xsave, &p->red_cl};
+    for (akra::Workspace *w : ws)
+        if (w->ptr && w->bytes) AKRA_CUDA_TRY(cudaMemsetAsync(w->ptr, byte, w->bytes, st));
+    return AKRA_OK;
+}
+
 extern "C" akra_status akra_plan_describe(akra_plan p, akra_plan_desc *out)
 {
     if (!p || !out) {

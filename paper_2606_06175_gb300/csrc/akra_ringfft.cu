@@ -158,12 +158,15 @@ k_ring_fft(int L, int nring, long long npix, int nmax, const int *__restrict__ r
     const int ring = rings ? rings[blockIdx.x] : (int)blockIdx.x;
     const int r = blockIdx.y;
     const int tid = threadIdx.x;
-    const RingInfo ri = rinfo[ring];
+    const RingInfo ri = rinfo[AKRA_IX(ring, nring, kDbgFftRing)];
     const int n = ri.nphi, sigma = ri.sigma;
     const long long first = ri.first;
     const FftFactors fac = factors[ri.ilen];
     const C2 *tw = tw_all + ri.tw_off;
     C2 *prow = phi + ((size_t)r * nring + ring) * (2 * (size_t)L + 1) + L;   // prow[m], |m| <= L
+    // checked offsets within the ring's Φ row (|m| <= L) and within the map (pixel < npix)
+#define AKRA_ROW(m) (AKRA_IX((long long)L + (m), 2LL * L + 1, kDbgFftPhi) - L)
+#define AKRA_PIX(j, site) (AKRA_IX(first + (j), npix, site) - first)
 
     if (MODE != (int)FftMode::Adjoint) {
         // fold Φ(m) into n bins
@@ -172,7 +175,7 @@ k_ring_fft(int L, int nring, long long npix, int nmax, const int *__restrict__ r
                 const int qlo = -((L + k) / n), qhi = floordiv(L - k, n);
                 C2 acc{0, 0};
                 for (int q = qlo; q <= qhi; q++) {
-                    const C2 v = prow[k + n * q];
+                    const C2 v = prow[AKRA_ROW(k + n * q)];
                     if (sigma && (q & 1)) { acc.x -= v.x; acc.y -= v.y; }
                     else { acc.x += v.x; acc.y += v.y; }
                 }
@@ -184,7 +187,7 @@ k_ring_fft(int L, int nring, long long npix, int nmax, const int *__restrict__ r
                 const int qlo = -((L + k) / n), qhi = floordiv(L - k, n);
                 C2 acc{0, 0};
                 for (int q = qlo + g; q <= qhi; q += G) {
-                    const C2 v = prow[k + n * q];
+                    const C2 v = prow[AKRA_ROW(k + n * q)];
                     if (sigma && (q & 1)) { acc.x -= v.x; acc.y -= v.y; }
                     else { acc.x += v.x; acc.y += v.y; }
                 }
@@ -208,17 +211,17 @@ k_ring_fft(int L, int nring, long long npix, int nmax, const int *__restrict__ r
             for (int j = tid; j < n; j += FFT_NT) {
                 C2 v = data[j];
                 if (weighted) {
-                    const T wj = W[first + j];
+                    const T wj = W[AKRA_IX(first + j, npix, kDbgFftWeight)];
                     v.x *= wj;
                     v.y *= wj;
                 }
-                o1[j] = v.x;
-                o2[j] = v.y;
+                o1[AKRA_PIX(j, kDbgFftMapOut)] = v.x;
+                o2[AKRA_PIX(j, kDbgFftMapOut)] = v.y;
             }
             return;
         }
         for (int j = tid; j < n; j += FFT_NT) {
-            const T wj = W[first + j];
+            const T wj = W[AKRA_IX(first + j, npix, kDbgFftWeight)];
             data[j].x *= wj;
             data[j].y *= wj;
         }
@@ -227,9 +230,9 @@ k_ring_fft(int L, int nring, long long npix, int nmax, const int *__restrict__ r
         const T *u1 = map_in + ((size_t)r * 2 + 0) * npix + first;
         const T *u2 = map_in + ((size_t)r * 2 + 1) * npix + first;
         for (int j = tid; j < n; j += FFT_NT) {
-            C2 v{u1[j], u2[j]};
+            C2 v{u1[AKRA_PIX(j, kDbgFftMapIn)], u2[AKRA_PIX(j, kDbgFftMapIn)]};
             if (weighted) {
-                const T wj = W[first + j];
+                const T wj = W[AKRA_IX(first + j, npix, kDbgFftWeight)];
                 v.x *= wj;
                 v.y *= wj;
             }
@@ -247,8 +250,10 @@ k_ring_fft(int L, int nring, long long npix, int nmax, const int *__restrict__ r
             v = cmul<T>(v, twid<T, -1>(tw, k));
             if (q & 1) { v.x = -v.x; v.y = -v.y; }
         }
-        prow[m] = v;
+        prow[AKRA_ROW(m)] = v;
     }
+#undef AKRA_ROW
+#undef AKRA_PIX
 }
 
 template <typename T> const cx_t<T> *tw_ptr(akra_plan p);
@@ -313,5 +318,7 @@ template akra_status ring_fft<float>(akra_plan, FftMode, void *, const void *, v
                                      const int *, int, cudaStream_t);
 template akra_status ring_fft<double>(akra_plan, FftMode, void *, const void *, void *, bool, int,
                                       const int *, int, cudaStream_t);
+
+AKRA_DEBUG_COLLECTOR(ringfft)
 
 }  // namespace akra

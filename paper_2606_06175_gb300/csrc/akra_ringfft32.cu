@@ -200,4 +200,6 @@ akra_status ring_fft32(akra_plan p, FftMode mode, void *phi, const void *map_in,
     return AKRA_OK;
 }
 
+AKRA_DEBUG_COLLECTOR(ringfft32)
+
 }  // namespace akra

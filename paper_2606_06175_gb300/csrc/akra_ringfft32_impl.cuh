@@ -257,7 +257,7 @@ __device__ __forceinline__ void ring_fft32_item(const Fft32Args &a, const int ri
     const float *__restrict__ map_in = a.map_in;
     float *__restrict__ map_out = a.map_out;
     const int tid = threadIdx.x;
-    const RingInfo ri = rinfo[ring];
+    const RingInfo ri = rinfo[AKRA_IX(ring, nring, kDbgFftRing)];
     const int n = ri.nphi, sigma = ri.sigma;
     const long long first = ri.first;
     const float2 *tw = tw_all + ri.tw_off;         // e^{iπ t/n}, t < 2n
@@ -266,6 +266,9 @@ __device__ __forceinline__ void ring_fft32_item(const Fft32Args &a, const int ri
     const int logM = 31 - __clz(M), logn = 31 - __clz(n);
     const float2 *bhat = pow2 ? nullptr : bhat_all + bhat_off[ri.ilen];
     float2 *prow = phi + ((size_t)r * nring + ring) * (2 * (size_t)L + 1) + L;
+    // checked offsets within the ring's Φ row (|m| <= L) and within the map (pixel < npix)
+#define AKRA_ROW(m) (AKRA_IX((long long)L + (m), 2LL * L + 1, kDbgFftPhi) - L)
+#define AKRA_PIX(j, site) (AKRA_IX(first + (j), npix, site) - first)
 
     if (MODE != (int)FftMode::Adjoint) {
         // fold Φ(m) into n bins: F[k] = e^{iπσk/n} Σ_q (-1)^{σq} Φ(k + nq)
@@ -282,7 +285,7 @@ __device__ __forceinline__ void ring_fft32_item(const Fft32Args &a, const int ri
                 for (int u = 0; u < F32_KPT; u++) {
                     const int k = tid + u * F32_NT, m = k + n * q;
                     if (k < n && m >= -L && m <= L) {
-                        const float2 v = prow[m];
+                        const float2 v = prow[AKRA_ROW(m)];
                         acc[u] = neg ? csub(acc[u], v) : cadd(acc[u], v);
                     }
                 }
@@ -298,7 +301,7 @@ __device__ __forceinline__ void ring_fft32_item(const Fft32Args &a, const int ri
                 const int qlo = -((L + k) / n), qhi = fdiv(L - k, n);
                 float2 acc = make_float2(0.f, 0.f);
                 for (int q = qlo + g; q <= qhi; q += G) {
-                    const float2 v = prow[k + n * q];
+                    const float2 v = prow[AKRA_ROW(k + n * q)];
                     if (sigma && (q & 1)) acc = csub(acc, v);
                     else acc = cadd(acc, v);
                 }
@@ -322,12 +325,12 @@ __device__ __forceinline__ void ring_fft32_item(const Fft32Args &a, const int ri
                 const int j = pow2 ? (int)(__brev((unsigned)k) >> (32 - logn)) : k;
                 float2 v = buf[pd(k)];
                 if (weighted) {
-                    const float wj = W[first + k];
+                    const float wj = W[AKRA_IX(first + k, npix, kDbgFftWeight)];
                     v.x *= wj;
                     v.y *= wj;
                 }
-                o1[j] = v.x;
-                o2[j] = v.y;
+                o1[AKRA_PIX(j, kDbgFftMapOut)] = v.x;
+                o2[AKRA_PIX(j, kDbgFftMapOut)] = v.y;
             }
             return;
         }
@@ -336,7 +339,7 @@ __device__ __forceinline__ void ring_fft32_item(const Fft32Args &a, const int ri
         for (int u = 0; u < F32_KPT; u++) {
             const int k = tid + u * F32_NT;
             if (k < n) {
-                const float wj = W[first + k];
+                const float wj = W[AKRA_IX(first + k, npix, kDbgFftWeight)];
                 buf[pd(k)].x *= wj;
                 buf[pd(k)].y *= wj;
             }
@@ -347,9 +350,9 @@ __device__ __forceinline__ void ring_fft32_item(const Fft32Args &a, const int ri
         const float *u2 = map_in + ((size_t)r * 2 + 1) * npix + first;
         for (int k = tid; k < n; k += F32_NT) {
             const int j = pow2 ? (int)(__brev((unsigned)k) >> (32 - logn)) : k;
-            float2 v = make_float2(u1[j], u2[j]);
+            float2 v = make_float2(u1[AKRA_PIX(j, kDbgFftMapIn)], u2[AKRA_PIX(j, kDbgFftMapIn)]);
             if (weighted) {
-                const float wj = W[first + k];
+                const float wj = W[AKRA_IX(first + k, npix, kDbgFftWeight)];
                 v.x *= wj;
                 v.y *= wj;
             }
@@ -369,8 +372,10 @@ __device__ __forceinline__ void ring_fft32_item(const Fft32Args &a, const int ri
             v = cmc(v, tw[k]);
             if (q & 1) v = make_float2(-v.x, -v.y);
         }
-        prow[m] = v;
+        prow[AKRA_ROW(m)] = v;
     }
+#undef AKRA_ROW
+#undef AKRA_PIX
 }
 
 
