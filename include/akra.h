@@ -357,6 +357,20 @@ akra_status akra_plan_get_shape(akra_plan plan, akra_prec prec, int R, int *P, i
  * The results do not depend on the shape beyond rounding order.  Errors: EINVAL. */
 akra_status akra_plan_set_shape(akra_plan plan, akra_prec prec, int R, int P, int PA, int RG);
 
+/* FP32 Legendre synthesis on the tensor core (the paper has no counterpart; an implementation
+ * choice of the FP32 operator).  group = 4, 8, 16 or 32 runs the synthesis of every FP32
+ * operator with (prec, R) = (AKRA_F32, R) on tcgen05 tensor cores, RHS taken `group` at a time:
+ * the recurrences stay on the CUDA cores, their values split into a TF32 head and an FP32
+ * remainder, and the l-sum is three TF32 products (head·head, head·rest, rest·head) accumulated in
+ * FP32 -- about 21 bits per product, within the FP32 operator's tolerance.  group = 0 selects the
+ * CUDA-core synthesis.  akra_autotune considers both; akra_plan_set_shape resets the choice to
+ * the CUDA-core synthesis.  If a tensor-core completion wait exceeds its bound (it should not),
+ * the next blocking call (a solve, akra_autotune, akra_time_H_stages) returns ECUDA.
+ * Errors: EINVAL (group, R, flat-sky plan). */
+akra_status akra_plan_set_tc_synthesis(akra_plan plan, int R, int group);
+/* The group set for (AKRA_F32, R): 0 (CUDA-core synthesis) or 4, 8, 16, 32.  Errors: EINVAL. */
+akra_status akra_plan_get_tc_synthesis(akra_plan plan, int R, int *group);
+
 /* Measured FMA rate of the current device in TFLOP/s (2 flops per FMA) for prec AKRA_F32 or
  * AKRA_F64: a saturating kernel of independent FMA chains on every SM, timed with CUDA events
  * (tens of milliseconds; blocking).  The denominator of the Legendre kernels' pipe fractions;

@@ -56,7 +56,7 @@ EXPORTS = ["akra_plan_create", "akra_plan_destroy", "akra_last_error", "akra_ver
            "akra_plan_get_shape", "akra_plan_set_shape", "akra_set_mixed_policy", "akra_fma_rate",
            "akra_cg_solve_fields", "akra_shuffle_shear", "akra_cl_spectra",
            "akra_plan_set_preconditioner", "akra_flat_plan_create", "akra_plan_fill_workspaces",
-           "akra_debug_violations"]
+           "akra_debug_violations", "akra_plan_set_tc_synthesis", "akra_plan_get_tc_synthesis"]
 
 _lib_handle = None
 
@@ -107,6 +107,8 @@ def load(build_if_missing: bool = False):
         "akra_autotune": ([vp, i, i, vp], i),
         "akra_plan_get_shape": ([vp, i, i, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)], i),
         "akra_plan_set_shape": ([vp, i, i, i, i, i], i),
+        "akra_plan_set_tc_synthesis": ([vp, i, i], i),
+        "akra_plan_get_tc_synthesis": ([vp, i, ctypes.POINTER(i)], i),
         "akra_time_H_stages": ([vp, i, i, i, vp, ctypes.POINTER(ctypes.c_double)], i),
         "akra_synth_spin2_static": ([vp, i, vp, vp, i, vp], i),
         "akra_cg_solve_adjoint": ([vp, i, vp, vp, i, d, i, ctypes.POINTER(CgInfo), vp], i),
@@ -410,6 +412,18 @@ def akra_plan_get_shape(plan: Plan, prec: int, R: int = 1) -> dict:
     _check(load().akra_plan_get_shape(plan.handle, prec, R, ctypes.byref(P), ctypes.byref(PA),
                                       ctypes.byref(RG)))
     return {"P": P.value, "PA": PA.value, "RG": RG.value}
+
+
+def akra_plan_set_tc_synthesis(plan: Plan, R: int, group: int):
+    """FP32 synthesis for R RHS on the tensor core with RHS groups of `group` (4, 8, 16, 32), or on
+    the CUDA cores (group 0)."""
+    _check(load().akra_plan_set_tc_synthesis(plan.handle, R, group))
+
+
+def akra_plan_get_tc_synthesis(plan: Plan, R: int = 1) -> int:
+    g = ctypes.c_int()
+    _check(load().akra_plan_get_tc_synthesis(plan.handle, R, ctypes.byref(g)))
+    return g.value
 
 
 def akra_plan_set_shape(plan: Plan, prec: int, R: int, P: int, PA: int, RG: int):

@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 OUT = os.path.join(HERE, "libakra.so")
 OUT_DEBUG = os.path.join(HERE, "libakra_debug.so")
-TUS = ["akra_plan", "akra_legendre", "akra_ringfft", "akra_ringfft32", "akra_cg", "akra_grad", "akra_batch",
+TUS = ["akra_plan", "akra_legendre", "akra_legendre_tc", "akra_ringfft", "akra_ringfft32", "akra_cg", "akra_grad", "akra_batch",
        "akra_static", "akra_diag", "akra_spectra", "akra_flat"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",

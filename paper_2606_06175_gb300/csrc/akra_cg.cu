@@ -648,6 +648,7 @@ static akra_status solve_b(akra_plan p, akra_prec prec, const void *bsrc, void *
     AKRA_CUDA_TRY(cudaStreamWaitEvent(user, p->ev_b, 0));
     AKRA_CUDA_TRY(cudaEventRecord(p->ev_a, cs));
     AKRA_TRY(bounded_wait(p->ev_a, deadline));
+    AKRA_TRY(tc_error_check(p));
     if (info) {
         info->iters = total_iters;
         info->outer = outer;

@@ -88,6 +88,7 @@ __device__ __forceinline__ long long dbg_index(long long i, long long bound, int
     akra_status debug_collect_##tu(DebugRecord *) { return AKRA_OK; }
 #endif
 akra_status debug_collect_legendre(DebugRecord *acc);
+akra_status debug_collect_legendre_tc(DebugRecord *acc);
 akra_status debug_collect_batch(DebugRecord *acc);
 akra_status debug_collect_ringfft(DebugRecord *acc);
 akra_status debug_collect_ringfft32(DebugRecord *acc);
@@ -156,6 +157,8 @@ struct LegShape {
     int NT;                // threads per block
     int RG;                // RHS handled together by one block
     int PA = 0;            // ring pairs per thread of the adjoint (0: same as P)
+    int TC = 0;            // FP32 synthesis on the tensor core with RHS groups of TC (4, 8, 16,
+                           // 32); 0: CUDA-core synthesis of shape (P, RG)
     int adjP() const { return PA > 0 ? PA : P; }
 };
 
@@ -176,6 +179,7 @@ struct LegArgs {
     T *partial;                       // adjoint output   [nchunks][R][ntri][4]
     const unsigned char *ring_active; // nullptr = all rings
     const int *skip;                  // device flag: return at once if set
+    int *err;                         // device flag set when a tensor-core wait runs out (or nullptr)
 };
 
 // arguments of one FP32 ring-FFT instance
@@ -288,6 +292,7 @@ struct akra_plan_s {
     std::map<long long, akra::CgGraph *> graphs;
     unsigned ws_gen = 0;                     // bumped whenever a workspace is reallocated
     const int *cur_skip = nullptr;           // device flag: operator kernels return early if set
+    int *d_tc_err = nullptr;                 // device flag: a tensor-core completion wait ran out
     void *h_pinned = nullptr;                // pinned host mirror for status polling
     size_t bytes_tables = 0;
     long long launches = 0;                  // kernels launched (host-side count)
@@ -301,6 +306,14 @@ size_t plan_device_bytes(akra_plan p);
 
 // the operator pieces (all asynchronous on `st`)
 enum class LegMode { Synth, KS };   // per-l factor f_l = -1 (pure spin-2 SHT) or D_l (KS)
+
+// FP32 synthesis with the tensor-core contraction (akra_legendre_tc.cu), RHS in groups of tcg
+akra_status legendre_synth_tc(akra_plan p, int tcg, LegMode mode, const void *alm, void *phi, int R,
+                              const int *units, int nunits, cudaStream_t st);
+akra_status legendre_tc_prepare();
+// reads and clears the plan's tensor-core error flag (blocking): ECUDA if a wait ran out
+akra_status tc_error_check(akra_plan p);
+
 
 LegShape leg_shape(akra_plan p, akra_prec prec, int R);
 int legendre_chunks(int nunits, const LegShape &s);

@@ -137,6 +137,8 @@ akra_status legendre_synth(akra_plan p, const LegShape &s, LegMode mode, const v
                            void *phi, int R, const int *units, int nunits, cudaStream_t st)
 {
     if (nunits <= 0) return AKRA_OK;
+    if constexpr (std::is_same<T, float>::value)
+        if (s.TC > 0) return legendre_synth_tc(p, s.TC, mode, alm, phi, R, units, nunits, st);
 #define AKRA_S(PP, RR)                                                                      \
     if (s.P == PP && s.RG == RR) {                                                          \
         launch_synth<T, PP, RR, 128>(p, mode, alm, phi, R, units, nunits, st);              \

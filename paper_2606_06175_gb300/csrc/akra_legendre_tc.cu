@@ -1,0 +1,342 @@
+// akra_legendre_tc.cu -- FP32 spin-2 Legendre synthesis (Eq. 1 in the φ-separated form, one m and
+// one ring pair per row) with the l-contraction on the 5th-generation tensor core.
+//
+// For one m, a chunk of 128 ring pairs and a group of RG right-hand sides, the synthesis is a
+// product of a generated matrix with the staged coefficients:
+//     D_{s,p}[u][n] = Σ_{l of parity p} ξ^s_l(u) · b_l[n],
+// u = ring pair, s = spin (+2, -2), p = parity of l - l0, n = (RHS, component of c or d) where
+// c = f_l σ_l s_l (E + iB), d = f_l σ_l s_l (E - iB) as in the FP32 CUDA-core item (s_l the state
+// sign, σ_l the monic scale, f_l = -1 or the KS factor D_l).  The recurrences run on the CUDA cores
+// (one pair per thread, both spins in one float2 with paired FMAs); every 16 l-steps the values
+// are split into a TF32 head and an FP32 remainder and stored as the A tiles, and one thread
+// issues the MMAs: 4 streams (s, p) x 3 products (head·head, head·rest, rest·head) of
+// M = 128 rows, N = 4 RG columns, K = 8 l-values, accumulated in FP32 in tensor memory.
+// Tiles are double-buffered: the recurrence of tile t+1 runs while the MMAs of tile t do.  After
+// the last tile each thread reads its own row (TMEM lane = ring pair) and forms Φ(±m) of both
+// rings as the CUDA-core item does.
+#include "akra_legendre_impl.cuh"
+#include "akra_tc.cuh"
+
+namespace akra {
+
+namespace {
+
+constexpr int TCT = 16;        // l-steps per tile: 8 of each parity (K = 8 TF32 per MMA)
+constexpr int TC_NT = 128;     // threads = ring pairs per block = MMA rows
+constexpr int kWaitLimit = 1 << 22;
+
+template <int RG>
+struct TcSynth {
+    static constexpr int N = 4 * RG;                         // MMA columns per stream
+    static constexpr int A_TILE = 128 * 8 * 4;               // 4 KB
+    static constexpr int B_TILE = N * 8 * 4;
+    static constexpr int BUF = 8 * A_TILE + 4 * B_TILE;      // A[s][p][h], B[p][h]
+    static constexpr int CF = TCT * 16;                      // float4 coefficients of a tile
+    static constexpr int USED = 2 * BUF + 2 * CF;
+    // TMEM columns: 4 streams x N (a power of two >= 32); shared memory sized so that the blocks
+    // resident on an SM never ask for more than its 512 columns
+    static constexpr uint32_t NCOL = 16 * RG < 32 ? 32 : 16 * RG;
+    static constexpr int MAXB = 512 / (int)NCOL;
+    static constexpr int SMEM = (MAXB >= 3 || USED * (MAXB + 1) > 227 * 1024) ? USED : (227 * 1024) / (MAXB + 1) + 1024;
+};
+
+__device__ __forceinline__ unsigned char *tc_a(unsigned char *buf, int s, int p, int h)
+{
+    return buf + ((s * 2 + p) * 2 + h) * (128 * 8 * 4);
+}
+
+template <int RG>
+__device__ __forceinline__ unsigned char *tc_b(unsigned char *buf, int p, int h)
+{
+    return buf + 8 * TcSynth<RG>::A_TILE + (p * 2 + h) * TcSynth<RG>::B_TILE;
+}
+
+// stage tile [lt, lt + 16): recurrence coefficients (threads 0..15) and the B tiles
+template <int RG>
+__device__ __forceinline__ void tc_stage(const LegArgs<float> &a, int m, long long mbase, int r0, int lt,
+                                         unsigned char *buf, float4 *cf)
+{
+    const int L = a.L, R = a.R;
+    const long long ntri = a.ntri;
+    const int tid = threadIdx.x;
+    if (tid < TCT) {
+        const int l = lt + tid;
+        cf[tid] = (l <= L) ? f2_coef_entry(a.coef[AKRA_IX(mbase + l, ntri, kDbgCoef)], tid)
+                           : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    for (int e = tid; e < TCT * RG; e += TC_NT) {
+        const int i = e / RG, rr = e - i * RG;
+        const int l = lt + i, r = r0 + rr, p = i & 1, k = i >> 1;
+        float v[4] = {0.f, 0.f, 0.f, 0.f};
+        if (l <= L && r < R) {
+            const long long abound = (long long)R * 2 * ntri;
+            (void)abound;
+            float2 E = a.alm[AKRA_IX(((size_t)r * 2 + 0) * ntri + mbase + l, abound, kDbgAlm)];
+            float2 B = a.alm[AKRA_IX(((size_t)r * 2 + 1) * ntri + mbase + l, abound, kDbgAlm)];
+            const float f = (a.fl ? a.fl[AKRA_IX(l, L + 1, kDbgKsFactor)] : -1.f) *
+                            a.coef[AKRA_IX(mbase + l, ntri, kDbgCoef)].z * f2_sign(i);
+            if (m == 0) E.y = B.y = 0.f;
+            v[0] = f * (E.x - B.y);   // c.re
+            v[1] = f * (E.y + B.x);   // c.im
+            v[2] = f * (E.x + B.y);   // d.re
+            v[3] = f * (E.y - B.x);   // d.im
+        }
+#pragma unroll
+        for (int c = 0; c < 4; c++) {
+            const float hd = tc::tf32_head(v[c]);
+            const uint32_t o = tc::tile_off(4 * rr + c, k);
+            *reinterpret_cast<float *>(tc_b<RG>(buf, p, 0) + o) = hd;
+            *reinterpret_cast<float *>(tc_b<RG>(buf, p, 1) + o) = v[c] - hd;
+        }
+    }
+}
+
+// the A rows of this thread (ring pair) for 8 consecutive steps: lam[j] = (ξ+, ξ-) at step
+// 8 half + j, so parity p holds k = 4 half + q at j = p + 2q
+__device__ __forceinline__ void tc_store_half(unsigned char *buf, int row, int half, const float2 (&lam)[8])
+{
+    const uint32_t o = tc::tile_off(row, 4 * half);
+#pragma unroll
+    for (int p = 0; p < 2; p++) {
+#pragma unroll
+        for (int s = 0; s < 2; s++) {
+            float4 hd, rs;
+            float *ph = &hd.x, *pr = &rs.x;
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                const float x = s == 0 ? lam[p + 2 * q].x : lam[p + 2 * q].y;
+                ph[q] = tc::tf32_head(x);
+                pr[q] = x - ph[q];
+            }
+            *reinterpret_cast<float4 *>(tc_a(buf, s, p, 0) + o) = hd;
+            *reinterpret_cast<float4 *>(tc_a(buf, s, p, 1) + o) = rs;
+        }
+    }
+}
+
+}  // namespace
+
+template <int RG>
+__global__ void __launch_bounds__(TC_NT) k_leg_synth_tc(LegArgs<float> a)
+{
+    using S = TcSynth<RG>;
+    constexpr int N = S::N;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(8) uint64_t s_mbar[2];
+    __shared__ uint32_t s_tmem;
+    if (a.skip && *a.skip) return;
+    const int m = blockIdx.x / a.nchunks, chunk = blockIdx.x - m * a.nchunks, r0 = blockIdx.y * RG;
+    const int L = a.L, nring = a.nring, nunits = a.nunits, nunit_all = a.nunit_all, R = a.R;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int l0 = m > 2 ? m : 2;
+    const long long mbase = (long long)m * (2 * L + 1 - m) / 2;
+    const long long tbound = (long long)(L + 1) * nunit_all;
+    const size_t row = 2 * (size_t)L + 1;
+    const long long pbound = (long long)R * nring * row;
+    (void)pbound;
+
+    // this thread's ring pair (row tid of every A tile)
+    const int iu = chunk * TC_NT + tid;
+    int uid1[1] = {iu < nunits ? (a.units ? a.units[AKRA_IX(iu, nunits, kDbgUnits)] : iu) : -1};
+    int gs1[1] = {kNeverLive};
+    float2 X2 = make_float2(0.f, 0.f);
+    float2 V[1] = {make_float2(0.f, 0.f)}, VO[1] = {make_float2(0.f, 0.f)};
+    int e1[1] = {0};
+    if (uid1[0] >= 0) {
+        const float x = (float)a.uinfo[AKRA_IX(uid1[0], nunit_all, kDbgUnitInfo)].x;
+        X2 = make_float2(x, x);
+        gs1[0] = a.start[AKRA_IX((size_t)m * nunit_all + uid1[0], tbound, kDbgStart)].x;
+    }
+    const int warp_first = __reduce_min_sync(0xffffffffu, gs1[0]);
+    const int l_first = block_min_start<TC_NT>(gs1[0]);
+
+    float dv[2][2][4];   // D of this row: [spin][parity][c.re, c.im, d.re, d.im], per RHS below
+    if (l_first <= L) {
+        if (warp == 0) tc::tmem_alloc(&s_tmem, S::NCOL);
+        if (tid == 0) {
+            tc::mbar_init(&s_mbar[0], 1);
+            tc::mbar_init(&s_mbar[1], 1);
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+        tc::fence_before();
+        __syncthreads();
+        tc::fence_after();
+    }
+    const bool active = l_first <= L;
+    const uint32_t tmem = active ? s_tmem : 0u;
+    bool ok = true;
+    const int T = active ? (L - l_first) / TCT + 1 : 0;
+    float4 *cf_all = reinterpret_cast<float4 *>(smem + 2 * S::BUF);
+    if (active) {
+        tc_stage<RG>(a, m, mbase, r0, l_first, smem, cf_all);
+        __syncthreads();
+    }
+    const uint32_t idesc = tc::idesc_tf32(128, N);
+    for (int t = 0; t < T; t++) {
+        const int lt = l_first + t * TCT, b = t & 1;
+        unsigned char *buf = smem + b * S::BUF;
+        const float4 *cf = cf_all + b * TCT;
+        f2_start_pairs<1>(a.seeds, a.start, (size_t)m * nunit_all, tbound, lt, uid1, gs1, V, VO, e1);
+        if (warp_first > lt + TCT - 1) {
+            // none of this warp's pairs has started: zero rows
+            const float2 z[8] = {};
+            tc_store_half(buf, tid, 0, z);
+            tc_store_half(buf, tid, 1, z);
+        } else {
+            const bool all_live = __all_sync(0xffffffffu, e1[0] == 0);
+#pragma unroll
+            for (int half = 0; half < 2; half++) {
+                float2 lam[8];
+#pragma unroll
+                for (int j = 0; j < 8; j++) {
+                    const int i = half * 8 + j;
+                    const float2 cur = (i & 1) == 0 ? V[0] : VO[0];
+                    lam[j] = (!all_live && e1[0] != 0) ? make_float2(0.f, 0.f) : cur;
+                    const float4 c4 = cf[i];
+                    const float2 tt = f2fma(make_float2(c4.x, c4.y), X2, make_float2(c4.z, c4.w));
+                    if ((i & 1) == 0) {
+                        VO[0] = f2fma(tt, V[0], VO[0]);
+                        if (!all_live) f2_rescale<1>(0, V, VO, e1, VO[0]);
+                    } else {
+                        V[0] = f2fma(tt, VO[0], V[0]);
+                        if (!all_live) f2_rescale<1>(0, V, VO, e1, V[0]);
+                    }
+                }
+                tc_store_half(buf, tid, half, lam);
+            }
+        }
+        if (t + 1 < T) {
+            // the other buffer is free once the MMAs of tile t-1 have completed
+            if (t >= 1) ok &= tc::mbar_wait(&s_mbar[(t + 1) & 1], ((t - 1) >> 1) & 1, kWaitLimit);
+            tc_stage<RG>(a, m, mbase, r0, lt + TCT, smem + ((t + 1) & 1) * S::BUF, cf_all + ((t + 1) & 1) * TCT);
+        }
+        tc::fence_async_smem();
+        tc::fence_before();
+        __syncthreads();
+        tc::fence_after();
+        if (tid == 0) {
+#pragma unroll
+            for (int s = 0; s < 2; s++)
+#pragma unroll
+                for (int p = 0; p < 2; p++) {
+                    const uint32_t d = tmem + (uint32_t)((s * 2 + p) * N);
+                    const uint64_t ah = tc::sdesc(tc::smem_u32(tc_a(buf, s, p, 0)));
+                    const uint64_t al = tc::sdesc(tc::smem_u32(tc_a(buf, s, p, 1)));
+                    const uint64_t bh = tc::sdesc(tc::smem_u32(tc_b<RG>(buf, p, 0)));
+                    const uint64_t bl = tc::sdesc(tc::smem_u32(tc_b<RG>(buf, p, 1)));
+                    tc::mma_tf32(d, ah, bh, idesc, t > 0 ? 1u : 0u);
+                    tc::mma_tf32(d, ah, bl, idesc, 1u);
+                    tc::mma_tf32(d, al, bh, idesc, 1u);
+                }
+            tc::commit(&s_mbar[b]);
+        }
+    }
+    if (active) {
+        ok &= tc::mbar_wait(&s_mbar[(T - 1) & 1], ((T - 1) >> 1) & 1, kWaitLimit);
+        tc::fence_after();
+        if (!ok && a.err) atomicExch(a.err, 1);
+    }
+
+    // Φ(±m) of both rings of this row's pair, per RHS
+    const bool swap = ((l0 + m) & 1) != 0;
+    UnitInfo ui;
+    ui.ring_n = ui.ring_s = -1;
+    if (uid1[0] >= 0) ui = a.uinfo[AKRA_IX(uid1[0], nunit_all, kDbgUnitInfo)];
+    for (int rr = 0; rr < RG; rr++) {
+        const int r = r0 + rr;
+        if (active) {
+#pragma unroll
+            for (int s = 0; s < 2; s++)
+#pragma unroll
+                for (int p = 0; p < 2; p++)
+                    tc::tmem_ld4(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)((s * 2 + p) * N + 4 * rr), dv[s][p]);
+        } else {
+#pragma unroll
+            for (int s = 0; s < 2; s++)
+#pragma unroll
+                for (int p = 0; p < 2; p++)
+#pragma unroll
+                    for (int c = 0; c < 4; c++) dv[s][p][c] = 0.f;
+        }
+        if (uid1[0] < 0 || r >= R) continue;
+        // per parity: [0] Σcλ+ re, [1] Σcλ+ im, [2] Σdλ- re, [3] Σdλ- im,
+        //             [4] Σcλ- re, [5] Σcλ- im, [6] Σdλ+ re, [7] Σdλ+ im
+        float se[8], so[8];
+#pragma unroll
+        for (int p = 0; p < 2; p++) {
+            float *dst = ((p == 0) != swap) ? se : so;
+            dst[0] = dv[0][p][0];
+            dst[1] = dv[0][p][1];
+            dst[2] = dv[1][p][2];
+            dst[3] = dv[1][p][3];
+            dst[4] = dv[1][p][0];
+            dst[5] = dv[1][p][1];
+            dst[6] = dv[0][p][2];
+            dst[7] = dv[0][p][3];
+        }
+#pragma unroll
+        for (int side = 0; side < 2; side++) {
+            const int ring = side == 0 ? ui.ring_n : ui.ring_s;
+            if (ring < 0) continue;
+            if (a.ring_active && !a.ring_active[AKRA_IX(ring, nring, kDbgRingActive)]) continue;
+            const int o = side == 0 ? 0 : 4;
+            const float sg = side == 0 ? 1.f : -1.f;
+            const float fr = se[o + 0] + sg * so[o + 0], fi = se[o + 1] + sg * so[o + 1];
+            const float gr = se[o + 2] + sg * so[o + 2], gi = se[o + 3] + sg * so[o + 3];
+            const size_t pb = ((size_t)r * nring + ring) * row + L;   // Φ(ring, m = 0)
+            a.phi[AKRA_IX(pb + m, pbound, kDbgPhiWrite)] = make_float2(fr, fi);
+            if (m > 0) a.phi[AKRA_IX(pb - m, pbound, kDbgPhiWrite)] = make_float2(gr, -gi);
+        }
+    }
+    if (active) {
+        tc::fence_before();
+        __syncthreads();
+        tc::fence_after();
+        if (warp == 0) tc::tmem_dealloc(tmem, S::NCOL);
+    }
+}
+
+template <int RG>
+static akra_status launch_synth_tc(akra_plan p, LegMode mode, const void *alm, void *phi, int R,
+                                   const int *units, int nunits, cudaStream_t st)
+{
+    LegArgs<float> a = leg_args<float>(p, LegShape{1, TC_NT, RG}, mode, units, nunits, R);
+    a.alm = (const float2 *)alm;
+    a.phi = (float2 *)phi;
+    a.err = p->d_tc_err;
+    dim3 grid((unsigned)(p->lmax + 1) * a.nchunks, (R + RG - 1) / RG);
+    k_leg_synth_tc<RG><<<grid, TC_NT, TcSynth<RG>::SMEM, st>>>(a);
+    AKRA_CUDA_TRY(cudaGetLastError());
+    p->launches++;
+    return AKRA_OK;
+}
+
+// the shared-memory opt-in of the tensor-core kernels (at plan creation, never inside a capture)
+akra_status legendre_tc_prepare()
+{
+    AKRA_CUDA_TRY(cudaFuncSetAttribute(k_leg_synth_tc<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcSynth<4>::SMEM));
+    AKRA_CUDA_TRY(cudaFuncSetAttribute(k_leg_synth_tc<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcSynth<8>::SMEM));
+    AKRA_CUDA_TRY(cudaFuncSetAttribute(k_leg_synth_tc<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcSynth<16>::SMEM));
+    AKRA_CUDA_TRY(cudaFuncSetAttribute(k_leg_synth_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcSynth<32>::SMEM));
+    return AKRA_OK;
+}
+
+// FP32 synthesis with the tensor-core contraction, RHS in groups of tcg (4, 8, 16 or 32)
+akra_status legendre_synth_tc(akra_plan p, int tcg, LegMode mode, const void *alm, void *phi, int R,
+                              const int *units, int nunits, cudaStream_t st)
+{
+    if (nunits <= 0) return AKRA_OK;
+    switch (tcg) {
+    case 4: return launch_synth_tc<4>(p, mode, alm, phi, R, units, nunits, st);
+    case 8: return launch_synth_tc<8>(p, mode, alm, phi, R, units, nunits, st);
+    case 16: return launch_synth_tc<16>(p, mode, alm, phi, R, units, nunits, st);
+    case 32: return launch_synth_tc<32>(p, mode, alm, phi, R, units, nunits, st);
+    default:
+        set_error("no tensor-core synthesis for an RHS group of %d", tcg);
+        return AKRA_EINVAL;
+    }
+}
+
+AKRA_DEBUG_COLLECTOR(legendre_tc)
+
+}  // namespace akra

@@ -343,6 +343,18 @@ akra_status ws_reserve(akra_plan p, Workspace &w, size_t bytes)
     return AKRA_OK;
 }
 
+akra_status tc_error_check(akra_plan p)
+{
+    if (!p->d_tc_err) return AKRA_OK;
+    int h = 0;
+    AKRA_CUDA_TRY(cudaMemcpy(&h, p->d_tc_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (!h) return AKRA_OK;
+    AKRA_CUDA_TRY(cudaMemset(p->d_tc_err, 0, sizeof(int)));
+    set_error("a tensor-core completion wait of the FP32 synthesis ran out of its bound: the FP32 "
+              "operator results since the last blocking call are invalid");
+    return AKRA_ECUDA;
+}
+
 size_t plan_device_bytes(akra_plan p)
 {
     return p->bytes_tables + p->phi.bytes + p->partial.bytes + p->cg.bytes + p->red.bytes +
@@ -484,6 +496,8 @@ static akra_status plan_build(akra_plan p)
     AKRA_TRY(dev_alloc(p, &p->d_W32r, sizeof(float) * p->npix));
     AKRA_TRY(dev_alloc(p, &p->d_pw64, sizeof(double) * p->ntri));
     AKRA_TRY(dev_alloc(p, &p->d_pw32, sizeof(float) * p->ntri));
+    AKRA_TRY(dev_alloc(p, &p->d_tc_err, sizeof(int)));
+    AKRA_CUDA_TRY(cudaMemset(p->d_tc_err, 0, sizeof(int)));
 
     std::vector<FftFactors> fac(N + 1);
     for (int i = 1; i <= N; i++) fac[i] = factorize(4 * i);
@@ -515,6 +529,7 @@ static akra_status plan_build(akra_plan p)
     AKRA_CUDA_TRY(cudaMemset(p->d_ring_active, 1, p->nring));
     AKRA_TRY(ring_fft_prepare(p));
     AKRA_TRY(ring_fft32_build(p));
+    AKRA_TRY(legendre_tc_prepare());
     AKRA_CUDA_TRY(cudaStreamCreateWithFlags(&p->stream, cudaStreamNonBlocking));
     AKRA_CUDA_TRY(cudaEventCreateWithFlags(&p->ev_a, cudaEventDisableTiming));
     AKRA_CUDA_TRY(cudaEventCreateWithFlags(&p->ev_b, cudaEventDisableTiming));
@@ -574,7 +589,7 @@ extern "C" void akra_plan_destroy(akra_plan p)
                     p->d_fft32_off, p->d_fft32_tw2, p->d_fft32_bhat, p->d_seed32, p->d_seed64,
                     p->d_start32, p->d_start64, p->d_steps, p->d_pw64, p->d_pw32, p->d_ftw64,
                     p->d_ftw32, p->d_fWt64, p->d_fWt32,
-                    p->d_fft32_rings_all, p->d_fft32_rings_act};
+                    p->d_fft32_rings_all, p->d_fft32_rings_act, p->d_tc_err};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     if (p->stream) cudaStreamDestroy(p->stream);
@@ -594,6 +609,7 @@ extern "C" akra_status akra_debug_violations(long long *count, int *site, long l
     DebugRecord acc{};
     AKRA_CUDA_TRY(cudaDeviceSynchronize());
     AKRA_TRY(debug_collect_legendre(&acc));
+    AKRA_TRY(debug_collect_legendre_tc(&acc));
     AKRA_TRY(debug_collect_batch(&acc));
     AKRA_TRY(debug_collect_ringfft(&acc));
     AKRA_TRY(debug_collect_ringfft32(&acc));
@@ -874,19 +890,43 @@ static akra_status tune_one(akra_plan p, akra_prec prec, int R, cudaStream_t st)
             }
         }
     }
+    // FP32: the tensor-core synthesis for every RHS group that R fills at least half
+    std::vector<int> tcs;
+    if (std::is_same<T, float>::value)
+        for (int g : {4, 8, 16, 32})
+            if (g == 4 || R > g / 2) tcs.push_back(g);
+    std::vector<float> ttc(tcs.size(), 0.f);
+    for (size_t q = 0; q < tcs.size() && s == AKRA_OK; q++) {
+        for (int rep = 0; rep < 3 && s == AKRA_OK; rep++) {
+            cudaEventRecord(e0, st);
+            s = legendre_synth_tc(p, tcs[q], LegMode::KS, alm, p->phi.ptr, R, units, nunits, st);
+            cudaEventRecord(e1, st);
+            cudaEventSynchronize(e1);
+            float m1 = 0;
+            cudaEventElapsedTime(&m1, e0, e1);
+            if (rep > 0) ttc[q] += m1;
+        }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaEventDestroy(e2);
     cudaFree(alm);
     if (s != AKRA_OK) return s;
+    AKRA_TRY(tc_error_check(p));
     LegShape pick = cands.back();
     float best = 1e30f;
-    for (size_t k = 0; k < cands.size(); k++)        // synthesis shape k ...
-        for (size_t j = 0; j < cands.size(); j++) {  // ... with adjoint shape j of the same RG
+    for (size_t j = 0; j < cands.size(); j++) {      // adjoint shape j ...
+        for (size_t k = 0; k < cands.size(); k++) {  // ... with a CUDA-core synthesis of the same RG
             if (cands[j].RG != cands[k].RG || ts[k] + ta[j] >= best) continue;
             best = ts[k] + ta[j];
             pick = LegShape{cands[k].P, cands[k].NT, cands[k].RG, cands[j].P};
         }
+        for (size_t q = 0; q < tcs.size(); q++) {    // ... or with the tensor-core synthesis
+            if (ttc[q] + ta[j] >= best) continue;
+            best = ttc[q] + ta[j];
+            pick = LegShape{cands[j].P, cands[j].NT, cands[j].RG, cands[j].P, tcs[q]};
+        }
+    }
     p->shapes[(long long)prec * 1000 + (R > 999 ? 999 : R)] = pick;
     p->ws_gen++;   // captured CG iterations used the previous shape
     return AKRA_OK;
@@ -937,6 +977,31 @@ extern "C" akra_status akra_plan_set_shape(akra_plan p, akra_prec prec, int R, i
     }
     p->shapes[(long long)prec * 1000 + (R > 999 ? 999 : R)] = LegShape{P, 128, RG, PA};
     p->ws_gen++;   // captured CG iterations used the previous shape
+    return AKRA_OK;
+}
+
+extern "C" akra_status akra_plan_set_tc_synthesis(akra_plan p, int R, int group)
+{
+    AKRA_TRY(reject_flat(p, "akra_plan_set_tc_synthesis"));
+    if (!p || R < 1 || R > 65535 || !(group == 0 || group == 4 || group == 8 || group == 16 || group == 32)) {
+        set_error("akra_plan_set_tc_synthesis: invalid argument (group must be 0, 4, 8, 16 or 32)");
+        return AKRA_EINVAL;
+    }
+    LegShape s = leg_shape(p, AKRA_F32, R);
+    s.TC = group;
+    p->shapes[(long long)AKRA_F32 * 1000 + (R > 999 ? 999 : R)] = s;
+    p->ws_gen++;   // captured CG iterations used the previous shape
+    return AKRA_OK;
+}
+
+extern "C" akra_status akra_plan_get_tc_synthesis(akra_plan p, int R, int *group)
+{
+    AKRA_TRY(reject_flat(p, "akra_plan_get_tc_synthesis"));
+    if (!p || !group || R < 1) {
+        set_error("akra_plan_get_tc_synthesis: invalid argument");
+        return AKRA_EINVAL;
+    }
+    *group = leg_shape(p, AKRA_F32, R).TC;
     return AKRA_OK;
 }
 
@@ -1025,6 +1090,7 @@ extern "C" akra_status akra_time_H_stages(akra_plan p, akra_prec prec, int R, in
         return AKRA_ENOWEIGHTS;
     }
     cudaStream_t st = (cudaStream_t)stream;
-    return prec == AKRA_F64 ? time_stages<double>(p, R, reps, st, ms_out)
-                            : time_stages<float>(p, R, reps, st, ms_out);
+    AKRA_TRY(prec == AKRA_F64 ? time_stages<double>(p, R, reps, st, ms_out)
+                              : time_stages<float>(p, R, reps, st, ms_out));
+    return tc_error_check(p);
 }
