@@ -274,7 +274,8 @@ def config2_block(A, dev):
 def batch_uneven_block(A, dev):
     """BASELINE config 4: 32 RHS at Nside 1024 / lmax 2048, 16 at 512 / 1024, 16 at 256 / 512
     (DES-like footprints, per-pixel Gaussian shape-noise realisations) in one batched mixed solve
-    with persistent work-queue Legendre launches; tile shape autotuned."""
+    with persistent work-queue Legendre launches; tile shape and the tensor-core synthesis group
+    autotuned."""
     import torch
 
     import synthetic as S
@@ -300,7 +301,8 @@ def batch_uneven_block(A, dev):
            "solve_s": t_b, "s_per_rhs": t_b / nrhs,
            "inner_iters": [i["iters"] for i in binfos], "outer": [i["outer"] for i in binfos],
            "max_relres": max(max(i["relres_rhs"]) for i in binfos),
-           "status": max(i["status"] for i in binfos), "tile": A.akra_batch_describe(bt)}
+           "status": max(i["status"] for i in binfos), "tile": A.akra_batch_describe(bt),
+           "tc_synthesis_group": A.akra_batch_get_tc_synthesis(bt)}
     del bt
     for pb in bplans:
         A.akra_plan_destroy(pb)

@@ -270,6 +270,17 @@ akra_status akra_batch_cg_solve(akra_batch batch, akra_prec prec, const void *co
 /* Current tile shape (ring pairs per thread, RHS per block) and batched launches so far. */
 akra_status akra_batch_describe(akra_batch batch, int *P, int *RG, long long *launches);
 
+/* Run the batch's FP32 Legendre synthesis on the tensor cores (as akra_plan_set_tc_synthesis
+ * does for one plan): group = 4, 8, 16 or 32 RHS per work item, 0 for the CUDA-core synthesis.
+ * The tensor-core items are (instance, m, 128-ring-pair chunk, RHS group), heaviest first; the
+ * adjoint keeps the CUDA-core items.  akra_batch_autotune considers every group up to twice the
+ * largest R (from R = 4 on).  A tensor-core completion wait that exceeds its bound is reported as
+ * ECUDA by the next akra_batch_cg_solve or akra_batch_autotune.  Blocking (rebuilds the work
+ * list).  Errors: EINVAL, ENOMEM. */
+akra_status akra_batch_set_tc_synthesis(akra_batch batch, int group);
+/* The batch's tensor-core synthesis group (0: CUDA-core synthesis).  Errors: EINVAL. */
+akra_status akra_batch_get_tc_synthesis(akra_batch batch, int *group);
+
 /* Preconditioner of the plan's CG solves.  AKRA_PRECOND_SCALAR (default): the paper's scalar
  * P = (mean_all(M N^-1) + λ_eff)^-1 of Eq. 15 (for a scalar P the PCG iterates equal the CG
  * ones).  AKRA_PRECOND_PER_L: the per-l diagonal (mean_all(M N^-1) D_l^2 + λ_eff)^-1, the

@@ -56,7 +56,8 @@ EXPORTS = ["akra_plan_create", "akra_plan_destroy", "akra_last_error", "akra_ver
            "akra_plan_get_shape", "akra_plan_set_shape", "akra_set_mixed_policy", "akra_fma_rate",
            "akra_cg_solve_fields", "akra_shuffle_shear", "akra_cl_spectra",
            "akra_plan_set_preconditioner", "akra_flat_plan_create", "akra_plan_fill_workspaces",
-           "akra_debug_violations", "akra_plan_set_tc_synthesis", "akra_plan_get_tc_synthesis"]
+           "akra_debug_violations", "akra_plan_set_tc_synthesis", "akra_plan_get_tc_synthesis",
+           "akra_batch_set_tc_synthesis", "akra_batch_get_tc_synthesis"]
 
 _lib_handle = None
 
@@ -109,6 +110,8 @@ def load(build_if_missing: bool = False):
         "akra_plan_set_shape": ([vp, i, i, i, i, i], i),
         "akra_plan_set_tc_synthesis": ([vp, i, i], i),
         "akra_plan_get_tc_synthesis": ([vp, i, ctypes.POINTER(i)], i),
+        "akra_batch_set_tc_synthesis": ([vp, i], i),
+        "akra_batch_get_tc_synthesis": ([vp, ctypes.POINTER(i)], i),
         "akra_time_H_stages": ([vp, i, i, i, vp, ctypes.POINTER(ctypes.c_double)], i),
         "akra_synth_spin2_static": ([vp, i, vp, vp, i, vp], i),
         "akra_cg_solve_adjoint": ([vp, i, vp, vp, i, d, i, ctypes.POINTER(CgInfo), vp], i),
@@ -516,6 +519,18 @@ def akra_batch_describe(batch: Batch) -> dict:
     P, RG, nl = ctypes.c_int(), ctypes.c_int(), ctypes.c_longlong()
     _check(load().akra_batch_describe(batch.handle, ctypes.byref(P), ctypes.byref(RG), ctypes.byref(nl)))
     return {"P": P.value, "RG": RG.value, "launches": nl.value}
+
+
+def akra_batch_set_tc_synthesis(batch: Batch, group: int):
+    """The batch's FP32 synthesis on the tensor core with RHS groups of `group` (4, 8, 16, 32), or
+    on the CUDA cores (group 0)."""
+    _check(load().akra_batch_set_tc_synthesis(batch.handle, group))
+
+
+def akra_batch_get_tc_synthesis(batch: Batch) -> int:
+    g = ctypes.c_int()
+    _check(load().akra_batch_get_tc_synthesis(batch.handle, ctypes.byref(g)))
+    return g.value
 
 
 def akra_batch_apply_H(batch: Batch, xs, out=None, stream=None):

@@ -3,7 +3,8 @@
 // the work items of all instances (a queue of (instance, m, chunk, RHS group) items ordered
 // by cost, heaviest first), one ring-FFT launch over all instances' rings, one persistent
 // Legendre-adjoint launch, then each instance's epilogue and CG vector kernels -- all in one
-// CUDA graph per iteration.  The FP64 outer refinement of the mixed-precision form runs per
+// CUDA graph per iteration.  The synthesis can instead run on the tensor cores (its own queue of
+// (instance, m, 128-pair chunk, RHS group) items; the adjoint keeps the CUDA-core items).  The FP64 outer refinement of the mixed-precision form runs per
 // instance between inner solves.  (Motivated by the paper's noise realisations and
 // tomographic bins, Sec. III; the batching itself is not in the paper.)
 #include <algorithm>
@@ -25,7 +26,11 @@ struct akra_batch_s {
     akra::Fft32Args *d_fft = nullptr;
     int4 *d_items = nullptr, *d_fitems = nullptr;
     int nitems = 0, nfitems = 0;
-    int *d_counter = nullptr;
+    int *d_counter = nullptr;             // queue heads: synthesis, adjoint, tensor-core synthesis
+    int tcg = 0;                          // tensor-core synthesis RHS group (0: CUDA-core synthesis)
+    akra::LegArgs<float> *d_syn_tc = nullptr;
+    int4 *d_titems = nullptr;
+    int ntitems = 0, titems_tcg = 0;
     int fft_mmax = 0;
     size_t fft_smem_set = 48 * 1024;     // dynamic shared memory the FFT kernel is cleared for
     akra::LegShape items_shape{0, 0, 0};
@@ -34,6 +39,7 @@ struct akra_batch_s {
     std::vector<unsigned> graph_gens;
     long long graph_kernels = 0;
     akra::LegShape graph_shape{0, 0, 0};
+    int graph_tcg = 0;
     int *h_flags = nullptr;               // pinned: one done flag per instance
     long long launches = 0;
 };
@@ -96,10 +102,44 @@ static akra_status batch_items(akra_batch b)
     return AKRA_OK;
 }
 
+// (re)build the tensor-core synthesis items: (instance, m, 128-pair chunk, RHS group), heaviest first
+static akra_status batch_titems(akra_batch b)
+{
+    if (b->tcg == 0 || (b->d_titems && b->titems_tcg == b->tcg)) return AKRA_OK;
+    struct It { long long cost; int4 v; };
+    std::vector<It> items;
+    for (int i = 0; i < b->ninst; i++) {
+        akra_plan p = b->plans[i];
+        const int nu = p->n_active_units;
+        const int nch = (nu + TC_NT - 1) / TC_NT, ng = (b->R[i] + b->tcg - 1) / b->tcg;
+        for (int m = 0; m <= p->lmax; m++)
+            for (int c = 0; c < nch; c++)
+                for (int g = 0; g < ng; g++) {
+                    const long long steps = p->lmax - std::max(m, 2) + 1;
+                    items.push_back({steps * std::min(TC_NT, nu - c * TC_NT), make_int4(i, m, c, g)});
+                }
+    }
+    std::stable_sort(items.begin(), items.end(), [](const It &a, const It &c) { return a.cost > c.cost; });
+    std::vector<int4> hv(items.size());
+    for (size_t k = 0; k < items.size(); k++) hv[k] = items[k].v;
+    if (b->d_titems) cudaFree(b->d_titems);
+    b->d_titems = nullptr;
+    if (cudaMalloc(&b->d_titems, sizeof(int4) * std::max<size_t>(hv.size(), 1)) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("akra_batch: work-list allocation failed");
+        return AKRA_ENOMEM;
+    }
+    AKRA_CUDA_TRY(cudaMemcpy(b->d_titems, hv.data(), sizeof(int4) * hv.size(), cudaMemcpyHostToDevice));
+    b->ntitems = (int)hv.size();
+    b->titems_tcg = b->tcg;
+    return AKRA_OK;
+}
+
 // FP32 workspaces of every instance for the batch shape, and FP64 ones for the outer residual
 static akra_status batch_reserve(akra_batch b)
 {
     AKRA_TRY(batch_items(b));
+    AKRA_TRY(batch_titems(b));
     for (int i = 0; i < b->ninst; i++) {
         akra_plan p = b->plans[i];
         const int R = b->R[i];
@@ -119,7 +159,7 @@ static akra_status batch_reserve(akra_batch b)
 static akra_status batch_args(akra_batch b, void *const *x, void *const *y, const int *const *skips,
                               cudaStream_t st)
 {
-    std::vector<LegArgs<float>> syn(b->ninst), adj(b->ninst);
+    std::vector<LegArgs<float>> syn(b->ninst), adj(b->ninst), syn_tc(b->ninst);
     std::vector<Fft32Args> fft(b->ninst);
     for (int i = 0; i < b->ninst; i++) {
         akra_plan p = b->plans[i];
@@ -128,6 +168,11 @@ static akra_status batch_args(akra_batch b, void *const *x, void *const *y, cons
         syn[i].alm = (const float2 *)x[i];
         syn[i].phi = (float2 *)p->phi.ptr;
         syn[i].skip = sk;
+        syn_tc[i] = leg_args<float>(p, LegShape{1, TC_NT, b->tcg > 0 ? b->tcg : 4}, LegMode::KS,
+                                    p->d_active_units, p->n_active_units, b->R[i]);
+        syn_tc[i].alm = syn[i].alm;
+        syn_tc[i].phi = syn[i].phi;
+        syn_tc[i].skip = sk;
         adj[i] = syn[i];
         adj[i].phi_in = (const float2 *)p->phi.ptr;
         adj[i].partial = (float *)p->partial.ptr;
@@ -139,6 +184,8 @@ static akra_status batch_args(akra_batch b, void *const *x, void *const *y, cons
     AKRA_CUDA_TRY(cudaMemcpyAsync(b->d_syn, syn.data(), sizeof(LegArgs<float>) * b->ninst, cudaMemcpyHostToDevice, st));
     AKRA_CUDA_TRY(cudaMemcpyAsync(b->d_adj, adj.data(), sizeof(LegArgs<float>) * b->ninst, cudaMemcpyHostToDevice, st));
     AKRA_CUDA_TRY(cudaMemcpyAsync(b->d_fft, fft.data(), sizeof(Fft32Args) * b->ninst, cudaMemcpyHostToDevice, st));
+    AKRA_CUDA_TRY(cudaMemcpyAsync(b->d_syn_tc, syn_tc.data(), sizeof(LegArgs<float>) * b->ninst,
+                                  cudaMemcpyHostToDevice, st));
     // the pageable sources must stay alive until the copies have been staged
     AKRA_CUDA_TRY(cudaStreamSynchronize(st));
     return AKRA_OK;
@@ -179,8 +226,15 @@ static akra_status launch_queue(akra_batch b, int which, cudaStream_t st)
 static akra_status batch_H32(akra_batch b, void *const *x, void *const *y, const int *const *skips,
                              cudaStream_t st)
 {
-    AKRA_CUDA_TRY(cudaMemsetAsync(b->d_counter, 0, 2 * sizeof(int), st));
-    AKRA_TRY(launch_queue(b, 0, st));
+    AKRA_CUDA_TRY(cudaMemsetAsync(b->d_counter, 0, 3 * sizeof(int), st));
+    if (b->tcg > 0) {
+        if (b->ntitems > 0) {
+            AKRA_TRY(legendre_synth_tc_queue(b->tcg, b->d_syn_tc, b->d_titems, b->ntitems, b->d_counter + 2, st));
+            b->launches++;
+        }
+    } else {
+        AKRA_TRY(launch_queue(b, 0, st));
+    }
     const size_t smem = (size_t)(f32_slots(b->fft_mmax) + F32_NT) * sizeof(float2);
     if (smem > b->fft_smem_set) {
         // the attribute belongs to this translation unit's instance of the kernel
@@ -209,7 +263,7 @@ static bool graph_valid(akra_batch b)
 {
     if (!b->graph) return false;
     const LegShape s = b->shape, g = b->graph_shape;
-    if (s.P != g.P || s.RG != g.RG || s.NT != g.NT) return false;
+    if (s.P != g.P || s.RG != g.RG || s.NT != g.NT || b->tcg != b->graph_tcg) return false;
     for (int i = 0; i < b->ninst; i++)
         if (b->graph_gens[i] != b->plans[i]->ws_gen) return false;
     return true;
@@ -254,6 +308,7 @@ static akra_status batch_graph(akra_batch b, std::vector<CgBufs> &cb)
     cudaGraphDestroy(graph);
     AKRA_CUDA_TRY(e2);
     b->graph_shape = b->shape;
+    b->graph_tcg = b->tcg;
     b->graph_gens.resize(b->ninst);
     for (int i = 0; i < b->ninst; i++) b->graph_gens[i] = b->plans[i]->ws_gen;
     return AKRA_OK;
@@ -346,7 +401,8 @@ extern "C" akra_status akra_batch_create(int ninst, const akra_plan *plans, cons
               cudaMalloc(&b->d_syn, sizeof(LegArgs<float>) * ninst) == cudaSuccess &&
               cudaMalloc(&b->d_adj, sizeof(LegArgs<float>) * ninst) == cudaSuccess &&
               cudaMalloc(&b->d_fft, sizeof(Fft32Args) * ninst) == cudaSuccess &&
-              cudaMalloc(&b->d_counter, 2 * sizeof(int)) == cudaSuccess &&
+              cudaMalloc(&b->d_syn_tc, sizeof(LegArgs<float>) * ninst) == cudaSuccess &&
+              cudaMalloc(&b->d_counter, 3 * sizeof(int)) == cudaSuccess &&
               cudaMallocHost(&b->h_flags, sizeof(int) * ninst) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
@@ -363,7 +419,7 @@ extern "C" void akra_batch_destroy(akra_batch b)
     if (!b) return;
     if (b->stream) cudaStreamSynchronize(b->stream);
     if (b->graph) cudaGraphExecDestroy(b->graph);
-    void *ptrs[] = {b->d_syn, b->d_adj, b->d_fft, b->d_items, b->d_fitems, b->d_counter};
+    void *ptrs[] = {b->d_syn, b->d_adj, b->d_fft, b->d_items, b->d_fitems, b->d_counter, b->d_syn_tc, b->d_titems};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     if (b->h_flags) cudaFreeHost(b->h_flags);
@@ -433,6 +489,8 @@ extern "C" akra_status akra_batch_autotune(akra_batch b, void *stream)
     cudaEventCreate(&e1);
     float best = 1e30f;
     LegShape pick = b->shape;
+    int pick_tcg = b->tcg;
+    b->tcg = 0;
     akra_status s = AKRA_OK;
     for (auto &c : cands) {
         if (c.RG > maxR && c.RG > 1) continue;
@@ -453,6 +511,30 @@ extern "C" akra_status akra_batch_autotune(akra_batch b, void *stream)
         if (tot < best) {
             best = tot;
             pick = c;
+            pick_tcg = b->tcg;
+        }
+    }
+    // then the tensor-core synthesis at the best shape, for groups not more than twice the
+    // largest RHS count
+    b->shape = pick;
+    for (int g : {4, 8, 16, 32}) {
+        if (s != AKRA_OK || g > 2 * maxR || maxR < 4) break;
+        b->tcg = g;
+        s = batch_reserve(b);
+        if (s == AKRA_OK) s = batch_args(b, xs.data(), ys.data(), nullptr, user);
+        float tot = 0;
+        for (int rep = 0; rep < 3 && s == AKRA_OK; rep++) {
+            cudaEventRecord(e0, user);
+            s = batch_H32(b, xs.data(), ys.data(), nullptr, user);
+            cudaEventRecord(e1, user);
+            cudaEventSynchronize(e1);
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0) tot += ms;
+        }
+        if (s == AKRA_OK && tot < best) {
+            best = tot;
+            pick_tcg = g;
         }
     }
     cudaEventDestroy(e0);
@@ -461,8 +543,30 @@ extern "C" akra_status akra_batch_autotune(akra_batch b, void *stream)
     for (void *q : xs) cudaFree(q);
     for (void *q : ys) cudaFree(q);
     b->shape = pick;
+    b->tcg = pick_tcg;
     if (s != AKRA_OK) return s;
+    for (int i = 0; i < b->ninst; i++) AKRA_TRY(tc_error_check(b->plans[i]));
     return batch_reserve(b);
+}
+
+extern "C" akra_status akra_batch_set_tc_synthesis(akra_batch b, int group)
+{
+    if (!b || (group != 0 && group != 4 && group != 8 && group != 16 && group != 32)) {
+        set_error("akra_batch_set_tc_synthesis: invalid argument (group 0, 4, 8, 16 or 32)");
+        return AKRA_EINVAL;
+    }
+    b->tcg = group;
+    return batch_reserve(b);
+}
+
+extern "C" akra_status akra_batch_get_tc_synthesis(akra_batch b, int *group)
+{
+    if (!b || !group) {
+        set_error("akra_batch_get_tc_synthesis: invalid argument");
+        return AKRA_EINVAL;
+    }
+    *group = b->tcg;
+    return AKRA_OK;
 }
 
 extern "C" akra_status akra_batch_cg_solve(akra_batch b, akra_prec prec, const void *const *d_shear,
@@ -592,6 +696,7 @@ extern "C" akra_status akra_batch_cg_solve(akra_batch b, akra_prec prec, const v
     AKRA_TRY(leave(b, user));
     AKRA_CUDA_TRY(cudaEventRecord(b->ev, st));
     AKRA_TRY(bounded_wait(b->ev, deadline));
+    for (int i = 0; i < n; i++) AKRA_TRY(tc_error_check(b->plans[i]));
     int worst = AKRA_OK;
     for (int i = 0; i < n; i++) {
         int w = AKRA_OK;

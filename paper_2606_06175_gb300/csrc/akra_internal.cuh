@@ -110,6 +110,16 @@ template <typename T> using v4_t = typename V4t<T>::type;
 // v * 2^(Q e); a rescale by 2^-Q happens when |v| > 2^(Q/2); contributions start when e == 0
 // recurrences start at grid points l0 + kStartGrid j (a multiple of every l-tile width)
 constexpr int kStartGrid = 64;
+// FP32 ring pairs within 0.1 rad of a pole (x = cos θ >= kDiffX) run the recurrence in difference
+// form: with d_l = μ_l - μ_{l-1} and u_l = t_l - 2 = A'_l (x - 1) + (A'_l - 2) ± c'_l (all three
+// pieces small and each accurate to FP32 rounding),
+//     d_{l+1} = u_l μ_l + d_l,   μ_{l+1} = μ_l + d_{l+1}.
+// Near x = 1 the standard step rounds t_l ~ 2 to an absolute 2^-23 while the recurrence turns
+// by an angle ~θ per step, so each step's phase error is ~2^-23/θ and grows over the l-range (up
+// to ~1e-1 relative at θ ~ 1e-3, l ~ 4000); the difference form carries the small quantities
+// themselves (measured in FP32 emulation: ~1e-6 at every θ < 0.1).  Away from the poles it has
+// no advantage and costs one more operation per step, so the other pairs keep the standard form.
+constexpr double kDiffX = 0.99500416527802582;   // cos(0.1)
 constexpr int kNeverLive = 0x7fffffff;   // start index of a pair whose harmonics stay negligible
 
 template <typename T> struct Scale;
@@ -144,9 +154,15 @@ struct UnitInfo {          // one north/south ring pair (or the equator ring alo
 };
 
 constexpr int kMaxFactors = 16;
+// FP64 ring FFT: a prime factor >= kBluePrime is transformed by Bluestein's chirp-z form (a
+// convolution of power-of-two length, O(p log p)) instead of a direct O(p^2) pass
+constexpr int kBluePrime = 67;
 struct FftFactors {
     int nf;
-    int f[kMaxFactors];    // radices, generic (>7) primes first
+    int f[kMaxFactors];    // mixed-radix passes: odd primes below kBluePrime, then 4s and a 2
+    int blue_p;            // a prime factor >= kBluePrime, transformed last by Bluestein (0: none)
+    int blue_M;            // its convolution length (a power of two >= 2 blue_p - 1)
+    long long blue_off;    // its tables in d_blue64: chirp h[p], then G+[M], G-[M]
 };
 
 constexpr int kMaxNside = 2048;
@@ -171,6 +187,7 @@ struct LegArgs {
     const UnitInfo *uinfo;
     const v4_t<T> *coef;              // recurrence coefficients
     const v4_t<T> *seeds;             // start states per (m, ring pair)
+    const float2 *dseeds;             // FP32: start differences (μ_g - μ_{g-1}) per (m, ring pair)
     const int2 *start;                // their grid points and exponent indices
     const T *fl;                      // synthesis: per-l factor (nullptr = -1)
     const cx_t<T> *alm;               // synthesis input  [R][2][ntri]
@@ -179,7 +196,7 @@ struct LegArgs {
     T *partial;                       // adjoint output   [nchunks][R][ntri][4]
     const unsigned char *ring_active; // nullptr = all rings
     const int *skip;                  // device flag: return at once if set
-    int *err;                         // device flag set when a tensor-core wait runs out (or nullptr)
+    int *err;                         // device flag set when a bounded in-kernel wait runs out
 };
 
 // arguments of one FP32 ring-FFT instance
@@ -222,6 +239,7 @@ struct akra_plan_s {
     akra::RingInfo *d_rings = nullptr;
     akra::UnitInfo *d_units = nullptr;
     akra::FftFactors *d_factors = nullptr;   // [nside + 1] by ring length index
+    double2 *d_blue64 = nullptr;             // FP64 Bluestein tables of the primes >= kBluePrime
     double4_32a *d_coef64 = nullptr;            // [ntri] {A, A B, A 2m/(l(l+1)), 0}
     float4 *d_coef32 = nullptr;
     double *d_seedC = nullptr;               // [lmax + 1] log2 seed prefactor per m
@@ -229,6 +247,8 @@ struct akra_plan_s {
     // {μ+_g, μ-_g, μ+_{g-1}, μ-_{g-1}} at the grid point g (l0 + 64 j) where the pair's
     // harmonics first exceed the precision's threshold, scaled by 2^(-Q e)
     float4 *d_seed32 = nullptr;              // [(lmax+1) nunit]
+    float2 *d_dseed32 = nullptr;             // [(lmax+1) nunit] {μ+_g - μ+_{g-1}, μ-_g - μ-_{g-1}}, scaled as
+                                             // d_seed32 (start of the FP32 difference form)
     double4_32a *d_seed64 = nullptr;         // [(lmax+1) nunit]
     int2 *d_start32 = nullptr;               // [(lmax+1) nunit] {g (kNeverLive: none), e}
     int2 *d_start64 = nullptr;
@@ -292,7 +312,7 @@ struct akra_plan_s {
     std::map<long long, akra::CgGraph *> graphs;
     unsigned ws_gen = 0;                     // bumped whenever a workspace is reallocated
     const int *cur_skip = nullptr;           // device flag: operator kernels return early if set
-    int *d_tc_err = nullptr;                 // device flag: a tensor-core completion wait ran out
+    int *d_tc_err = nullptr;                 // device flag: a bounded wait inside a Legendre kernel ran out
     void *h_pinned = nullptr;                // pinned host mirror for status polling
     size_t bytes_tables = 0;
     long long launches = 0;                  // kernels launched (host-side count)
@@ -310,8 +330,12 @@ enum class LegMode { Synth, KS };   // per-l factor f_l = -1 (pure spin-2 SHT) o
 // FP32 synthesis with the tensor-core contraction (akra_legendre_tc.cu), RHS in groups of tcg
 akra_status legendre_synth_tc(akra_plan p, int tcg, LegMode mode, const void *alm, void *phi, int R,
                               const int *units, int nunits, cudaStream_t st);
+constexpr int TC_NT = 128;   // tensor-core synthesis: threads = ring pairs per block = MMA rows
 akra_status legendre_tc_prepare();
-// reads and clears the plan's tensor-core error flag (blocking): ECUDA if a wait ran out
+// persistent tensor-core synthesis over a work list of (instance, m, 128-pair chunk, RHS group)
+akra_status legendre_synth_tc_queue(int tcg, const LegArgs<float> *insts, const int4 *items, int nitems,
+                                    int *counter, cudaStream_t st);
+// reads and clears the plan's kernel-wait error flag (blocking): ECUDA if a bounded wait ran out
 akra_status tc_error_check(akra_plan p);
 
 

@@ -101,10 +101,12 @@ LegArgs<T> leg_args(akra_plan p, const LegShape &s, LegMode mode, const int *uni
     a.uinfo = p->d_units;
     a.coef = coef_ptr<T>(p);
     a.seeds = seed_ptr<T>(p);
+    a.dseeds = p->d_dseed32;
     a.start = start_ptr<T>(p);
     a.fl = mode == LegMode::KS ? D_ptr<T>(p) : nullptr;
     a.ring_active = units == p->d_all_units ? nullptr : p->d_ring_active;
     a.skip = p->cur_skip;
+    a.err = p->d_tc_err;
     return a;
 }
 

@@ -1,26 +1,27 @@
-// akra_legendre_f32x2.cuh -- FP32 Legendre work items with paired FP32 FMAs (sm_100 family:
-// one fma.rn.f32x2 instruction performs two independent, correctly rounded FP32 FMAs).
+// akra_legendre_f32x2.cuh -- the FP32 Legendre adjoint with paired FP32 FMAs (sm_100 family:
+// one fma.rn.f32x2 instruction performs two independent, correctly rounded FP32 FMAs; it
+// occupies the FMA pipe for two cycles but takes one issue slot).
 //
-// The FP32 Legendre kernels are bound by instruction issue (one FMA per issue slot, plus the
-// shared-memory traffic of the staged tiles).  Here the two spin recurrences of a ring pair
-// advance together as one float2 (λ+, λ-):
+// The two spin recurrences of a ring pair advance together as one float2 (λ+, λ-):
 //   * recurrence: T = (A'x + c', A'x - c') is one paired FMA, the update another (2 issues per
 //     pair-step instead of 4);
-//   * synthesis contraction: the staged coefficient a_l is stored twice, (a, a), and
-//     (Σ a λ+, Σ a λ-) += (a, a)·(λ+, λ-): 4 paired FMAs per pair-step and RHS instead of 8;
-//   * adjoint contraction: the ring-pair data are paired across the spins, (X+, X-), and
+//   * contraction: the ring-pair data are paired across the spins, (X+, X-), and
 //     (Σ λ+ X+, Σ λ- X-) += (λ+, λ-)·(X+, X-), the two halves added once per step after the
 //     sum over the thread's pairs: 4 paired FMAs per pair-step and RHS instead of 8.
-// The recurrences and the synthesis round every product and sum exactly as the scalar form
-// does; the adjoint sums the two spins' terms in separate partial sums, added once per step
-// (another summation order, the same FP32 accuracy).
+// The adjoint, which also spends issue slots on its warp reduction, gains from the freed
+// slots (12.77 -> 12.08 ms at Nside 2048 / lmax 4096); the synthesis, bound by the FMA pipe
+// itself, does not and keeps the scalar form.  The recurrences round every product and sum as
+// the scalar form does; the contraction sums the two spins' terms in separate partial sums,
+// added once per step (another summation order, the same FP32 accuracy).
 //
 // Sign-alternated state: with s_l = (-1)^floor((l - l0)/2) the monic recurrence
 // μ_{l+1} = t_l μ_l - μ_{l-1} becomes, for ξ_l = s_l μ_l,
 //     ξ_{l+1} = r_l t_l ξ_l + ξ_{l-1},   r_l = s_{l+1}/s_l = +1 (l - l0 even), -1 (odd),
 // an update with no negated operand.  r_l is folded into the staged coefficients, s_l into
-// the staged alm (synthesis) and into the per-l scale of the partial sums (adjoint); the
+// the staged coefficients of the synthesis and into the per-l scale of the partial sums of the
+// adjoint; the
 // start state (μ_g, μ_{g-1}) at a grid point g (g - l0 a multiple of 64) is (ξ_g, -ξ_{g-1}).
+// The tensor-core synthesis (akra_legendre_tc.cu) runs the same sign-alternated recurrence.
 // Sign flips are exact, so the arithmetic is the scalar form's.
 #pragma once
 #include "akra_internal.cuh"
@@ -69,197 +70,6 @@ __device__ __forceinline__ void f2_rescale(int k, float2 (&V)[P], float2 (&VO)[P
 }
 
 // ---------------------------------------------------------------------------
-// synthesis: Φ(ring, ±m) for every ring of the listed units (FP32, paired FMAs)
-//   s_cf[i]: {rA', rA', rc', -rc'};  s_a2[i][r][0] = (c.re, c.re, c.im, c.im),
-//   s_a2[i][r][1] = (d.re, d.re, d.im, d.im), with c = f s σ (E + iB), d = f s σ (E - iB)
-// ---------------------------------------------------------------------------
-template <int P, int RG, int NT>
-__device__ __forceinline__ void leg_synth_item_f2(const LegArgs<float> &a, const int m, const int chunk,
-                                                  const int r0, float4 *s_cf, float4 (*s_a2)[RG][2])
-{
-    const int L = a.L, nring = a.nring, nunits = a.nunits, nunit_all = a.nunit_all, R = a.R;
-    const long long ntri = a.ntri;
-    const int *__restrict__ units = a.units;
-    const UnitInfo *__restrict__ uinfo = a.uinfo;
-    const float4 *__restrict__ coef = a.coef;
-    const float4 *__restrict__ seeds = a.seeds;
-    const int2 *__restrict__ start = a.start;
-    const unsigned char *__restrict__ ring_active = a.ring_active;
-    const float *__restrict__ fl = a.fl;
-    const float2 *__restrict__ alm = a.alm;
-    float2 *__restrict__ phi = a.phi;
-    const int l0 = m > 2 ? m : 2;
-    const int tid = threadIdx.x;
-    const long long mbase = (long long)m * (2 * L + 1 - m) / 2;
-    const long long tbound = (long long)(L + 1) * nunit_all;   // extent of the start tables
-    const size_t row = 2 * (size_t)L + 1;
-
-    float2 X2[P], V[P], VO[P];
-    int e[P], uid[P], gs[P];
-    // acc[k][r][slot][j]: j = 0 (Σ c.re λ+, Σ c.re λ-), 1 (c.im), 2 (d.re), 3 (d.im)
-    float2 acc[P][RG][2][4];
-    int my_first = kNeverLive;
-#pragma unroll
-    for (int k = 0; k < P; k++) {
-        const int iu = (chunk * P + k) * NT + tid;
-        uid[k] = iu < nunits ? (units ? units[AKRA_IX(iu, nunits, kDbgUnits)] : iu) : -1;
-        X2[k] = make_float2(0.f, 0.f);
-        V[k] = VO[k] = make_float2(0.f, 0.f);
-        e[k] = 0;
-        gs[k] = kNeverLive;
-        if (uid[k] >= 0) {
-            const float x = (float)uinfo[AKRA_IX(uid[k], nunit_all, kDbgUnitInfo)].x;
-            X2[k] = make_float2(x, x);
-            gs[k] = start[AKRA_IX((size_t)m * nunit_all + uid[k], tbound, kDbgStart)].x;
-        }
-        my_first = min(my_first, gs[k]);
-#pragma unroll
-        for (int r = 0; r < RG; r++)
-#pragma unroll
-            for (int s = 0; s < 2; s++)
-#pragma unroll
-                for (int j = 0; j < 4; j++) acc[k][r][s][j] = make_float2(0.f, 0.f);
-    }
-    const int warp_first = __reduce_min_sync(0xffffffffu, my_first);
-    const int l_first = block_min_start<NT>(my_first);
-
-    for (int lt = l_first; lt <= L; lt += TL) {
-        __syncthreads();
-        for (int i = tid; i < TL; i += NT) {
-            const int l = lt + i;
-            s_cf[i] = (l <= L) ? f2_coef_entry(coef[AKRA_IX(mbase + l, ntri, kDbgCoef)], i)
-                               : make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-        for (int i = tid; i < TL * RG; i += NT) {
-            const int li = i / RG, rr = i - li * RG;
-            const int l = lt + li, r = r0 + rr;
-            float4 c4 = make_float4(0.f, 0.f, 0.f, 0.f), d4 = c4;
-            if (l <= L && r < R) {
-                const long long abound = (long long)R * 2 * ntri;
-                float2 E = alm[AKRA_IX(((size_t)r * 2 + 0) * ntri + mbase + l, abound, kDbgAlm)];
-                float2 B = alm[AKRA_IX(((size_t)r * 2 + 1) * ntri + mbase + l, abound, kDbgAlm)];
-                // KS (or -1) factor, monic scale σ_l and the state sign s_l
-                const float f = (fl ? fl[AKRA_IX(l, L + 1, kDbgKsFactor)] : -1.f) *
-                                coef[AKRA_IX(mbase + l, ntri, kDbgCoef)].z * f2_sign(li);
-                if (m == 0) E.y = B.y = 0.f;
-                const float cr = f * (E.x - B.y), ci = f * (E.y + B.x);
-                const float dr = f * (E.x + B.y), di = f * (E.y - B.x);
-                c4 = make_float4(cr, cr, ci, ci);
-                d4 = make_float4(dr, dr, di, di);
-            }
-            s_a2[li][rr][0] = c4;
-            s_a2[li][rr][1] = d4;
-        }
-        __syncthreads();
-        const int nl = min(TL, L - lt + 1);
-        f2_start_pairs<P>(seeds, start, (size_t)m * nunit_all, tbound, lt, uid, gs, V, VO, e);
-        if (warp_first > lt + TL - 1) continue;   // none of this warp's pairs has started yet
-        bool live = true;
-#pragma unroll
-        for (int k = 0; k < P; k++) live &= (e[k] == 0);
-        const bool all_live = __all_sync(0xffffffffu, live);
-
-        // one l-step at slot S (= parity of l - l0): contract with the current state, then recur
-#define AKRA_F2_SYNTH_STEP(I, S, GATED)                                                         \
-    {                                                                                           \
-        bool any = true;                                                                        \
-        if (GATED) {                                                                            \
-            bool a_ = false;                                                                    \
-            _Pragma("unroll") for (int k = 0; k < P; k++) a_ |= (e[k] == 0);                    \
-            any = __any_sync(0xffffffffu, a_);                                                  \
-        }                                                                                       \
-        if (any) {                                                                              \
-            _Pragma("unroll") for (int k = 0; k < P; k++) {                                     \
-                const float2 cur = (S) == 0 ? V[k] : VO[k];                                     \
-                const float2 lam = (GATED && e[k] != 0) ? make_float2(0.f, 0.f) : cur;          \
-                _Pragma("unroll") for (int r = 0; r < RG; r++) {                                \
-                    const float4 c4 = s_a2[I][r][0];                                            \
-                    const float4 d4 = s_a2[I][r][1];                                            \
-                    float2 *ac = acc[k][r][S];                                                  \
-                    ac[0] = f2fma(make_float2(c4.x, c4.y), lam, ac[0]);                         \
-                    ac[1] = f2fma(make_float2(c4.z, c4.w), lam, ac[1]);                         \
-                    ac[2] = f2fma(make_float2(d4.x, d4.y), lam, ac[2]);                         \
-                    ac[3] = f2fma(make_float2(d4.z, d4.w), lam, ac[3]);                         \
-                }                                                                               \
-            }                                                                                   \
-        }                                                                                       \
-        {                                                                                       \
-            const float4 cf = s_cf[I];                                                          \
-            _Pragma("unroll") for (int k = 0; k < P; k++) {                                     \
-                const float2 t = f2fma(make_float2(cf.x, cf.y), X2[k], make_float2(cf.z, cf.w)); \
-                /* the new value overwrites the older state; the roles swap every step */      \
-                if ((S) == 0) {                                                                 \
-                    VO[k] = f2fma(t, V[k], VO[k]);                                              \
-                    if (GATED) f2_rescale<P>(k, V, VO, e, VO[k]);                               \
-                } else {                                                                        \
-                    V[k] = f2fma(t, VO[k], V[k]);                                               \
-                    if (GATED) f2_rescale<P>(k, V, VO, e, V[k]);                                \
-                }                                                                               \
-            }                                                                                   \
-        }                                                                                       \
-    }
-
-        if (all_live) {
-            for (int i = 0; i < nl; i += 2) {
-                AKRA_F2_SYNTH_STEP(i, 0, false)
-                AKRA_F2_SYNTH_STEP(i + 1, 1, false)
-            }
-        } else {
-            for (int i = 0; i < nl; i += 2) {
-                AKRA_F2_SYNTH_STEP(i, 0, true)
-                AKRA_F2_SYNTH_STEP(i + 1, 1, true)
-            }
-        }
-#undef AKRA_F2_SYNTH_STEP
-    }
-
-    // combine parities into the north and south rings and write Φ(±m)
-    const bool swap = ((l0 + m) & 1) != 0;   // slot 0 holds odd (l+m) when l0+m is odd
-    const long long pbound = (long long)R * nring * row;   // extent of Φ
-#pragma unroll
-    for (int k = 0; k < P; k++) {
-        if (uid[k] < 0) continue;
-        const UnitInfo ui = uinfo[AKRA_IX(uid[k], nunit_all, kDbgUnitInfo)];
-#pragma unroll
-        for (int rr = 0; rr < RG; rr++) {
-            const int r = r0 + rr;
-            if (r >= R) continue;
-            // per parity: [0] Σcλ+ re, [1] Σcλ+ im, [2] Σdλ- re, [3] Σdλ- im,
-            //             [4] Σcλ- re, [5] Σcλ- im, [6] Σdλ+ re, [7] Σdλ+ im
-            float se[8], so[8];
-#pragma unroll
-            for (int s = 0; s < 2; s++) {
-                const float2 *q = acc[k][rr][s];
-                float *dst = ((s == 0) != swap) ? se : so;
-                dst[0] = q[0].x;
-                dst[1] = q[1].x;
-                dst[2] = q[2].y;
-                dst[3] = q[3].y;
-                dst[4] = q[0].y;
-                dst[5] = q[1].y;
-                dst[6] = q[2].x;
-                dst[7] = q[3].x;
-            }
-            // north: Φ(m) = Σ c λ+,  conj Φ(-m) = Σ d λ-      (even + odd)
-            // south: Φ(m) = Σ c λ-,  conj Φ(-m) = Σ d λ+      (even - odd)
-#pragma unroll
-            for (int side = 0; side < 2; side++) {
-                const int ring = side == 0 ? ui.ring_n : ui.ring_s;
-                if (ring < 0) continue;
-                if (ring_active && !ring_active[AKRA_IX(ring, nring, kDbgRingActive)]) continue;
-                const int o = side == 0 ? 0 : 4;
-                const float sg = side == 0 ? 1.f : -1.f;
-                const float fr = se[o + 0] + sg * so[o + 0], fi = se[o + 1] + sg * so[o + 1];
-                const float gr = se[o + 2] + sg * so[o + 2], gi = se[o + 3] + sg * so[o + 3];
-                const size_t pb = ((size_t)r * nring + ring) * row + L;   // Φ(ring, m = 0)
-                phi[AKRA_IX(pb + m, pbound, kDbgPhiWrite)] = make_float2(fr, fi);
-                if (m > 0) phi[AKRA_IX(pb - m, pbound, kDbgPhiWrite)] = make_float2(gr, -gi);
-            }
-        }
-    }
-}
-
-// ---------------------------------------------------------------------------
 // adjoint: partial[chunk][r][idx(l,m)] = Σ_{units in chunk} (E-part, B-part) at each l (FP32,
 // paired FMAs).  Per unit and RHS the spin-paired data are Q0 = (X1.re, X2.re),
 // Q1 = (X1.im, X2.im), Q2 = (X3.re, X4.re), Q3 = (X3.im, X4.im) (X1..X4 as in the scalar item),
@@ -270,8 +80,11 @@ __device__ __forceinline__ void leg_synth_item_f2(const LegArgs<float> &a, const
 template <int P, int RG, int NT>
 __device__ __forceinline__ void leg_adjoint_item_f2(const LegArgs<float> &a, const int m, const int chunk,
                                                     const int r0, float4 *s_cf, float *s_sig,
-                                                    float (*s_red)[TL][RG][4], float (*s_tr)[32][36])
+                                                    float (*s_red)[TL][RG][4], float (*s_tr)[32][36],
+                                                    float4 *s_cfd)
 {
+    // s_cfd: difference-form coefficients {A', A', (A'-2) + c', (A'-2) - c'} per step, staged only in
+    // blocks that hold ring pairs near a pole
     constexpr int NW = NT / 32;
     constexpr int K = 8 / RG;   // l-steps per reduction block: K * 4 * RG = 32 values per lane
     static_assert(K >= 2 && K * 4 * RG == 32, "RG must be 1, 2 or 4");
@@ -296,9 +109,11 @@ __device__ __forceinline__ void leg_adjoint_item_f2(const LegArgs<float> &a, con
     (void)pbound;
     (void)qbound;
 
-    float2 X2[P], V[P], VO[P];
+    float2 X2[P], V[P], VO[P];   // X2 = (x, x), or (x - 1, x - 1) for the difference form
     int e[P], uid[P], gs[P];
+    bool dk[P];                  // this warp's pairs of slot k run the difference form (warp-uniform)
     int my_first = kNeverLive;
+    bool any_diff = false;
     float2 Q[P][RG][4];
 #pragma unroll
     for (int k = 0; k < P; k++) {
@@ -312,11 +127,18 @@ __device__ __forceinline__ void leg_adjoint_item_f2(const LegArgs<float> &a, con
         gs[k] = kNeverLive;
         UnitInfo ui;
         ui.ring_n = ui.ring_s = -1;
+        bool polar = false;
         if (u >= 0) {
             ui = uinfo[AKRA_IX(u, nunit_all, kDbgUnitInfo)];
-            const float x = (float)ui.x;
-            X2[k] = make_float2(x, x);
+            polar = ui.x >= kDiffX;
             gs[k] = start[AKRA_IX((size_t)m * nunit_all + u, tbound, kDbgStart)].x;
+        }
+        dk[k] = __any_sync(0xffffffffu, polar);
+        any_diff |= dk[k];
+        if (u >= 0) {
+            // x - 1 = -2 sin^2(θ/2), accurate near the pole
+            const float x = dk[k] ? (float)(-exp2(2.0 * ui.ls + 1.0)) : (float)ui.x;
+            X2[k] = make_float2(x, x);
         }
         my_first = min(my_first, gs[k]);
 #pragma unroll
@@ -354,6 +176,7 @@ __device__ __forceinline__ void leg_adjoint_item_f2(const LegArgs<float> &a, con
     float (*tr)[36] = s_tr[warp];
     const int warp_first = __reduce_min_sync(0xffffffffu, my_first);
     const int l_first = block_min_start<NT>(my_first);
+    const bool blk_diff = __syncthreads_or(any_diff) != 0;   // block-uniform
     // the l below the first start get zero partial sums
     for (int i = tid; i < (min(l_first, L + 1) - l0) * RG * 4; i += NT) {
         const int step = i / (RG * 4), rem = i - step * RG * 4, rr = rem >> 2, q = rem & 3;
@@ -369,10 +192,17 @@ __device__ __forceinline__ void leg_adjoint_item_f2(const LegArgs<float> &a, con
             const float4 c = (l <= L) ? coef[AKRA_IX(mbase + l, ntri, kDbgCoef)] : make_float4(0.f, 0.f, 0.f, 0.f);
             s_cf[i] = f2_coef_entry(c, i);
             s_sig[i] = c.z * f2_sign(i);   // the recurrence ran on ξ_l = s_l λ_l / σ_l
+            if (blk_diff) s_cfd[i] = make_float4(c.x, c.x, c.w + c.y, c.w - c.y);
         }
         __syncthreads();
         const int nl = min(TL, L - lt + 1);
         f2_start_pairs<P>(seeds, start, (size_t)m * nunit_all, tbound, lt, uid, gs, V, VO, e);
+        if (blk_diff) {
+#pragma unroll
+            for (int k = 0; k < P; k++)
+                if (dk[k] && gs[k] == lt)   // difference form: second register holds μ_g - μ_{g-1}
+                    VO[k] = a.dseeds[AKRA_IX((size_t)m * nunit_all + uid[k], tbound, kDbgSeeds)];
+        }
         if (warp_first > lt + TL - 1) {
             // none of this warp's pairs has started yet: its rows of the tile sum are zero
             float *zr = &s_red[warp][0][0][0];
@@ -386,7 +216,7 @@ __device__ __forceinline__ void leg_adjoint_item_f2(const LegArgs<float> &a, con
 
         // K l-steps (slot of step kk = parity of kk), each step's 4 RG sums stored at once into
         // this lane's column of the warp's transpose buffer, then the warp reduction
-#define AKRA_F2_ADJ_KBLOCK(GATED)                                                               \
+#define AKRA_F2_ADJ_KBLOCK(GATED, DIFF)                                                         \
     for (int kb = 0; kb < nkb; kb++) {                                                          \
         _Pragma("unroll") for (int kk = 0; kk < K; kk++) {                                      \
             const bool slotA = (kk & 1) == 0;                                                   \
@@ -402,7 +232,10 @@ __device__ __forceinline__ void leg_adjoint_item_f2(const LegArgs<float> &a, con
             if (any) {                                                                          \
                 _Pragma("unroll") for (int k = 0; k < P; k++) {                                 \
                     const float2 cur = slotA ? V[k] : VO[k];                                    \
-                    const float2 lam = (GATED && e[k] != 0) ? make_float2(0.f, 0.f) : cur;      \
+                    /* difference form: the state is μ; the contraction takes ξ = s_l μ, with */ \
+                    /* s_l from the step's index in the tile (K = 2 at RG = 4: kk alone misses it) */ \
+                    const float2 cx = (DIFF && dk[k] && ((kb * K + kk) & 2)) ? make_float2(-cur.x, -cur.y) : cur; \
+                    const float2 lam = (GATED && e[k] != 0) ? make_float2(0.f, 0.f) : cx;       \
                     _Pragma("unroll") for (int rr = 0; rr < RG; rr++)                           \
                         _Pragma("unroll") for (int j = 0; j < 4; j++)                           \
                             F[rr][j] = f2fma(lam, Q[k][rr][j], F[rr][j]);                       \
@@ -424,13 +257,31 @@ __device__ __forceinline__ void leg_adjoint_item_f2(const LegArgs<float> &a, con
             }                                                                                   \
             const float4 cf = s_cf[kb * K + kk];                                                \
             _Pragma("unroll") for (int k = 0; k < P; k++) {                                     \
-                const float2 t = f2fma(make_float2(cf.x, cf.y), X2[k], make_float2(cf.z, cf.w)); \
-                if (slotA) {                                                                    \
-                    VO[k] = f2fma(t, V[k], VO[k]);                                              \
-                    if (GATED) f2_rescale<P>(k, V, VO, e, VO[k]);                               \
+                if (DIFF && dk[k]) {                                                            \
+                    /* d_{l+1} = u μ_l + d_l, μ_{l+1} = μ_l + d_{l+1}: the register that held d_l */ \
+                    /* receives μ_{l+1}, the one that held μ_l receives d_{l+1} */             \
+                    const float4 cd = s_cfd[kb * K + kk];                                       \
+                    const float2 uu = f2fma(make_float2(cd.x, cd.y), X2[k], make_float2(cd.z, cd.w)); \
+                    if (slotA) {                                                                \
+                        const float2 dn = f2fma(uu, V[k], VO[k]);                               \
+                        VO[k] = __fadd2_rn(V[k], dn);                                           \
+                        V[k] = dn;                                                              \
+                        if (GATED) f2_rescale<P>(k, V, VO, e, VO[k]);                           \
+                    } else {                                                                    \
+                        const float2 dn = f2fma(uu, VO[k], V[k]);                               \
+                        V[k] = __fadd2_rn(VO[k], dn);                                           \
+                        VO[k] = dn;                                                             \
+                        if (GATED) f2_rescale<P>(k, V, VO, e, V[k]);                            \
+                    }                                                                           \
                 } else {                                                                        \
-                    V[k] = f2fma(t, VO[k], V[k]);                                               \
-                    if (GATED) f2_rescale<P>(k, V, VO, e, V[k]);                                \
+                    const float2 t = f2fma(make_float2(cf.x, cf.y), X2[k], make_float2(cf.z, cf.w)); \
+                    if (slotA) {                                                                \
+                        VO[k] = f2fma(t, V[k], VO[k]);                                          \
+                        if (GATED) f2_rescale<P>(k, V, VO, e, VO[k]);                           \
+                    } else {                                                                    \
+                        V[k] = f2fma(t, VO[k], V[k]);                                           \
+                        if (GATED) f2_rescale<P>(k, V, VO, e, V[k]);                            \
+                    }                                                                           \
                 }                                                                               \
             }                                                                                   \
         }                                                                                       \
@@ -446,10 +297,12 @@ __device__ __forceinline__ void leg_adjoint_item_f2(const LegArgs<float> &a, con
         }                                                                                       \
     }
 
-        if (all_live) {
-            AKRA_F2_ADJ_KBLOCK(false)
+        if (blk_diff) {
+            AKRA_F2_ADJ_KBLOCK(true, true)   // a block with pairs near a pole (rare)
+        } else if (all_live) {
+            AKRA_F2_ADJ_KBLOCK(false, false)
         } else {
-            AKRA_F2_ADJ_KBLOCK(true)
+            AKRA_F2_ADJ_KBLOCK(true, false)
         }
 #undef AKRA_F2_ADJ_KBLOCK
         }

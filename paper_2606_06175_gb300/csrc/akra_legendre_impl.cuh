@@ -47,6 +47,23 @@ __device__ __forceinline__ void start_pairs(const V4 *__restrict__ seeds, const 
     }
 }
 
+// FP32 difference-form pairs: at their start the second state register holds d_g = μ_g - μ_{g-1}
+template <typename T, int P>
+__device__ __forceinline__ void start_diff(const float2 *__restrict__ dseeds, size_t base, long long tbound,
+                                           int lt, const int (&uid)[P], const int (&gs)[P], const bool (&dk)[P],
+                                           T (&vpo)[P], T (&vmo)[P])
+{
+    (void)tbound;
+#pragma unroll
+    for (int k = 0; k < P; k++) {
+        if (dk[k] && gs[k] == lt) {
+            const float2 d = dseeds[AKRA_IX(base + uid[k], tbound, kDbgSeeds)];
+            vpo[k] = d.x;
+            vmo[k] = d.y;
+        }
+    }
+}
+
 }  // namespace akra
 
 #include "akra_legendre_f32x2.cuh"   // FP32 items with paired FMAs (use TL, block_min_start)
@@ -80,22 +97,30 @@ __device__ __forceinline__ void leg_synth_item(const LegArgs<T> &a, const int m,
 
     // every pair's recurrence starts at its grid point gs (state loaded there); until then
     // its state is zero, which the recurrence keeps and the contraction ignores
-    T x[P], vp[P], vm[P], vpo[P], vmo[P];
+    T x[P], y[P], vp[P], vm[P], vpo[P], vmo[P];
     int e[P], uid[P], gs[P];
+    bool dk[P];   // FP32: this warp's pairs of slot k run the difference form (warp-uniform)
     T acc[P][RG][16];
     int my_first = kNeverLive;
+    bool any_diff = false;
 #pragma unroll
     for (int k = 0; k < P; k++) {
         const int iu = (chunk * P + k) * NT + tid;
         uid[k] = iu < nunits ? (units ? units[AKRA_IX(iu, nunits, kDbgUnits)] : iu) : -1;
-        x[k] = 0;
+        x[k] = y[k] = 0;
         vp[k] = vm[k] = vpo[k] = vmo[k] = 0;
         e[k] = 0;
         gs[k] = kNeverLive;
+        bool polar = false;
         if (uid[k] >= 0) {
-            x[k] = (T)uinfo[AKRA_IX(uid[k], nunit_all, kDbgUnitInfo)].x;
+            const UnitInfo ui = uinfo[AKRA_IX(uid[k], nunit_all, kDbgUnitInfo)];
+            x[k] = (T)ui.x;
+            y[k] = (T)(-exp2(2.0 * ui.ls + 1.0));   // x - 1 = -2 sin^2(θ/2), accurate near the pole
+            polar = std::is_same<T, float>::value && ui.x >= kDiffX;
             gs[k] = start[AKRA_IX((size_t)m * nunit_all + uid[k], tbound, kDbgStart)].x;
         }
+        dk[k] = __any_sync(0xffffffffu, polar);
+        any_diff |= dk[k];
         my_first = min(my_first, gs[k]);
 #pragma unroll
         for (int r = 0; r < RG; r++)
@@ -104,6 +129,8 @@ __device__ __forceinline__ void leg_synth_item(const LegArgs<T> &a, const int m,
     }
     const int warp_first = __reduce_min_sync(0xffffffffu, my_first);
     const int l_first = block_min_start<NT>(my_first);
+    const bool blk_diff = __syncthreads_or(any_diff) != 0;   // block-uniform
+    __shared__ float2 s_cb[TL];   // difference form: {(A'-2) + c', (A'-2) - c'} per step
 
     for (int lt = l_first; lt <= L; lt += TL) {
         __syncthreads();
@@ -113,6 +140,10 @@ __device__ __forceinline__ void leg_synth_item(const LegArgs<T> &a, const int m,
             const V4 c0 = (l <= L) ? coef[AKRA_IX(mbase + l, ntri, kDbgCoef)] : V4{0, 0, 0, 0};
             const V4 c1 = (l + 1 <= L) ? coef[AKRA_IX(mbase + l + 1, ntri, kDbgCoef)] : V4{0, 0, 0, 0};
             s_coef[i] = V4{c0.x, c0.y, c1.x, c1.y};
+            if (blk_diff) {
+                s_cb[2 * i] = make_float2((float)(c0.w + c0.y), (float)(c0.w - c0.y));
+                s_cb[2 * i + 1] = make_float2((float)(c1.w + c1.y), (float)(c1.w - c1.y));
+            }
         }
         for (int i = tid; i < TL * RG; i += NT) {
             const int li = i / RG, rr = i - li * RG;
@@ -134,6 +165,7 @@ __device__ __forceinline__ void leg_synth_item(const LegArgs<T> &a, const int m,
         __syncthreads();
         const int nl = min(TL, L - lt + 1);
         start_pairs(seeds, start, (size_t)m * nunit_all, tbound, lt, uid, gs, vp, vm, vpo, vmo, e);
+        if (blk_diff) start_diff<T, P>(a.dseeds, (size_t)m * nunit_all, tbound, lt, uid, gs, dk, vpo, vmo);
         if (warp_first > lt + TL - 1) continue;   // none of this warp's pairs has started yet
         bool live = true;
 #pragma unroll
@@ -143,7 +175,7 @@ __device__ __forceinline__ void leg_synth_item(const LegArgs<T> &a, const int m,
         // one l-step: contract at l (slot S = parity of l - l0), then recur to l+1.
         // vp = 2λ, vm = (-2)λ; accumulators per slot: P1 = Σ c 2λ, P2 = Σ d (-2)λ,
         // P3 = Σ c (-2)λ, P4 = Σ d 2λ (complex)
-#define AKRA_SYNTH_STEP(I, S, GATED, CA, CC)                                                        \
+#define AKRA_SYNTH_STEP(I, S, GATED, CA, CC, DIFF)                                                  \
     {                                                                                       \
         bool any = true;                                                                    \
         if (GATED) {                                                                        \
@@ -170,13 +202,24 @@ __device__ __forceinline__ void leg_synth_item(const LegArgs<T> &a, const int m,
             }                                                                               \
         }                                                                                   \
         _Pragma("unroll") for (int k = 0; k < P; k++) {                                     \
-            const T t1 = fma((CA), x[k], (CC));                                             \
-            const T t2 = fma((CA), x[k], -(CC));                                            \
             /* the new value overwrites the older register; the roles swap every step */    \
             T &cp_ = (S) == 0 ? vp[k] : vpo[k], &op_ = (S) == 0 ? vpo[k] : vp[k];           \
             T &cm_ = (S) == 0 ? vm[k] : vmo[k], &om_ = (S) == 0 ? vmo[k] : vm[k];           \
-            op_ = fma(t1, cp_, -op_);                                                       \
-            om_ = fma(t2, cm_, -om_);                                                       \
+            if (DIFF && dk[k]) {                                                            \
+                /* difference form: op_ held d_l, receives μ_{l+1}; cp_ receives d_{l+1} */ \
+                const float2 cb = s_cb[I];                                                  \
+                const T u1 = fma((CA), y[k], (T)cb.x), u2 = fma((CA), y[k], (T)cb.y);       \
+                const T d1 = fma(u1, cp_, op_), d2 = fma(u2, cm_, om_);                     \
+                op_ = cp_ + d1;                                                             \
+                om_ = cm_ + d2;                                                             \
+                cp_ = d1;                                                                   \
+                cm_ = d2;                                                                   \
+            } else {                                                                        \
+                const T t1 = fma((CA), x[k], (CC));                                         \
+                const T t2 = fma((CA), x[k], -(CC));                                        \
+                op_ = fma(t1, cp_, -op_);                                                   \
+                om_ = fma(t2, cm_, -om_);                                                   \
+            }                                                                               \
             if (GATED && e[k] < 0 && (fabs(op_) > Scale<T>::hi() || fabs(om_) > Scale<T>::hi())) { \
                 vp[k] *= Scale<T>::inv();                                                   \
                 vm[k] *= Scale<T>::inv();                                                   \
@@ -187,17 +230,26 @@ __device__ __forceinline__ void leg_synth_item(const LegArgs<T> &a, const int m,
         }                                                                                   \
     }
 
-        if (all_live) {
-            for (int i = 0; i < nl; i += 2) {
-                const V4 cc = s_coef[i >> 1];
-                AKRA_SYNTH_STEP(i, 0, false, cc.x, cc.y)
-                AKRA_SYNTH_STEP(i + 1, 1, false, cc.z, cc.w)
+        if (!(std::is_same<T, float>::value && blk_diff)) {
+            if (all_live) {
+                for (int i = 0; i < nl; i += 2) {
+                    const V4 cc = s_coef[i >> 1];
+                    AKRA_SYNTH_STEP(i, 0, false, cc.x, cc.y, false)
+                    AKRA_SYNTH_STEP(i + 1, 1, false, cc.z, cc.w, false)
+                }
+            } else {
+                for (int i = 0; i < nl; i += 2) {
+                    const V4 cc = s_coef[i >> 1];
+                    AKRA_SYNTH_STEP(i, 0, true, cc.x, cc.y, false)
+                    AKRA_SYNTH_STEP(i + 1, 1, true, cc.z, cc.w, false)
+                }
             }
-        } else {
+        } else if constexpr (std::is_same<T, float>::value) {
+            // a block with pairs near a pole (rare): some warps run the difference form
             for (int i = 0; i < nl; i += 2) {
                 const V4 cc = s_coef[i >> 1];
-                AKRA_SYNTH_STEP(i, 0, true, cc.x, cc.y)
-                AKRA_SYNTH_STEP(i + 1, 1, true, cc.z, cc.w)
+                AKRA_SYNTH_STEP(i, 0, true, cc.x, cc.y, true)
+                AKRA_SYNTH_STEP(i + 1, 1, true, cc.z, cc.w, true)
             }
         }
 #undef AKRA_SYNTH_STEP
@@ -249,19 +301,16 @@ __device__ __forceinline__ void leg_synth_item(const LegArgs<T> &a, const int m,
 //     (l+m) even: E += 2λ U1 + (-2)λ U2,  B += 2λ U3 + (-2)λ U4
 //     (l+m) odd : E += 2λ U3 - (-2)λ U4,  B += 2λ U1 - (-2)λ U2
 // ---------------------------------------------------------------------------
-// one synthesis work item: FP32 with paired FMAs, FP64 scalar
+// one synthesis work item (FP32 and FP64 share the scalar item: for the synthesis, whose
+// contraction reads one staged coefficient per step for all of a thread's pairs, the paired-FMA
+// form measured slower -- 10.25 against 9.50 ms at Nside 2048 / lmax 4096 -- as the FMA pipe,
+// not instruction issue, bounds it)
 template <typename T, int P, int RG, int NT>
 __device__ __forceinline__ void synth_item(const LegArgs<T> &a, int m, int chunk, int r0)
 {
-    if constexpr (std::is_same<T, float>::value) {
-        __shared__ float4 s_cf[TL];
-        __shared__ float4 s_a2[TL][RG][2];
-        leg_synth_item_f2<P, RG, NT>(a, m, chunk, r0, s_cf, s_a2);
-    } else {
-        __shared__ v4_t<T> s_coef[TL];
-        __shared__ v4_t<T> s_alm[TL][RG];
-        leg_synth_item<T, P, RG, NT>(a, m, chunk, r0, s_coef, s_alm);
-    }
+    __shared__ v4_t<T> s_coef[TL];
+    __shared__ v4_t<T> s_alm[TL][RG];
+    leg_synth_item<T, P, RG, NT>(a, m, chunk, r0, s_coef, s_alm);
 }
 
 template <typename T, int P, int RG, int NT>
@@ -519,7 +568,8 @@ __device__ __forceinline__ void adjoint_item(const LegArgs<T> &a, int m, int chu
         __shared__ float s_sig[TL];
         __shared__ float s_red[NT / 32][TL][RG][4];
         __shared__ __align__(16) float s_tr[NT / 32][32][36];
-        leg_adjoint_item_f2<P, RG, NT>(a, m, chunk, r0, s_cf, s_sig, s_red, s_tr);
+        __shared__ float4 s_cfd[TL];
+        leg_adjoint_item_f2<P, RG, NT>(a, m, chunk, r0, s_cf, s_sig, s_red, s_tr, s_cfd);
     } else {
         __shared__ v4_t<T> s_coef[AdjTile<T, RG>::v];
         __shared__ T s_red[NT / 32][AdjTile<T, RG>::v][RG][4];

@@ -14,6 +14,8 @@
 // Tiles are double-buffered: the recurrence of tile t+1 runs while the MMAs of tile t do.  After
 // the last tile each thread reads its own row (TMEM lane = ring pair) and forms Φ(±m) of both
 // rings as the CUDA-core item does.
+#include <algorithm>
+
 #include "akra_legendre_impl.cuh"
 #include "akra_tc.cuh"
 
@@ -22,8 +24,7 @@ namespace akra {
 namespace {
 
 constexpr int TCT = 16;        // l-steps per tile: 8 of each parity (K = 8 TF32 per MMA)
-constexpr int TC_NT = 128;     // threads = ring pairs per block = MMA rows
-constexpr int kWaitLimit = 1 << 22;
+constexpr int kWaitLimit = 1 << 20;
 
 template <int RG>
 struct TcSynth {
@@ -32,7 +33,7 @@ struct TcSynth {
     static constexpr int B_TILE = N * 8 * 4;
     static constexpr int BUF = 8 * A_TILE + 4 * B_TILE;      // A[s][p][h], B[p][h]
     static constexpr int CF = TCT * 16;                      // float4 coefficients of a tile
-    static constexpr int USED = 2 * BUF + 2 * CF;
+    static constexpr int USED = 2 * BUF + 4 * CF;            // + standard / difference-form coefficients
     // TMEM columns: 4 streams x N (a power of two >= 32); shared memory sized so that the blocks
     // resident on an SM never ask for more than its 512 columns
     static constexpr uint32_t NCOL = 16 * RG < 32 ? 32 : 16 * RG;
@@ -51,18 +52,20 @@ __device__ __forceinline__ unsigned char *tc_b(unsigned char *buf, int p, int h)
     return buf + 8 * TcSynth<RG>::A_TILE + (p * 2 + h) * TcSynth<RG>::B_TILE;
 }
 
-// stage tile [lt, lt + 16): recurrence coefficients (threads 0..15) and the B tiles
+// stage tile [lt, lt + 16): recurrence coefficients (threads 0..15; with diff also the
+// difference-form ones {A', A', (A'-2) + c', (A'-2) - c'}) and the B tiles
 template <int RG>
 __device__ __forceinline__ void tc_stage(const LegArgs<float> &a, int m, long long mbase, int r0, int lt,
-                                         unsigned char *buf, float4 *cf)
+                                         unsigned char *buf, float4 *cf, float4 *cfd, bool diff)
 {
     const int L = a.L, R = a.R;
     const long long ntri = a.ntri;
     const int tid = threadIdx.x;
     if (tid < TCT) {
         const int l = lt + tid;
-        cf[tid] = (l <= L) ? f2_coef_entry(a.coef[AKRA_IX(mbase + l, ntri, kDbgCoef)], tid)
-                           : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 c = (l <= L) ? a.coef[AKRA_IX(mbase + l, ntri, kDbgCoef)] : make_float4(0.f, 0.f, 0.f, 0.f);
+        cf[tid] = f2_coef_entry(c, tid);
+        if (diff) cfd[tid] = make_float4(c.x, c.x, c.w + c.y, c.w - c.y);
     }
     for (int e = tid; e < TCT * RG; e += TC_NT) {
         const int i = e / RG, rr = e - i * RG;
@@ -116,16 +119,16 @@ __device__ __forceinline__ void tc_store_half(unsigned char *buf, int row, int h
 
 }  // namespace
 
+// one work item (m, chunk of 128 ring pairs, RHS group from r0) into the block's TMEM columns
+// (allocated once per block by the caller: a CTA allocates only until it gives up its permit).
+// The two mbarriers are initialised at the start of the item and invalidated at its end, once
+// every commit issued to them has been waited for, so a persistent block can run items back to back.
 template <int RG>
-__global__ void __launch_bounds__(TC_NT) k_leg_synth_tc(LegArgs<float> a)
+__device__ __forceinline__ void tc_synth_item(const LegArgs<float> &a, const int m, const int chunk, const int r0,
+                                              unsigned char *smem, uint64_t *s_mbar, const uint32_t tmem_base)
 {
     using S = TcSynth<RG>;
     constexpr int N = S::N;
-    extern __shared__ __align__(1024) unsigned char smem[];
-    __shared__ __align__(8) uint64_t s_mbar[2];
-    __shared__ uint32_t s_tmem;
-    if (a.skip && *a.skip) return;
-    const int m = blockIdx.x / a.nchunks, chunk = blockIdx.x - m * a.nchunks, r0 = blockIdx.y * RG;
     const int L = a.L, nring = a.nring, nunits = a.nunits, nunit_all = a.nunit_all, R = a.R;
     const int tid = threadIdx.x, warp = tid >> 5;
     const int l0 = m > 2 ? m : 2;
@@ -142,17 +145,25 @@ __global__ void __launch_bounds__(TC_NT) k_leg_synth_tc(LegArgs<float> a)
     float2 X2 = make_float2(0.f, 0.f);
     float2 V[1] = {make_float2(0.f, 0.f)}, VO[1] = {make_float2(0.f, 0.f)};
     int e1[1] = {0};
+    bool polar = false;
+    UnitInfo u0;
     if (uid1[0] >= 0) {
-        const float x = (float)a.uinfo[AKRA_IX(uid1[0], nunit_all, kDbgUnitInfo)].x;
-        X2 = make_float2(x, x);
+        u0 = a.uinfo[AKRA_IX(uid1[0], nunit_all, kDbgUnitInfo)];
+        polar = u0.x >= kDiffX;
         gs1[0] = a.start[AKRA_IX((size_t)m * nunit_all + uid1[0], tbound, kDbgStart)].x;
+    }
+    // pairs near a pole run the difference form (warp-uniform; X2 then holds x - 1)
+    const bool dkw = __any_sync(0xffffffffu, polar);
+    if (uid1[0] >= 0) {
+        const float x = dkw ? (float)(-exp2(2.0 * u0.ls + 1.0)) : (float)u0.x;
+        X2 = make_float2(x, x);
     }
     const int warp_first = __reduce_min_sync(0xffffffffu, gs1[0]);
     const int l_first = block_min_start<TC_NT>(gs1[0]);
+    const bool blk_diff = __syncthreads_or(dkw) != 0;
 
     float dv[2][2][4];   // D of this row: [spin][parity][c.re, c.im, d.re, d.im], per RHS below
     if (l_first <= L) {
-        if (warp == 0) tc::tmem_alloc(&s_tmem, S::NCOL);
         if (tid == 0) {
             tc::mbar_init(&s_mbar[0], 1);
             tc::mbar_init(&s_mbar[1], 1);
@@ -163,12 +174,13 @@ __global__ void __launch_bounds__(TC_NT) k_leg_synth_tc(LegArgs<float> a)
         tc::fence_after();
     }
     const bool active = l_first <= L;
-    const uint32_t tmem = active ? s_tmem : 0u;
+    const uint32_t tmem = tmem_base;
     bool ok = true;
     const int T = active ? (L - l_first) / TCT + 1 : 0;
     float4 *cf_all = reinterpret_cast<float4 *>(smem + 2 * S::BUF);
+    float4 *cfd_all = cf_all + 2 * TCT;
     if (active) {
-        tc_stage<RG>(a, m, mbase, r0, l_first, smem, cf_all);
+        tc_stage<RG>(a, m, mbase, r0, l_first, smem, cf_all, cfd_all, blk_diff);
         __syncthreads();
     }
     const uint32_t idesc = tc::idesc_tf32(128, N);
@@ -176,7 +188,10 @@ __global__ void __launch_bounds__(TC_NT) k_leg_synth_tc(LegArgs<float> a)
         const int lt = l_first + t * TCT, b = t & 1;
         unsigned char *buf = smem + b * S::BUF;
         const float4 *cf = cf_all + b * TCT;
+        const float4 *cfd = cfd_all + b * TCT;
         f2_start_pairs<1>(a.seeds, a.start, (size_t)m * nunit_all, tbound, lt, uid1, gs1, V, VO, e1);
+        if (dkw && gs1[0] == lt)   // difference form: second register holds μ_g - μ_{g-1}
+            VO[0] = a.dseeds[AKRA_IX((size_t)m * nunit_all + uid1[0], tbound, kDbgSeeds)];
         if (warp_first > lt + TCT - 1) {
             // none of this warp's pairs has started: zero rows
             const float2 z[8] = {};
@@ -191,15 +206,33 @@ __global__ void __launch_bounds__(TC_NT) k_leg_synth_tc(LegArgs<float> a)
                 for (int j = 0; j < 8; j++) {
                     const int i = half * 8 + j;
                     const float2 cur = (i & 1) == 0 ? V[0] : VO[0];
-                    lam[j] = (!all_live && e1[0] != 0) ? make_float2(0.f, 0.f) : cur;
-                    const float4 c4 = cf[i];
-                    const float2 tt = f2fma(make_float2(c4.x, c4.y), X2, make_float2(c4.z, c4.w));
-                    if ((i & 1) == 0) {
-                        VO[0] = f2fma(tt, V[0], VO[0]);
-                        if (!all_live) f2_rescale<1>(0, V, VO, e1, VO[0]);
+                    // difference form: the state is μ, the A tiles take ξ = s_l μ
+                    const float2 cx = (dkw && (i & 2)) ? make_float2(-cur.x, -cur.y) : cur;
+                    lam[j] = (!all_live && e1[0] != 0) ? make_float2(0.f, 0.f) : cx;
+                    if (dkw) {
+                        const float4 cd = cfd[i];
+                        const float2 uu = f2fma(make_float2(cd.x, cd.y), X2, make_float2(cd.z, cd.w));
+                        if ((i & 1) == 0) {
+                            const float2 dn = f2fma(uu, V[0], VO[0]);
+                            VO[0] = __fadd2_rn(V[0], dn);
+                            V[0] = dn;
+                            if (!all_live) f2_rescale<1>(0, V, VO, e1, VO[0]);
+                        } else {
+                            const float2 dn = f2fma(uu, VO[0], V[0]);
+                            V[0] = __fadd2_rn(VO[0], dn);
+                            VO[0] = dn;
+                            if (!all_live) f2_rescale<1>(0, V, VO, e1, V[0]);
+                        }
                     } else {
-                        V[0] = f2fma(tt, VO[0], V[0]);
-                        if (!all_live) f2_rescale<1>(0, V, VO, e1, V[0]);
+                        const float4 c4 = cf[i];
+                        const float2 tt = f2fma(make_float2(c4.x, c4.y), X2, make_float2(c4.z, c4.w));
+                        if ((i & 1) == 0) {
+                            VO[0] = f2fma(tt, V[0], VO[0]);
+                            if (!all_live) f2_rescale<1>(0, V, VO, e1, VO[0]);
+                        } else {
+                            V[0] = f2fma(tt, VO[0], V[0]);
+                            if (!all_live) f2_rescale<1>(0, V, VO, e1, V[0]);
+                        }
                     }
                 }
                 tc_store_half(buf, tid, half, lam);
@@ -207,8 +240,9 @@ __global__ void __launch_bounds__(TC_NT) k_leg_synth_tc(LegArgs<float> a)
         }
         if (t + 1 < T) {
             // the other buffer is free once the MMAs of tile t-1 have completed
-            if (t >= 1) ok &= tc::mbar_wait(&s_mbar[(t + 1) & 1], ((t - 1) >> 1) & 1, kWaitLimit);
-            tc_stage<RG>(a, m, mbase, r0, lt + TCT, smem + ((t + 1) & 1) * S::BUF, cf_all + ((t + 1) & 1) * TCT);
+            if (t >= 1) ok &= tc::mbar_wait(&s_mbar[(t + 1) & 1], ((t - 1) >> 1) & 1, kWaitLimit, a.err);
+            tc_stage<RG>(a, m, mbase, r0, lt + TCT, smem + ((t + 1) & 1) * S::BUF, cf_all + ((t + 1) & 1) * TCT,
+                         cfd_all + ((t + 1) & 1) * TCT, blk_diff);
         }
         tc::fence_async_smem();
         tc::fence_before();
@@ -232,7 +266,10 @@ __global__ void __launch_bounds__(TC_NT) k_leg_synth_tc(LegArgs<float> a)
         }
     }
     if (active) {
-        ok &= tc::mbar_wait(&s_mbar[(T - 1) & 1], ((T - 1) >> 1) & 1, kWaitLimit);
+        // the last two commits (tiles T-2 and T-1, one per barrier; earlier ones were waited for in
+        // the loop), so that no arrival is pending when the barriers are invalidated
+        if (T >= 2) ok &= tc::mbar_wait(&s_mbar[(T - 2) & 1], ((T - 2) >> 1) & 1, kWaitLimit, a.err);
+        ok &= tc::mbar_wait(&s_mbar[(T - 1) & 1], ((T - 1) >> 1) & 1, kWaitLimit, a.err);
         tc::fence_after();
         if (!ok && a.err) atomicExch(a.err, 1);
     }
@@ -288,12 +325,75 @@ __global__ void __launch_bounds__(TC_NT) k_leg_synth_tc(LegArgs<float> a)
             if (m > 0) a.phi[AKRA_IX(pb - m, pbound, kDbgPhiWrite)] = make_float2(gr, -gi);
         }
     }
-    if (active) {
-        tc::fence_before();
-        __syncthreads();
-        tc::fence_after();
-        if (warp == 0) tc::tmem_dealloc(tmem, S::NCOL);
+    // every thread's TMEM loads (and, for the next item, its shared-memory reads) come before
+    // the next item's set-up
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    if (active && tid == 0) {
+        tc::mbar_inval(&s_mbar[0]);
+        tc::mbar_inval(&s_mbar[1]);
     }
+    __syncthreads();
+}
+
+// TMEM columns of the block, allocated by warp 0 (which then gives up the block's permit)
+template <int RG>
+__device__ __forceinline__ uint32_t tc_block_alloc(uint32_t *s_tmem)
+{
+    if (threadIdx.x < 32) tc::tmem_alloc(s_tmem, TcSynth<RG>::NCOL);
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    return *s_tmem;
+}
+
+template <int RG>
+__device__ __forceinline__ void tc_block_free(uint32_t tmem)
+{
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    if (threadIdx.x < 32) tc::tmem_dealloc(tmem, TcSynth<RG>::NCOL);
+}
+
+template <int RG>
+__global__ void __launch_bounds__(TC_NT) k_leg_synth_tc(LegArgs<float> a)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(8) uint64_t s_mbar[2];
+    __shared__ uint32_t s_tmem;
+    if (a.skip && *a.skip) return;
+    const uint32_t tmem = tc_block_alloc<RG>(&s_tmem);
+    const int m = blockIdx.x / a.nchunks;
+    tc_synth_item<RG>(a, m, blockIdx.x - m * a.nchunks, blockIdx.y * RG, smem, s_mbar, tmem);
+    tc_block_free<RG>(tmem);
+}
+
+// persistent form over several plans: blocks take (instance, m, chunk, RHS group) items from a
+// queue ordered by cost
+template <int RG>
+__global__ void __launch_bounds__(TC_NT)
+k_leg_synth_tc_queue(const LegArgs<float> *__restrict__ insts, const int4 *__restrict__ items, int nitems,
+                     int *counter)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(8) uint64_t s_mbar[2];
+    __shared__ uint32_t s_tmem;
+    __shared__ int s_it;
+    const uint32_t tmem = tc_block_alloc<RG>(&s_tmem);
+    for (;;) {
+        if (threadIdx.x == 0) s_it = atomicAdd(counter, 1);
+        __syncthreads();
+        const int it = s_it;
+        __syncthreads();
+        if (it >= nitems) break;
+        const int4 w = items[it];
+        const LegArgs<float> &a = insts[w.x];
+        if (a.skip && *a.skip) continue;
+        tc_synth_item<RG>(a, w.y, w.z, w.w * RG, smem, s_mbar, tmem);
+    }
+    tc_block_free<RG>(tmem);
 }
 
 template <int RG>
@@ -303,7 +403,6 @@ static akra_status launch_synth_tc(akra_plan p, LegMode mode, const void *alm, v
     LegArgs<float> a = leg_args<float>(p, LegShape{1, TC_NT, RG}, mode, units, nunits, R);
     a.alm = (const float2 *)alm;
     a.phi = (float2 *)phi;
-    a.err = p->d_tc_err;
     dim3 grid((unsigned)(p->lmax + 1) * a.nchunks, (R + RG - 1) / RG);
     k_leg_synth_tc<RG><<<grid, TC_NT, TcSynth<RG>::SMEM, st>>>(a);
     AKRA_CUDA_TRY(cudaGetLastError());
@@ -314,11 +413,43 @@ static akra_status launch_synth_tc(akra_plan p, LegMode mode, const void *alm, v
 // the shared-memory opt-in of the tensor-core kernels (at plan creation, never inside a capture)
 akra_status legendre_tc_prepare()
 {
-    AKRA_CUDA_TRY(cudaFuncSetAttribute(k_leg_synth_tc<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcSynth<4>::SMEM));
-    AKRA_CUDA_TRY(cudaFuncSetAttribute(k_leg_synth_tc<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcSynth<8>::SMEM));
-    AKRA_CUDA_TRY(cudaFuncSetAttribute(k_leg_synth_tc<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcSynth<16>::SMEM));
-    AKRA_CUDA_TRY(cudaFuncSetAttribute(k_leg_synth_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcSynth<32>::SMEM));
+#define AKRA_TC_ATTR(G)                                                                                  \
+    AKRA_CUDA_TRY(cudaFuncSetAttribute(k_leg_synth_tc<G>, cudaFuncAttributeMaxDynamicSharedMemorySize,      \
+                                       TcSynth<G>::SMEM));                                               \
+    AKRA_CUDA_TRY(cudaFuncSetAttribute(k_leg_synth_tc_queue<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                       TcSynth<G>::SMEM));
+    AKRA_TC_ATTR(4) AKRA_TC_ATTR(8) AKRA_TC_ATTR(16) AKRA_TC_ATTR(32)
+#undef AKRA_TC_ATTR
     return AKRA_OK;
+}
+
+// persistent tensor-core synthesis over a batch's item list (akra_batch.cu)
+template <int RG>
+static akra_status launch_tc_queue(const LegArgs<float> *insts, const int4 *items, int nitems, int *counter,
+                                   cudaStream_t st)
+{
+    int dev = 0, nsm = 1, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_leg_synth_tc_queue<RG>, TC_NT, TcSynth<RG>::SMEM);
+    const int grid = std::max(1, std::min(nitems, nsm * std::max(per_sm, 1)));
+    k_leg_synth_tc_queue<RG><<<grid, TC_NT, TcSynth<RG>::SMEM, st>>>(insts, items, nitems, counter);
+    AKRA_CUDA_TRY(cudaGetLastError());
+    return AKRA_OK;
+}
+
+akra_status legendre_synth_tc_queue(int tcg, const LegArgs<float> *insts, const int4 *items, int nitems,
+                                    int *counter, cudaStream_t st)
+{
+    switch (tcg) {
+    case 4: return launch_tc_queue<4>(insts, items, nitems, counter, st);
+    case 8: return launch_tc_queue<8>(insts, items, nitems, counter, st);
+    case 16: return launch_tc_queue<16>(insts, items, nitems, counter, st);
+    case 32: return launch_tc_queue<32>(insts, items, nitems, counter, st);
+    default:
+        set_error("no tensor-core synthesis for an RHS group of %d", tcg);
+        return AKRA_EINVAL;
+    }
 }
 
 // FP32 synthesis with the tensor-core contraction, RHS in groups of tcg (4, 8, 16 or 32)

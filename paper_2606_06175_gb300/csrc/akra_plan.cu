@@ -1,6 +1,7 @@
 // akra_plan.cu -- plan creation (HEALPix ring geometry, recurrence coefficients, ring
 // twiddles), pixel weights, operator composition and the C entry points for the
 // transforms and H.  The CG entry points live in akra_cg.cu.
+#include <complex>
 #include <cstdarg>
 #include <cstring>
 #include <algorithm>
@@ -83,9 +84,13 @@ __global__ void k_geometry(int N, RingInfo *rings, UnitInfo *units)
 //   sλ_{l+1} = (A_l x + s A_l m/(l(l+1))) sλ_l - A_l B_l sλ_{l-1}
 //   A_l = sqrt((2l+3)/(2l+1)) (l+1)(2l+1) / sqrt(((l+1)^2-m^2)((l+1)^2-4))
 //   B_l = sqrt((l^2-m^2)(l^2-4))/(l(2l+1)) sqrt((2l+1)/(2l-1))   (0 at l = l0)
-// stored in monic form: with sλ_l = σ_l μ_l, σ_{l0} = σ_{l0+1} = 1, σ_{l+1} = A_l B_l σ_{l-1},
-//   μ_{l+1} = (A'_l x ± c'_l) μ_l - μ_{l-1},  A'_l = A_l σ_l/σ_{l+1},  c'_l = A_l (2m/(l(l+1))) σ_l/σ_{l+1}
-// (σ stays within [0.17, 1] up to lmax 4096).  Entry {A', c', σ_l, 0}.  One thread per m.
+// stored in monic form: with sλ_l = σ_l μ_l, σ_{l0} = 1, σ_{l0+1} = κ, σ_{l+1} = A_l B_l σ_{l-1},
+//   μ_{l+1} = (A'_l x ± c'_l) μ_l - μ_{l-1},  A'_l = A_l σ_l/σ_{l+1},  c'_l = A_l (2m/(l(l+1))) σ_l/σ_{l+1}.
+// σ_{l+1} = A_l B_l σ_{l-1} fixes each parity chain up to its start value; κ (the odd chain's)
+// is chosen so that σ_lmax = σ_{lmax-1}, which makes the scale smooth in l (A'_l -> 2 as l grows
+// instead of alternating between two values).  Near the poles (x -> 1) the step of a smooth
+// monic recurrence, μ_{l+1} - μ_l, is then small, which the difference form of the FP32 kernels
+// relies on.  Entry {A', c', σ_l, A' - 2} (A' - 2 formed in FP64).  One thread per m.
 __global__ void k_coef(int L, double4_32a *c64, float4 *c32)
 {
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
@@ -96,20 +101,36 @@ __global__ void k_coef(int L, double4_32a *c64, float4 *c32)
         c64[mbase + l] = make_double4_32a(0.0, 0.0, 0.0, 0.0);
         c32[mbase + l] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    double sig_prev = 1.0, sig = 1.0;   // σ_{l-1}, σ_l
     const double mm = (double)m * m;
-    for (int l = l0; l <= L; l++) {
+    auto AB = [&](int l, double &A, double &B) {
         const double dl = l, lp1 = l + 1.0;
-        const double A = sqrt((2 * dl + 3) / (2 * dl + 1)) * lp1 * (2 * dl + 1) /
-                         sqrt((lp1 * lp1 - mm) * (lp1 * lp1 - 4.0));
-        const double B = (l == l0) ? 0.0
-                                   : sqrt((dl * dl - mm) * (dl * dl - 4.0)) / (dl * (2 * dl + 1)) *
-                                         sqrt((2 * dl + 1) / (2 * dl - 1));
-        const double sig_next = (l == l0) ? 1.0 : A * B * sig_prev;
+        A = sqrt((2 * dl + 3) / (2 * dl + 1)) * lp1 * (2 * dl + 1) / sqrt((lp1 * lp1 - mm) * (lp1 * lp1 - 4.0));
+        B = (l == l0) ? 0.0
+                      : sqrt((dl * dl - mm) * (dl * dl - 4.0)) / (dl * (2 * dl + 1)) * sqrt((2 * dl + 1) / (2 * dl - 1));
+    };
+    // pass 1: both chains with unit start values, to σ_lmax and σ_{lmax-1}
+    double kappa = 1.0;
+    if (L > l0) {
+        double sig_prev = 1.0, sig = 1.0;   // σ_{l-1}, σ_l
+        for (int l = l0; l < L; l++) {
+            double A, B;
+            AB(l, A, B);
+            const double sig_next = (l == l0) ? 1.0 : A * B * sig_prev;
+            sig_prev = sig;
+            sig = sig_next;
+        }
+        // now sig = σ_L, sig_prev = σ_{L-1}; the chain of l0 + 1 is the one scaled by κ
+        kappa = ((L - l0) & 1) ? sig_prev / sig : sig / sig_prev;
+    }
+    double sig_prev = 1.0, sig = 1.0;
+    for (int l = l0; l <= L; l++) {
+        double A, B;
+        AB(l, A, B);
+        const double sig_next = (l == l0) ? kappa : A * B * sig_prev;
         const double r = sig / sig_next;
-        const double a = A * r, c = A * 2.0 * m / (dl * (dl + 1)) * r;
+        const double a = A * r, c = A * 2.0 * m / ((double)l * (l + 1.0)) * r;
         c64[mbase + l] = make_double4_32a(a, c, sig, 0.0);
-        c32[mbase + l] = make_float4((float)a, (float)c, (float)sig, 0.f);
+        c32[mbase + l] = make_float4((float)a, (float)c, (float)sig, (float)(a - 2.0));
         sig_prev = sig;
         sig = sig_next;
     }
@@ -161,7 +182,7 @@ __device__ void seed_values(int m, double Cm, double ls, double lc, int Q, doubl
 // Σ_m (lmax + 1 - g) that the kernels take.
 __global__ void k_start_states(int L, int nunit, const double *seedC, const UnitInfo *units,
                                const double4_32a *coef, float4 *s32, double4_32a *s64,
-                               int2 *g32, int2 *g64, unsigned long long *steps)
+                               int2 *g32, int2 *g64, unsigned long long *steps, float2 *d32)
 {
     const int m = blockIdx.y;
     const int u = blockIdx.x * blockDim.x + threadIdx.x;
@@ -205,6 +226,8 @@ __global__ void k_start_states(int L, int nunit, const double *seedC, const Unit
             const int sh = Scale<double>::Q * ge - Scale<float>::Q * e32;
             s32[o] = make_float4((float)ldexp(gp, sh), (float)ldexp(gm, sh), (float)ldexp(gpo, sh),
                                  (float)ldexp(gmo, sh));
+            // the difference form starts from (μ_g, μ_g - μ_{g-1}), the difference taken in FP64
+            d32[o] = make_float2((float)ldexp(gp - gpo, sh), (float)ldexp(gm - gmo, sh));
             g32[o] = make_int2(gl, e32);
             atomicAdd(&steps[u], (unsigned long long)(L + 1 - gl));
             break;
@@ -225,6 +248,7 @@ __global__ void k_start_states(int L, int nunit, const double *seedC, const Unit
     }
     if (l > L) {
         s32[o] = make_float4(0.f, 0.f, 0.f, 0.f);
+        d32[o] = make_float2(0.f, 0.f);
         g32[o] = make_int2(kNeverLive, 0);
         if (!have64) {
             s64[o] = make_double4_32a(0.0, 0.0, 0.0, 0.0);
@@ -307,7 +331,10 @@ __global__ void k_weights(const RingInfo *rings, const double *ninv, double omeg
     }
 }
 
-// radices of n = 4i: odd primes first (direct passes, smallest Ns), then 4s and a 2
+// radices of n = 4i: odd primes below kBluePrime first (direct passes, smallest Ns), then 4s
+// and a 2; a prime >= kBluePrime (at most one: two would exceed 4 nside) is left for a last,
+// Bluestein pass, where each of its length-p transforms reads and writes only its own strided
+// positions of the ring
 static FftFactors factorize(int n)
 {
     FftFactors f{};
@@ -318,9 +345,65 @@ static FftFactors factorize(int n)
     for (int d = 3; (long long)d * d <= m; d += 2)
         while (m % d == 0) { big.push_back(d); m /= d; }
     if (m > 1) big.push_back(m);
-    for (int d : big) f.f[f.nf++] = d;
+    for (int d : big) {
+        if (d >= kBluePrime) f.blue_p = d;
+        else f.f[f.nf++] = d;
+    }
     for (int d : small) f.f[f.nf++] = d;
+    if (f.blue_p) {
+        f.blue_M = 1;
+        while (f.blue_M < 2 * f.blue_p - 1) f.blue_M *= 2;
+    }
     return f;
+}
+
+// in-place radix-2 DFT on the host, out_k = Σ_j x_j e^{sign 2πi jk/M} (M a power of two)
+static void host_fft(std::vector<std::complex<double>> &x, int sign)
+{
+    const int M = (int)x.size();
+    for (int i = 1, j = 0; i < M; i++) {
+        int bit = M >> 1;
+        for (; j & bit; bit >>= 1) j ^= bit;
+        j ^= bit;
+        if (i < j) std::swap(x[i], x[j]);
+    }
+    for (int len = 2; len <= M; len <<= 1) {
+        for (int i = 0; i < M; i += len)
+            for (int k = 0; k < len / 2; k++) {
+                double sn, cs;
+                sincospi(sign * 2.0 * k / len, &sn, &cs);
+                const std::complex<double> w(cs, sn), u = x[i + k], v = x[i + k + len / 2] * w;
+                x[i + k] = u + v;
+                x[i + k + len / 2] = u - v;
+            }
+    }
+}
+
+// Bluestein tables of prime p with convolution length M: h_q = e^{iπ q²/p} (q < p) and, for
+// each transform sign s = ±1, G_s = DFT^-_M(g_s) with g_s[k] = e^{-s iπ k²/p} at k and M - k
+// (|k| < p), so that Σ_q z_q e^{s 2πi qr/p} = h_r^s · (1/M) DFT^+_M(DFT^-_M(z h^s) · G_s)[r]
+// (h^+ = h, h^- = conj(h)).  Phases from q² mod 2p, exact in integers.
+static void blue_tables(int p, int M, std::vector<double2> &out)
+{
+    auto cis = [&](long long t) {   // e^{iπ t / p}
+        double sn, cs;
+        sincospi((double)(t % (2LL * p)) / p, &sn, &cs);
+        return std::complex<double>(cs, sn);
+    };
+    for (int q = 0; q < p; q++) {
+        const std::complex<double> h = cis((long long)q * q);
+        out.push_back(make_double2(h.real(), h.imag()));
+    }
+    for (int s : {1, -1}) {
+        std::vector<std::complex<double>> g(M, 0.0);
+        for (int k = 0; k < p; k++) {
+            const std::complex<double> v = s > 0 ? std::conj(cis((long long)k * k)) : cis((long long)k * k);
+            g[k] = v;
+            if (k > 0) g[M - k] = v;
+        }
+        host_fft(g, -1);
+        for (int k = 0; k < M; k++) out.push_back(make_double2(g[k].real(), g[k].imag()));
+    }
 }
 
 akra_status ws_reserve(akra_plan p, Workspace &w, size_t bytes)
@@ -350,8 +433,9 @@ akra_status tc_error_check(akra_plan p)
     AKRA_CUDA_TRY(cudaMemcpy(&h, p->d_tc_err, sizeof(int), cudaMemcpyDeviceToHost));
     if (!h) return AKRA_OK;
     AKRA_CUDA_TRY(cudaMemset(p->d_tc_err, 0, sizeof(int)));
-    set_error("a tensor-core completion wait of the FP32 synthesis ran out of its bound: the FP32 "
-              "operator results since the last blocking call are invalid");
+    set_error("a bounded wait inside an FP32 Legendre kernel (tensor-core completion or the "
+              "adjoint's tile hand-over) ran out: the FP32 operator results since the last "
+              "blocking call are invalid");
     return AKRA_ECUDA;
 }
 
@@ -478,6 +562,7 @@ static akra_status plan_build(akra_plan p)
     AKRA_TRY(dev_alloc(p, &p->d_seedC, sizeof(double) * (L + 1)));
     AKRA_TRY(dev_alloc(p, &p->d_D64, sizeof(double) * (L + 1)));
     AKRA_TRY(dev_alloc(p, &p->d_seed32, sizeof(float4) * (size_t)(L + 1) * p->nunit));
+    AKRA_TRY(dev_alloc(p, &p->d_dseed32, sizeof(float2) * (size_t)(L + 1) * p->nunit));
     AKRA_TRY(dev_alloc(p, &p->d_seed64, sizeof(double4_32a) * (size_t)(L + 1) * p->nunit));
     AKRA_TRY(dev_alloc(p, &p->d_start32, sizeof(int2) * (size_t)(L + 1) * p->nunit));
     AKRA_TRY(dev_alloc(p, &p->d_start64, sizeof(int2) * (size_t)(L + 1) * p->nunit));
@@ -500,9 +585,26 @@ static akra_status plan_build(akra_plan p)
     AKRA_CUDA_TRY(cudaMemset(p->d_tc_err, 0, sizeof(int)));
 
     std::vector<FftFactors> fac(N + 1);
-    for (int i = 1; i <= N; i++) fac[i] = factorize(4 * i);
+    std::vector<double2> blue;
+    std::map<int, long long> blue_at;   // prime -> table offset
+    for (int i = 1; i <= N; i++) {
+        fac[i] = factorize(4 * i);
+        const int bp = fac[i].blue_p;
+        if (!bp) continue;
+        auto it = blue_at.find(bp);
+        if (it == blue_at.end()) {
+            it = blue_at.emplace(bp, (long long)blue.size()).first;
+            blue_tables(bp, fac[i].blue_M, blue);
+        }
+        fac[i].blue_off = it->second;
+    }
     AKRA_CUDA_TRY(cudaMemcpy(p->d_factors, fac.data(), sizeof(FftFactors) * (N + 1),
                              cudaMemcpyHostToDevice));
+    if (!blue.empty()) {
+        AKRA_TRY(dev_alloc(p, &p->d_blue64, sizeof(double2) * blue.size()));
+        AKRA_CUDA_TRY(cudaMemcpy(p->d_blue64, blue.data(), sizeof(double2) * blue.size(),
+                                 cudaMemcpyHostToDevice));
+    }
     const int nthr = 256;
     k_geometry<<<(p->nring + nthr - 1) / nthr, nthr>>>(N, p->d_rings, p->d_units);
     AKRA_CUDA_TRY(cudaGetLastError());
@@ -513,7 +615,7 @@ static akra_status plan_build(akra_plan p)
     AKRA_CUDA_TRY(cudaMemset(p->d_steps, 0, sizeof(unsigned long long) * 2 * p->nunit));
     k_start_states<<<dim3((p->nunit + 127) / 128, L + 1), 128>>>(
         L, p->nunit, p->d_seedC, p->d_units, p->d_coef64, p->d_seed32, p->d_seed64, p->d_start32,
-        p->d_start64, p->d_steps);
+        p->d_start64, p->d_steps, p->d_dseed32);
     AKRA_CUDA_TRY(cudaGetLastError());
     p->steps32.assign(p->nunit, 0);
     p->steps64.assign(p->nunit, 0);
@@ -589,7 +691,7 @@ extern "C" void akra_plan_destroy(akra_plan p)
                     p->d_fft32_off, p->d_fft32_tw2, p->d_fft32_bhat, p->d_seed32, p->d_seed64,
                     p->d_start32, p->d_start64, p->d_steps, p->d_pw64, p->d_pw32, p->d_ftw64,
                     p->d_ftw32, p->d_fWt64, p->d_fWt32,
-                    p->d_fft32_rings_all, p->d_fft32_rings_act, p->d_tc_err};
+                    p->d_fft32_rings_all, p->d_fft32_rings_act, p->d_tc_err, p->d_dseed32, p->d_blue64};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     if (p->stream) cudaStreamDestroy(p->stream);

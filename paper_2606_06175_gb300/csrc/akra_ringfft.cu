@@ -9,9 +9,14 @@
 // Transpose direction (w_j = W_j f_j or the caller's map):
 //   Φ'(m) = Σ_j w_j e^{-imφ_j} = e^{-iπσk/n} (-1)^{σq} Σ_j w_j e^{-2πijk/n},  m = k + nq.
 // The length-n DFTs run in shared memory, one CTA per ring: a mixed-radix Stockham
-// autosort with radices 4 and 2 as register butterflies and every odd prime factor as a
-// direct (output-oriented) pass; every pass reads all its inputs into registers,
-// synchronises, then writes in place.  Twiddles come from the plan's per-length table e^{iπt/n}, t < 2n.
+// autosort with radices 4 and 2 as register butterflies and every odd prime factor below 67
+// as a direct (output-oriented) pass; every pass reads all its inputs into registers,
+// synchronises, then writes in place.  A prime factor p >= 67 (polar rings n = 4i with such a
+// p in i) is the last pass, Bluestein's chirp-z form: each of its n/p length-p transforms reads
+// and writes only the positions j + Ns r of the ring, and is a cyclic convolution of
+// power-of-two length M >= 2p - 1 done with two length-M FFTs in a shared-memory scratch
+// (O(p log p) instead of the direct pass's O(p^2)).  Twiddles come from the plan's per-length
+// table e^{iπt/n}, t < 2n (the length-M ones from the table of the ring length M).
 #include "akra_internal.cuh"
 
 namespace akra {
@@ -124,9 +129,60 @@ __device__ void pass_generic(cx_t<T> *data, int n, int Ns, int p, const cx_t<T> 
     __syncthreads();
 }
 
+// power-of-two length M in shared memory (radix 4 passes and a 2), twiddles of length M
+template <typename T, int DIR>
+__device__ void fft_pow2(cx_t<T> *data, int M, const cx_t<T> *__restrict__ twM)
+{
+    int Ns = 1;
+    for (; Ns * 4 <= M; Ns *= 4) pass_small<T, 4, DIR>(data, M, Ns, twM);
+    if (Ns < M) pass_small<T, 2, DIR>(data, M, Ns, twM);
+}
+
+// the last pass of length-n transform for a prime p = n / Ns >= kBluePrime: for each
+// j < Ns, Z_r = Σ_q x[j + q Ns] e^{DIR 2πi qj/n} e^{DIR 2πi qr/p} -> x[j + r Ns], by
+// Bluestein: with h_q = e^{DIR iπ q²/p}, Z_r = h_r (1/M) DFT+(DFT-(a) · G)[r], a_q = x' h_q
+template <typename T, int DIR>
+__device__ void pass_bluestein(cx_t<T> *data, int n, const FftFactors &fac, const cx_t<T> *__restrict__ tw,
+                               const cx_t<T> *__restrict__ twM, const cx_t<T> *__restrict__ blue, cx_t<T> *scratch)
+{
+    using C2 = cx_t<T>;
+    const int p = fac.blue_p, M = fac.blue_M, Ns = n / p;
+    const C2 *h = blue + fac.blue_off;                     // h_q, q < p
+    const C2 *G = h + p + (DIR > 0 ? 0 : M);               // G for this transform sign
+    const T invM = T(1) / (T)M;
+    for (int j = 0; j < Ns; j++) {
+        for (int q = threadIdx.x; q < M; q += FFT_NT) {
+            C2 v{0, 0};
+            if (q < p) {
+                v = data[j + q * Ns];
+                if (j) v = cmul<T>(v, twid<T, DIR>(tw, (int)((2LL * q * j) % (2 * n))));
+                C2 hq = h[q];
+                if (DIR < 0) hq.y = -hq.y;
+                v = cmul<T>(v, hq);
+            }
+            scratch[q] = v;
+        }
+        __syncthreads();
+        fft_pow2<T, -1>(scratch, M, twM);
+        for (int f = threadIdx.x; f < M; f += FFT_NT) scratch[f] = cmul<T>(scratch[f], G[f]);
+        __syncthreads();
+        fft_pow2<T, +1>(scratch, M, twM);
+        for (int r = threadIdx.x; r < p; r += FFT_NT) {
+            C2 hr = h[r];
+            if (DIR < 0) hr.y = -hr.y;
+            C2 v = cmul<T>(scratch[r], hr);
+            v.x *= invM;
+            v.y *= invM;
+            data[j + r * Ns] = v;
+        }
+        __syncthreads();
+    }
+}
+
 template <typename T, int DIR>
 __device__ void fft_inplace(cx_t<T> *data, int n, const FftFactors &fac,
-                            const cx_t<T> *__restrict__ tw)
+                            const cx_t<T> *__restrict__ tw, const cx_t<T> *__restrict__ tw_all,
+                            const cx_t<T> *__restrict__ blue, cx_t<T> *scratch)
 {
     int Ns = 1;
     for (int i = 0; i < fac.nf; i++) {
@@ -138,6 +194,11 @@ __device__ void fft_inplace(cx_t<T> *data, int n, const FftFactors &fac,
         }
         Ns *= R;
     }
+    if (fac.blue_p) {
+        // twiddles of length M = 4i sit at offset 4 i (i - 1) of the plan's table
+        const long long iM = fac.blue_M / 4;
+        pass_bluestein<T, DIR>(data, n, fac, tw, tw_all + 4 * iM * (iM - 1), blue, scratch);
+    }
 }
 
 __device__ __forceinline__ int floordiv(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
@@ -148,13 +209,14 @@ k_ring_fft(int L, int nring, long long npix, int nmax, const int *__restrict__ r
            const RingInfo *__restrict__ rinfo, const FftFactors *__restrict__ factors,
            const cx_t<T> *__restrict__ tw_all, const T *__restrict__ W, int weighted,
            cx_t<T> *__restrict__ phi, const T *__restrict__ map_in, T *__restrict__ map_out,
-           const int *__restrict__ skip)
+           const int *__restrict__ skip, const cx_t<T> *__restrict__ blue)
 {
     using C2 = cx_t<T>;
     if (skip && *skip) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C2 *data = reinterpret_cast<C2 *>(smem_raw);
     C2 *red = data + nmax;
+    C2 *scratch = red + FFT_NT;   // Bluestein convolution buffer (when the plan has one)
     const int ring = rings ? rings[blockIdx.x] : (int)blockIdx.x;
     const int r = blockIdx.y;
     const int tid = threadIdx.x;
@@ -204,7 +266,7 @@ k_ring_fft(int L, int nring, long long npix, int nmax, const int *__restrict__ r
             }
         }
         __syncthreads();
-        fft_inplace<T, +1>(data, n, fac, tw);
+        fft_inplace<T, +1>(data, n, fac, tw, tw_all, blue, scratch);
         if (MODE == (int)FftMode::Synth) {
             T *o1 = map_out + ((size_t)r * 2 + 0) * npix + first;
             T *o2 = map_out + ((size_t)r * 2 + 1) * npix + first;
@@ -240,7 +302,7 @@ k_ring_fft(int L, int nring, long long npix, int nmax, const int *__restrict__ r
         }
         __syncthreads();
     }
-    fft_inplace<T, -1>(data, n, fac, tw);
+    fft_inplace<T, -1>(data, n, fac, tw, tw_all, blue, scratch);
     // unfold: Φ'(m) = e^{-iπσk/n} (-1)^{σq} Ŵ[k],  m = k + nq
     for (int mm = tid; mm < 2 * L + 1; mm += FFT_NT) {
         const int m = mm - L;
@@ -263,17 +325,42 @@ template <typename T> const T *W_ptr(akra_plan p);
 template <> const float *W_ptr<float>(akra_plan p) { return p->d_W32; }
 template <> const double *W_ptr<double>(akra_plan p) { return p->d_W64; }
 
+// largest Bluestein convolution length of the plan's ring lengths (0: none)
+static int blue_maxM(akra_plan p)
+{
+    int mx = 0;
+    for (int i = 1; i <= p->nside; i++) {
+        const int n = 4 * i;
+        int m = i;
+        while (m % 2 == 0) m /= 2;
+        int big = 0;
+        for (int d = 3; d * d <= m; d += 2)
+            while (m % d == 0) m /= d;
+        if (m > 1) big = m;
+        (void)n;
+        if (big >= kBluePrime) {
+            int M = 1;
+            while (M < 2 * big - 1) M *= 2;
+            mx = M > mx ? M : mx;
+        }
+    }
+    return mx;
+}
+
 template <typename T, int MODE>
 static akra_status launch_fft(akra_plan p, void *phi, const void *map_in, void *map_out,
                               bool weighted, int R, const int *rings, int nrings, cudaStream_t st)
 {
     const int nmax = 4 * p->nside;
-    const size_t smem = (size_t)(nmax + FFT_NT) * sizeof(cx_t<T>);
+    const bool dbl = sizeof(T) == sizeof(double);
+    const int mblue = dbl ? blue_maxM(p) : 0;
+    const size_t smem = (size_t)(nmax + FFT_NT + mblue) * sizeof(cx_t<T>);
     auto kern = k_ring_fft<T, MODE>;
     dim3 grid(nrings, R);
     kern<<<grid, FFT_NT, smem, st>>>(p->lmax, p->nring, p->npix, nmax, rings, p->d_rings,
                                      p->d_factors, tw_ptr<T>(p), W_ptr<T>(p), weighted ? 1 : 0,
-                                     (cx_t<T> *)phi, (const T *)map_in, (T *)map_out, p->cur_skip);
+                                     (cx_t<T> *)phi, (const T *)map_in, (T *)map_out, p->cur_skip,
+                                     dbl ? (const cx_t<T> *)p->d_blue64 : nullptr);
     AKRA_CUDA_TRY(cudaGetLastError());
     p->launches++;
     return AKRA_OK;
@@ -304,7 +391,8 @@ akra_status ring_fft_prepare(akra_plan p)
     (void)p;
     const int nmax = FFT_NMAX;
     const int s32 = (nmax + FFT_NT) * (int)sizeof(float2);
-    const int s64 = (nmax + FFT_NT) * (int)sizeof(double2);
+    // FP64: + the Bluestein scratch of the largest prime below kMaxNside (M = 4096)
+    const int s64 = (nmax + FFT_NT + 4096) * (int)sizeof(double2);
     AKRA_CUDA_TRY(cudaFuncSetAttribute(k_ring_fft<float, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, s32));
     AKRA_CUDA_TRY(cudaFuncSetAttribute(k_ring_fft<float, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, s32));
     AKRA_CUDA_TRY(cudaFuncSetAttribute(k_ring_fft<float, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, s32));

@@ -58,12 +58,20 @@ __device__ __forceinline__ void mbar_init(uint64_t *mbar, int count)
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(mbar)), "r"(count));
 }
 
-// wait for the completion of the mbarrier phase with the given parity, at most `limit` polls;
-// returns false on timeout (the caller records an error instead of waiting forever)
-__device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t parity, int limit)
+// an mbarrier with no pending arrivals goes back to plain shared memory (before a re-init)
+__device__ __forceinline__ void mbar_inval(uint64_t *mbar)
+{
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" :: "r"(smem_u32(mbar)) : "memory");
+}
+
+// wait for the completion of the mbarrier phase with the given parity, at most `limit` polls,
+// and not at all once the launch's error flag is set; returns false on timeout (the caller
+// records an error instead of waiting forever)
+__device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t parity, int limit, const int *err)
 {
     uint32_t done = 0;
     for (int it = 0; it < limit; it++) {
+        if (err && (it & 1023) == 1023 && *(volatile const int *)err) return false;
         asm volatile("{\n\t.reg .pred q;\n\tmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\n\t"
                      "selp.u32 %0, 1, 0, q;\n\t}"
                      : "=r"(done) : "r"(smem_u32(mbar)), "r"(parity) : "memory");

@@ -35,9 +35,33 @@ def main():
                     help="force the Legendre tile shape of --prec (R = 1)")
     ap.add_argument("--cufft", action="store_true",
                     help="time the FP32 ring-FFT stage against cuFFT on the same rings")
+    ap.add_argument("--autotune", action="store_true", help="autotune the tile shapes of --prec first")
+    ap.add_argument("--tc", type=int, default=0, metavar="G",
+                    help="FP32 synthesis on the tensor core with RHS groups of G (with --rhs)")
+    ap.add_argument("--rhs", type=int, default=1, help="right-hand sides of the H applications")
+    ap.add_argument("--batch", action="store_true",
+                    help="one batched FP32 H over two instances (Nside and Nside/2, --rhs RHS each) instead")
     args = ap.parse_args()
     N, L = args.nside, args.lmax
     dev = torch.device("cuda", 0)
+    if args.batch:
+        plans, xs = [], []
+        for k, (nb, lb) in enumerate(((N, L), (N // 2, L // 2))):
+            svb = S.survey(nb, "des", S.SEEDS["batch"] + k)
+            pb = A.akra_plan_create(nb, lb)
+            A.akra_plan_set_weights(pb, torch.from_numpy(svb["ninv"]).to(dev), 1e-3)
+            plans.append(pb)
+            xs.append(torch.zeros((args.rhs, 2, pb.ntri), dtype=torch.complex64, device=dev))
+        bt = A.akra_batch_create(plans, [args.rhs, args.rhs])
+        if args.autotune:
+            A.akra_batch_autotune(bt)
+        if args.tc:
+            A.akra_batch_set_tc_synthesis(bt, args.tc)
+        for _ in range(args.reps):
+            A.akra_batch_apply_H(bt, xs)
+        torch.cuda.synchronize()
+        print("ok batch", A.akra_batch_describe(bt), "tc", A.akra_batch_get_tc_synthesis(bt))
+        return
     if args.flat:
         sv = S.flat_survey(args.flat)
         fp = A.akra_flat_plan_create(args.flat)
@@ -53,8 +77,13 @@ def main():
     plan = A.akra_plan_create(N, L)
     A.akra_plan_set_weights(plan, torch.from_numpy(sv["ninv"]).to(dev), 1e-3)
     prec = A.F32 if args.prec == "f32" else A.F64
+    R = args.rhs
     if args.shape:
-        A.akra_plan_set_shape(plan, prec, 1, *args.shape)
+        A.akra_plan_set_shape(plan, prec, R, *args.shape)
+    if args.autotune:
+        A.akra_autotune(plan, prec, R)
+    if args.tc:
+        A.akra_plan_set_tc_synthesis(plan, R, args.tc)
     kE = S.grf_alm(L, S.cl_kappa(L), sv["rng_alm"])
     x64 = torch.from_numpy(np.stack([kE, np.zeros_like(kE)])[None]).to(dev)
     if args.cufft:
@@ -66,9 +95,12 @@ def main():
         print(info)
     else:
         x = x64 if prec == A.F64 else x64.to(torch.complex64)
+        x = x.repeat(R, 1, 1).contiguous()
         for _ in range(args.reps):
             A.akra_apply_H(plan, prec, x)
     torch.cuda.synchronize()
+    sh = A.akra_plan_get_shape(plan, prec, R)
+    print("shape", sh["P"], sh["PA"], sh["RG"], "tc", A.akra_plan_get_tc_synthesis(plan, R) if prec == A.F32 else 0)
     print("ok", A.akra_plan_describe(plan)["kernel_launches"])
 
 

@@ -67,6 +67,63 @@ def test_batched_H_matches_oracle():
             assert rel(yn[r], ref[r]) < tol32(L)
 
 
+@pytest.mark.parametrize("group", [4, 8, 16, 32])
+def test_batched_H_with_tensor_synthesis_matches_oracle(group):
+    """The batch's synthesis on the tensor cores (persistent queue over 128-pair chunks and RHS
+    groups of every size; R = 5, 9, 3 leave the last group of each instance partly filled)."""
+    rng = np.random.default_rng(40 + group)
+    spec = [(8, 16, 5), (32, 70, 9), (16, 40, 3)]
+    plans, xs, refs = [], [], []
+    for N, L, R in spec:
+        th, ph = O.pixel_angles(N)
+        ninv = np.where((th > 0.5) & (np.cos(2 * ph) > -0.8), 1.0 + rng.random(12 * N * N), 0.0)
+        p = A.akra_plan_create(N, L)
+        A.akra_plan_set_weights(p, torch.from_numpy(ninv).to(DEV), 1e-3)
+        pairs = [(S.random_alm(L, rng), S.random_alm(L, rng)) for _ in range(R)]
+        xs.append(torch.from_numpy(np.stack([np.stack(q) for q in pairs])).to(DEV, torch.complex64))
+        w = O.Weights(N, ninv, 1e-3)
+        refs.append([np.stack(O.apply_H(N, L, w, *q)) for q in pairs])
+        plans.append(p)
+    b = A.akra_batch_create(plans, [R for *_, R in spec])
+    A.akra_batch_set_tc_synthesis(b, group)
+    assert A.akra_batch_get_tc_synthesis(b) == group
+    for _ in range(2):   # the second pass reuses the blocks' TMEM and barriers across items
+        ys = A.akra_batch_apply_H(b, xs)
+        for (N, L, R), y, ref in zip(spec, ys, refs):
+            yn = y.to(torch.complex128).cpu().numpy()
+            for r in range(R):
+                assert rel(yn[r], ref[r]) < tol32(L), (group, N, L, r, rel(yn[r], ref[r]))
+    A.akra_batch_set_tc_synthesis(b, 0)
+    ys = A.akra_batch_apply_H(b, xs)
+    for (N, L, R), y, ref in zip(spec, ys, refs):
+        yn = y.to(torch.complex128).cpu().numpy()
+        assert max(rel(yn[r], ref[r]) for r in range(R)) < tol32(L)
+    with pytest.raises(A.AkraError):
+        A.akra_batch_set_tc_synthesis(b, 12)
+
+
+def test_batched_mixed_solve_with_tensor_synthesis():
+    inst, rng = _small_instances(3)
+    b = A.akra_batch_create([p for *_, p in inst], [R for _, _, R, _, _ in inst])
+    A.akra_batch_set_tc_synthesis(b, 4)
+    shears, refs = [], []
+    for N, L, R, ninv, p in inst:
+        ys = []
+        for _ in range(R):
+            kE = S.random_alm(L, rng, lmin=2) * 0.05
+            y = np.stack(O.forward_A(N, L, kE, np.zeros_like(kE))) + 0.01 * rng.normal(size=(2, 12 * N * N))
+            ys.append(np.where(ninv > 0, y, 0.0))
+        w = O.Weights(N, ninv, 1e-3)
+        refs.append([np.stack(O.cg_solve(N, L, w, y[0], y[1], tol=1e-12, maxiter=5000)[0]) for y in ys])
+        shears.append(torch.from_numpy(np.stack(ys)).to(DEV, torch.float64))
+    xs, infos = A.akra_batch_cg_solve(b, A.MIXED, shears, tol=1e-9, maxiter=5000)
+    for (N, L, R, _, _), x, ref, info in zip(inst, xs, refs, infos):
+        assert info["status"] == 0 and info["relres"] < 1e-9, info
+        xn = x.to(torch.complex128).cpu().numpy()
+        for r in range(R):
+            assert rel(xn[r], ref[r]) < 1e-6, (N, L, r)
+
+
 @pytest.mark.parametrize("prec", [A.MIXED, A.F32])
 def test_batched_solve_matches_oracle(prec):
     inst, rng = _small_instances(2)
