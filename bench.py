@@ -73,12 +73,12 @@ def fp32_peak_tflops(sm_count, mhz):
 
 
 def kernel_source_sha():
-    """Short hash of the Legendre kernels' source: a DRAM-traffic capture is only valid for
-    the kernel source it was taken with."""
+    """Short hash of the CUDA-core Legendre kernels' device code (scalar items and the paired
+    FP32 adjoint): a DRAM-traffic capture is only valid for the kernel code it was taken with."""
     import hashlib
 
     h = hashlib.sha256()
-    for f in ("akra_legendre_impl.cuh", "akra_legendre.cu"):
+    for f in ("akra_legendre_impl.cuh", "akra_legendre_f32x2.cuh"):
         with open(os.path.join(ROOT, "paper_2606_06175_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:12]
@@ -574,6 +574,11 @@ def main():
         "fp64_legendre": {k: {"ms": st64[k], "achieved": flops64 / (st64[k] * 1e-3) / 1e12,
                               "frac_of_nominal_fp64": flops64 / (st64[k] * 1e-3) / 1e12 / 1.25}
                           for k in ("legendre_synth", "legendre_adjoint")},
+        # counted steps / lane-steps the warps execute at the chosen shapes (start-point spread
+        # within a warp and 64-step tile granularity)
+        "lane_efficiency": {
+            "legendre_synth": A.akra_legendre_lane_steps(plan, A.F32, False, shape["P"])["efficiency"],
+            "legendre_adjoint": A.akra_legendre_lane_steps(plan, A.F32, True, shape["PA"])["efficiency"]},
     }
 
     # ---- untimed comparison blocks ----

@@ -388,6 +388,19 @@ akra_status akra_plan_get_tc_synthesis(akra_plan plan, int R, int *group);
  * the paper has no counterpart.  Errors: EINVAL, ENOMEM, ECUDA. */
 akra_status akra_fma_rate(akra_prec prec, double *tflops);
 
+/* Work accounting of one Legendre launch (diagnostic; the paper has no counterpart).  For the
+ * plan's ring pairs (its active ones once weights are set) laid out as the synthesis
+ * (adjoint = 0) or the adjoint (adjoint = 1) lays them out with P ring pairs per thread and NT
+ * threads per block, *steps = the (l, m, ring pair) steps from each pair's start point to lmax
+ * (the work counted in roofline figures; akra_plan_desc.legendre_steps_*), *lane_steps = the
+ * steps the lanes execute: a warp runs all 32 P of its slots from the first 64-step l-tile that
+ * holds its earliest start (tiles counted from the block's earliest start) to lmax.  The ratio
+ * is the fraction of executed lane-steps that carry counted work.  Blocking.
+ * Errors: EINVAL (P outside 1..64, NT not a multiple of 32 in 32..1024, flat-sky plan), ENOMEM,
+ * ECUDA. */
+akra_status akra_legendre_lane_steps(akra_plan plan, akra_prec prec, int adjoint, int P, int NT,
+                                     long long *lane_steps, long long *steps);
+
 /* Time the four stages of one H application (Legendre synthesis, ring FFT x W x FFT,
  * Legendre adjoint, epilogue) with CUDA events on `stream`, averaged over `reps` runs after
  * one warm-up, on the plan's own scratch input.  ms_out[0..3] receive the per-stage

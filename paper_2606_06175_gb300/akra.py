@@ -57,7 +57,7 @@ EXPORTS = ["akra_plan_create", "akra_plan_destroy", "akra_last_error", "akra_ver
            "akra_cg_solve_fields", "akra_shuffle_shear", "akra_cl_spectra",
            "akra_plan_set_preconditioner", "akra_flat_plan_create", "akra_plan_fill_workspaces",
            "akra_debug_violations", "akra_plan_set_tc_synthesis", "akra_plan_get_tc_synthesis",
-           "akra_batch_set_tc_synthesis", "akra_batch_get_tc_synthesis"]
+           "akra_batch_set_tc_synthesis", "akra_batch_get_tc_synthesis", "akra_legendre_lane_steps"]
 
 _lib_handle = None
 
@@ -112,6 +112,8 @@ def load(build_if_missing: bool = False):
         "akra_plan_get_tc_synthesis": ([vp, i, ctypes.POINTER(i)], i),
         "akra_batch_set_tc_synthesis": ([vp, i], i),
         "akra_batch_get_tc_synthesis": ([vp, ctypes.POINTER(i)], i),
+        "akra_legendre_lane_steps": ([vp, i, i, i, i, ctypes.POINTER(ctypes.c_longlong),
+                                      ctypes.POINTER(ctypes.c_longlong)], i),
         "akra_time_H_stages": ([vp, i, i, i, vp, ctypes.POINTER(ctypes.c_double)], i),
         "akra_synth_spin2_static": ([vp, i, vp, vp, i, vp], i),
         "akra_cg_solve_adjoint": ([vp, i, vp, vp, i, d, i, ctypes.POINTER(CgInfo), vp], i),
@@ -463,6 +465,15 @@ def akra_cl_spectra(plan: Plan, prec: int, a: torch.Tensor, b: torch.Tensor = No
     _check(load().akra_cl_spectra(plan.handle, prec, _ptr(a), _ptr(b), R, nb,
                                   e if nb else None, _ptr(out), _stream(stream)))
     return out
+
+
+def akra_legendre_lane_steps(plan: Plan, prec: int, adjoint: bool, P: int, NT: int = 128) -> dict:
+    """Executed lane-steps and counted steps of one Legendre launch with P ring pairs per thread."""
+    ls, st = ctypes.c_longlong(), ctypes.c_longlong()
+    _check(load().akra_legendre_lane_steps(plan.handle, prec, 1 if adjoint else 0, P, NT,
+                                           ctypes.byref(ls), ctypes.byref(st)))
+    return {"lane_steps": ls.value, "steps": st.value,
+            "efficiency": st.value / ls.value if ls.value else 0.0}
 
 
 def akra_fma_rate(prec: int) -> float:

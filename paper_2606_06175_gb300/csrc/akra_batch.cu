@@ -29,6 +29,7 @@ struct akra_batch_s {
     int *d_counter = nullptr;             // queue heads: synthesis, adjoint, tensor-core synthesis
     int tcg = 0;                          // tensor-core synthesis RHS group (0: CUDA-core synthesis)
     akra::LegArgs<float> *d_syn_tc = nullptr;
+    std::vector<akra::LegArgs<float>> h_syn_tc;   // host copies: the B-operand staging launches
     int4 *d_titems = nullptr;
     int ntitems = 0, titems_tcg = 0;
     int fft_mmax = 0;
@@ -149,6 +150,7 @@ static akra_status batch_reserve(akra_batch b)
                                      nch64 * R * p->ntri * 4 * sizeof(double));
         AKRA_TRY(ws_reserve(p, p->phi, (size_t)R * p->nring * (2 * (size_t)p->lmax + 1) * sizeof(double2)));
         AKRA_TRY(ws_reserve(p, p->partial, part));
+        AKRA_TRY(tc_reserve(p, b->tcg, R));
         CgBufs cb;
         AKRA_TRY(cg_reserve(p, R, cb));
     }
@@ -173,6 +175,8 @@ static akra_status batch_args(akra_batch b, void *const *x, void *const *y, cons
         syn_tc[i].alm = syn[i].alm;
         syn_tc[i].phi = syn[i].phi;
         syn_tc[i].skip = sk;
+        syn_tc[i].bpre = (const float *)p->bpre.ptr;
+        syn_tc[i].tc_groups = b->tcg > 0 ? (b->R[i] + b->tcg - 1) / b->tcg : 0;
         adj[i] = syn[i];
         adj[i].phi_in = (const float2 *)p->phi.ptr;
         adj[i].partial = (float *)p->partial.ptr;
@@ -186,6 +190,7 @@ static akra_status batch_args(akra_batch b, void *const *x, void *const *y, cons
     AKRA_CUDA_TRY(cudaMemcpyAsync(b->d_fft, fft.data(), sizeof(Fft32Args) * b->ninst, cudaMemcpyHostToDevice, st));
     AKRA_CUDA_TRY(cudaMemcpyAsync(b->d_syn_tc, syn_tc.data(), sizeof(LegArgs<float>) * b->ninst,
                                   cudaMemcpyHostToDevice, st));
+    b->h_syn_tc = syn_tc;
     // the pageable sources must stay alive until the copies have been staged
     AKRA_CUDA_TRY(cudaStreamSynchronize(st));
     return AKRA_OK;
@@ -216,7 +221,7 @@ static akra_status launch_queue(akra_batch b, int which, cudaStream_t st)
 {
     const LegShape s = b->shape;
 #define AKRA_Q(PP, RR) if (s.P == PP && s.RG == RR) return launch_queue_pair<PP, RR>(b, which, st);
-    AKRA_Q(1, 1) AKRA_Q(2, 1) AKRA_Q(4, 1) AKRA_Q(1, 2) AKRA_Q(2, 2) AKRA_Q(1, 4)
+    AKRA_Q(1, 1) AKRA_Q(2, 1) AKRA_Q(4, 1) AKRA_Q(5, 1) AKRA_Q(6, 1) AKRA_Q(1, 2) AKRA_Q(2, 2) AKRA_Q(1, 4)
 #undef AKRA_Q
     set_error("akra_batch: no kernel for P=%d RG=%d", s.P, s.RG);
     return AKRA_EINVAL;
@@ -228,6 +233,10 @@ static akra_status batch_H32(akra_batch b, void *const *x, void *const *y, const
 {
     AKRA_CUDA_TRY(cudaMemsetAsync(b->d_counter, 0, 3 * sizeof(int), st));
     if (b->tcg > 0) {
+        for (int i = 0; i < b->ninst; i++) {
+            AKRA_TRY(legendre_tc_bstage(b->tcg, b->h_syn_tc[i], st));
+            b->launches++;
+        }
         if (b->ntitems > 0) {
             AKRA_TRY(legendre_synth_tc_queue(b->tcg, b->d_syn_tc, b->d_titems, b->ntitems, b->d_counter + 2, st));
             b->launches++;
@@ -469,7 +478,8 @@ extern "C" akra_status akra_batch_autotune(akra_batch b, void *stream)
         return AKRA_EINVAL;
     }
     cudaStream_t user = (cudaStream_t)stream;
-    std::vector<LegShape> cands = {{1, 128, 4}, {2, 128, 2}, {1, 128, 2}, {4, 128, 1}, {2, 128, 1}};
+    std::vector<LegShape> cands = {{1, 128, 4}, {2, 128, 2}, {1, 128, 2}, {4, 128, 1}, {5, 128, 1}, {6, 128, 1},
+                                   {2, 128, 1}};
     const int maxR = *std::max_element(b->R.begin(), b->R.end());
     std::vector<void *> xs(b->ninst), ys(b->ninst);
     for (int i = 0; i < b->ninst; i++) {
@@ -490,51 +500,34 @@ extern "C" akra_status akra_batch_autotune(akra_batch b, void *stream)
     float best = 1e30f;
     LegShape pick = b->shape;
     int pick_tcg = b->tcg;
-    b->tcg = 0;
     akra_status s = AKRA_OK;
-    for (auto &c : cands) {
-        if (c.RG > maxR && c.RG > 1) continue;
-        b->shape = c;
-        s = batch_reserve(b);
-        if (s == AKRA_OK) s = batch_args(b, xs.data(), ys.data(), nullptr, user);
-        float tot = 0;
-        for (int rep = 0; rep < 3 && s == AKRA_OK; rep++) {
-            cudaEventRecord(e0, user);
-            s = batch_H32(b, xs.data(), ys.data(), nullptr, user);
-            cudaEventRecord(e1, user);
-            cudaEventSynchronize(e1);
-            float ms = 0;
-            cudaEventElapsedTime(&ms, e0, e1);
-            if (rep > 0) tot += ms;
-        }
-        if (s != AKRA_OK) break;
-        if (tot < best) {
-            best = tot;
-            pick = c;
-            pick_tcg = b->tcg;
-        }
-    }
-    // then the tensor-core synthesis at the best shape, for groups not more than twice the
-    // largest RHS count
-    b->shape = pick;
-    for (int g : {4, 8, 16, 32}) {
-        if (s != AKRA_OK || g > 2 * maxR || maxR < 4) break;
-        b->tcg = g;
-        s = batch_reserve(b);
-        if (s == AKRA_OK) s = batch_args(b, xs.data(), ys.data(), nullptr, user);
-        float tot = 0;
-        for (int rep = 0; rep < 3 && s == AKRA_OK; rep++) {
-            cudaEventRecord(e0, user);
-            s = batch_H32(b, xs.data(), ys.data(), nullptr, user);
-            cudaEventRecord(e1, user);
-            cudaEventSynchronize(e1);
-            float ms = 0;
-            cudaEventElapsedTime(&ms, e0, e1);
-            if (rep > 0) tot += ms;
-        }
-        if (s == AKRA_OK && tot < best) {
-            best = tot;
-            pick_tcg = g;
+    // every (tile shape, synthesis) pair: the CUDA-core synthesis (group 0) and, from R = 4 on,
+    // the tensor-core one with groups up to twice the largest RHS count (the shape then serves
+    // the adjoint alone)
+    for (int g : {0, 4, 8, 16, 32}) {
+        if (g > 0 && (maxR < 4 || g > 2 * maxR)) continue;
+        for (auto &c : cands) {
+            if (s != AKRA_OK) break;
+            if (c.RG > maxR && c.RG > 1) continue;
+            b->shape = c;
+            b->tcg = g;
+            s = batch_reserve(b);
+            if (s == AKRA_OK) s = batch_args(b, xs.data(), ys.data(), nullptr, user);
+            float tot = 0;
+            for (int rep = 0; rep < 3 && s == AKRA_OK; rep++) {
+                cudaEventRecord(e0, user);
+                s = batch_H32(b, xs.data(), ys.data(), nullptr, user);
+                cudaEventRecord(e1, user);
+                cudaEventSynchronize(e1);
+                float ms = 0;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (rep > 0) tot += ms;
+            }
+            if (s == AKRA_OK && tot < best) {
+                best = tot;
+                pick = c;
+                pick_tcg = g;
+            }
         }
     }
     cudaEventDestroy(e0);

@@ -386,6 +386,7 @@ static akra_status cg_graph(akra_plan p, int R, CgBufs &b, cudaGraphExec_t *out)
         AKRA_TRY(ws_reserve(p, p->phi, (size_t)R * p->nring * (2 * (size_t)p->lmax + 1) * sizeof(cx_t<T>)));
     const int nch = legendre_chunks(p->n_active_units, s);
     AKRA_TRY(ws_reserve(p, p->partial, (size_t)nch * R * p->ntri * 4 * sizeof(T)));
+    if (PrecIdx<T>::v == 1 && !is_flat(p)) AKRA_TRY(tc_reserve(p, s.TC, R));
     AKRA_TRY(cg_reserve(p, R, b));   // pointers are stable now (nothing grows below)
     void **v = vecs<T>(b);
     CgState *st = b.st[PrecIdx<T>::v];

@@ -82,9 +82,80 @@ static akra_status fma_rate(double *tflops)
     return AKRA_OK;
 }
 
+// Lane-steps a Legendre launch executes against the steps it counts.  One block per (m, chunk)
+// with the kernels' layout of ring pairs: synthesis pair (chunk P + k) NT + tid; adjoint pair
+// chunk P NT + warp 32 P + k 32 + lane.  A warp computes all 32 P of its slots from the first
+// l-tile (64-step tiles from the block's earliest start) that holds its earliest start, to lmax;
+// the counted steps are each live pair's own, from its start to lmax.
+__global__ void k_lane_steps(const int2 *__restrict__ start, const int *__restrict__ units, int nunits,
+                             int nunit_all, int L, int P, int nchunks, int adjoint, int tile,
+                             unsigned long long *out)
+{
+    __shared__ int s_first;
+    const int m = blockIdx.x / nchunks, chunk = blockIdx.x - m * nchunks;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, NT = blockDim.x;
+    if (tid == 0) s_first = kNeverLive;
+    __syncthreads();
+    int my_first = kNeverLive;
+    unsigned long long counted = 0;
+    for (int k = 0; k < P; k++) {
+        const long long iu = adjoint ? (long long)chunk * P * NT + warp * 32 * P + k * 32 + lane
+                                     : ((long long)chunk * P + k) * NT + tid;
+        int g = kNeverLive;
+        if (iu < nunits) g = start[(size_t)m * nunit_all + units[iu]].x;
+        if (g <= L) counted += (unsigned long long)(L - g + 1);
+        my_first = min(my_first, g);
+    }
+    const int warp_first = __reduce_min_sync(0xffffffffu, my_first);
+    atomicMin(&s_first, my_first);
+    __syncthreads();
+    const int l_first = s_first;
+    for (int o = 16; o > 0; o >>= 1) counted += __shfl_xor_sync(0xffffffffu, counted, o);
+    if (lane == 0) {
+        atomicAdd(&out[1], counted);
+        if (warp_first <= L) {
+            const int t0 = l_first + (warp_first - l_first) / tile * tile;
+            atomicAdd(&out[0], 32ull * P * (unsigned long long)(L - t0 + 1));
+        }
+    }
+}
+
 }  // namespace akra
 
 using namespace akra;
+
+extern "C" akra_status akra_legendre_lane_steps(akra_plan p, akra_prec prec, int adjoint, int P, int NT,
+                                                long long *lane_steps, long long *steps)
+{
+    if (!p || !lane_steps || !steps || (prec != AKRA_F64 && prec != AKRA_F32) || P < 1 || P > 64 ||
+        NT < 32 || NT > 1024 || NT % 32 != 0) {
+        set_error("akra_legendre_lane_steps: invalid argument");
+        return AKRA_EINVAL;
+    }
+    AKRA_TRY(reject_flat(p, "akra_legendre_lane_steps"));
+    *lane_steps = *steps = 0;
+    const int *units = p->has_weights ? p->d_active_units : p->d_all_units;
+    const int nunits = p->has_weights ? p->n_active_units : p->nunit;
+    if (nunits <= 0) return AKRA_OK;
+    const int nchunks = (nunits + P * NT - 1) / (P * NT);
+    unsigned long long *d = nullptr, h[2] = {0, 0};
+    if (cudaMalloc(&d, sizeof(h)) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("akra_legendre_lane_steps: allocation failed");
+        return AKRA_ENOMEM;
+    }
+    cudaMemset(d, 0, sizeof(h));
+    k_lane_steps<<<(p->lmax + 1) * nchunks, NT>>>(prec == AKRA_F32 ? p->d_start32 : p->d_start64, units, nunits,
+                                                 p->nunit, p->lmax, P, nchunks, adjoint ? 1 : 0, 64, d);
+    const cudaError_t e1 = cudaGetLastError();
+    const cudaError_t e2 = cudaMemcpy(h, d, sizeof(h), cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    AKRA_CUDA_TRY(e1);
+    AKRA_CUDA_TRY(e2);
+    *lane_steps = (long long)h[0];
+    *steps = (long long)h[1];
+    return AKRA_OK;
+}
 
 extern "C" akra_status akra_fma_rate(akra_prec prec, double *tflops)
 {

@@ -53,7 +53,7 @@ struct DebugRecord {
 enum DebugSite {
     kDbgUnits = 1, kDbgUnitInfo, kDbgStart, kDbgSeeds, kDbgCoef, kDbgAlm, kDbgKsFactor,
     kDbgPhiWrite, kDbgPhiRead, kDbgPartialWrite, kDbgPartialRead, kDbgAlmOut, kDbgRingActive,
-    kDbgFftPhi, kDbgFftMapIn, kDbgFftMapOut, kDbgFftWeight, kDbgFftRing
+    kDbgFftPhi, kDbgFftMapIn, kDbgFftMapOut, kDbgFftWeight, kDbgFftRing, kDbgBpre
 };
 #ifdef AKRA_DEBUG
 static __device__ DebugRecord g_akra_dbg;   // one per translation unit
@@ -197,6 +197,13 @@ struct LegArgs {
     const unsigned char *ring_active; // nullptr = all rings
     const int *skip;                  // device flag: return at once if set
     int *err;                         // device flag set when a bounded in-kernel wait runs out
+    // tensor-core synthesis: the B operand pre-staged per (m, 16-step tile, RHS group) in the
+    // tile layout of shared memory (legendre_tc_bstage), the first tile index of each m, and the
+    // number of RHS groups
+    const float *bpre;
+    const long long *tc_tilebase;
+    int tc_groups;
+    long long tc_tiles;
 };
 
 // arguments of one FP32 ring-FFT instance
@@ -306,6 +313,9 @@ struct akra_plan_s {
     akra::Workspace phi, partial, cg, red;
     akra::Workspace xsave;                   // κ_E kept aside by the conditional B-mode solve
     akra::Workspace red_cl;                  // per-l spectra before binning into band powers
+    akra::Workspace bpre;                    // tensor-core synthesis: pre-staged B operand tiles
+    long long tc_tiles = 0;                  // 16-step l-tiles over all m (from l0(m) to lmax)
+    long long *d_tc_tilebase = nullptr;      // [lmax+1] first tile index of each m
     cudaStream_t stream = nullptr;           // internal stream for captured CG graphs
     cudaEvent_t ev_a = nullptr, ev_b = nullptr;
     std::map<long long, akra::LegShape> shapes;   // key: prec*1000 + R
@@ -332,6 +342,12 @@ akra_status legendre_synth_tc(akra_plan p, int tcg, LegMode mode, const void *al
                               const int *units, int nunits, cudaStream_t st);
 constexpr int TC_NT = 128;   // tensor-core synthesis: threads = ring pairs per block = MMA rows
 akra_status legendre_tc_prepare();
+// bytes of the pre-staged B operand for R RHS in groups of tcg, and its reservation (a no-op when
+// large enough; call before any stream capture that may run the tensor-core synthesis)
+size_t tc_bpre_bytes(akra_plan p, int tcg, int R);
+akra_status tc_reserve(akra_plan p, int tcg, int R);
+// write the B operand tiles of x (one plan's [R][2][ntri] alm) for RHS groups of tcg
+akra_status legendre_tc_bstage(int tcg, const LegArgs<float> &a, cudaStream_t st);
 // persistent tensor-core synthesis over a work list of (instance, m, 128-pair chunk, RHS group)
 akra_status legendre_synth_tc_queue(int tcg, const LegArgs<float> *insts, const int4 *items, int nitems,
                                     int *counter, cudaStream_t st);

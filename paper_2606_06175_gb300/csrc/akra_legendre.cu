@@ -107,6 +107,10 @@ LegArgs<T> leg_args(akra_plan p, const LegShape &s, LegMode mode, const int *uni
     a.ring_active = units == p->d_all_units ? nullptr : p->d_ring_active;
     a.skip = p->cur_skip;
     a.err = p->d_tc_err;
+    a.bpre = (const float *)p->bpre.ptr;
+    a.tc_tilebase = p->d_tc_tilebase;
+    a.tc_groups = s.TC > 0 ? (R + s.TC - 1) / s.TC : 0;
+    a.tc_tiles = p->tc_tiles;
     return a;
 }
 

@@ -30,10 +30,15 @@ template <int RG>
 struct TcSynth {
     static constexpr int N = 4 * RG;                         // MMA columns per stream
     static constexpr int A_TILE = 128 * 8 * 4;               // 4 KB
+    static constexpr int A_BUF = 8 * A_TILE;                 // A[s][p][h] of one tile
     static constexpr int B_TILE = N * 8 * 4;
-    static constexpr int BUF = 8 * A_TILE + 4 * B_TILE;      // A[s][p][h], B[p][h]
-    static constexpr int CF = TCT * 16;                      // float4 coefficients of a tile
-    static constexpr int USED = 2 * BUF + 4 * CF;            // + standard / difference-form coefficients
+    static constexpr int B_SLOT = 4 * B_TILE;                // B[p][h] of one tile, pre-staged layout
+    static constexpr int NSLOT = 4;                          // B / coefficient ring: 3 tiles ahead
+    static constexpr int CF = TCT * 16;                      // 16 float4 coefficients of a tile
+    static constexpr int OFF_B = 2 * A_BUF;
+    static constexpr int OFF_CRAW = OFF_B + NSLOT * B_SLOT;  // raw coefficient ring
+    static constexpr int OFF_CF = OFF_CRAW + NSLOT * CF;     // standard / difference-form, 2 tiles each
+    static constexpr int USED = OFF_CF + 4 * CF;
     // TMEM columns: 4 streams x N (a power of two >= 32); shared memory sized so that the blocks
     // resident on an SM never ask for more than its 512 columns
     static constexpr uint32_t NCOL = 16 * RG < 32 ? 32 : 16 * RG;
@@ -41,56 +46,49 @@ struct TcSynth {
     static constexpr int SMEM = (MAXB >= 3 || USED * (MAXB + 1) > 227 * 1024) ? USED : (227 * 1024) / (MAXB + 1) + 1024;
 };
 
-__device__ __forceinline__ unsigned char *tc_a(unsigned char *buf, int s, int p, int h)
+__device__ __forceinline__ unsigned char *tc_a(unsigned char *abuf, int s, int p, int h)
 {
-    return buf + ((s * 2 + p) * 2 + h) * (128 * 8 * 4);
+    return abuf + ((s * 2 + p) * 2 + h) * (128 * 8 * 4);
 }
 
 template <int RG>
-__device__ __forceinline__ unsigned char *tc_b(unsigned char *buf, int p, int h)
+__device__ __forceinline__ unsigned char *tc_b(unsigned char *bslot, int p, int h)
 {
-    return buf + 8 * TcSynth<RG>::A_TILE + (p * 2 + h) * TcSynth<RG>::B_TILE;
+    return bslot + (p * 2 + h) * TcSynth<RG>::B_TILE;
 }
 
-// stage tile [lt, lt + 16): recurrence coefficients (threads 0..15; with diff also the
-// difference-form ones {A', A', (A'-2) + c', (A'-2) - c'}) and the B tiles
+// issue the asynchronous copies of tile lj (l = lj .. lj+15, lj - l0 a multiple of 16) of RHS group
+// g: its pre-staged B operand into a B slot and its 16 raw coefficient entries (zero past lmax)
 template <int RG>
-__device__ __forceinline__ void tc_stage(const LegArgs<float> &a, int m, long long mbase, int r0, int lt,
-                                         unsigned char *buf, float4 *cf, float4 *cfd, bool diff)
+__device__ __forceinline__ void tc_prefetch(const LegArgs<float> &a, int m, long long mbase, int l0, int g, int lj,
+                                            unsigned char *bslot, float4 *craw)
 {
-    const int L = a.L, R = a.R;
-    const long long ntri = a.ntri;
+    using S = TcSynth<RG>;
+    const int tid = threadIdx.x;
+    constexpr int CH = S::B_SLOT / 16;                       // 16-byte chunks of a B slot
+    const long long base = ((a.tc_tilebase[m] + (lj - l0) / TCT) * a.tc_groups + g) * CH;
+    const long long bound = a.tc_tiles * a.tc_groups * CH;
+    (void)bound;
+    const float4 *src = reinterpret_cast<const float4 *>(a.bpre);
+    for (int c = tid; c < CH; c += TC_NT)
+        tc::cp_async16(bslot + 16 * c, src + AKRA_IX(base + c, bound, kDbgBpre), 16);
+    if (tid < TCT) {
+        const int l = lj + tid;
+        const bool in = l <= a.L;
+        tc::cp_async16(craw + tid, a.coef + AKRA_IX(mbase + (in ? l : l0), a.ntri, kDbgCoef), in ? 16u : 0u);
+    }
+}
+
+// the per-step recurrence coefficients of a tile from its raw entries {A', c', σ, A' - 2}:
+// sign-alternated {rA', rA', rc', -rc'} and, for blocks with polar pairs, the difference form's
+// {A', A', (A' - 2) + c', (A' - 2) - c'} (threads 0..15)
+__device__ __forceinline__ void tc_coefs(const float4 *craw, float4 *cf, float4 *cfd, bool diff)
+{
     const int tid = threadIdx.x;
     if (tid < TCT) {
-        const int l = lt + tid;
-        const float4 c = (l <= L) ? a.coef[AKRA_IX(mbase + l, ntri, kDbgCoef)] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 c = craw[tid];
         cf[tid] = f2_coef_entry(c, tid);
         if (diff) cfd[tid] = make_float4(c.x, c.x, c.w + c.y, c.w - c.y);
-    }
-    for (int e = tid; e < TCT * RG; e += TC_NT) {
-        const int i = e / RG, rr = e - i * RG;
-        const int l = lt + i, r = r0 + rr, p = i & 1, k = i >> 1;
-        float v[4] = {0.f, 0.f, 0.f, 0.f};
-        if (l <= L && r < R) {
-            const long long abound = (long long)R * 2 * ntri;
-            (void)abound;
-            float2 E = a.alm[AKRA_IX(((size_t)r * 2 + 0) * ntri + mbase + l, abound, kDbgAlm)];
-            float2 B = a.alm[AKRA_IX(((size_t)r * 2 + 1) * ntri + mbase + l, abound, kDbgAlm)];
-            const float f = (a.fl ? a.fl[AKRA_IX(l, L + 1, kDbgKsFactor)] : -1.f) *
-                            a.coef[AKRA_IX(mbase + l, ntri, kDbgCoef)].z * f2_sign(i);
-            if (m == 0) E.y = B.y = 0.f;
-            v[0] = f * (E.x - B.y);   // c.re
-            v[1] = f * (E.y + B.x);   // c.im
-            v[2] = f * (E.x + B.y);   // d.re
-            v[3] = f * (E.y - B.x);   // d.im
-        }
-#pragma unroll
-        for (int c = 0; c < 4; c++) {
-            const float hd = tc::tf32_head(v[c]);
-            const uint32_t o = tc::tile_off(4 * rr + c, k);
-            *reinterpret_cast<float *>(tc_b<RG>(buf, p, 0) + o) = hd;
-            *reinterpret_cast<float *>(tc_b<RG>(buf, p, 1) + o) = v[c] - hd;
-        }
     }
 }
 
@@ -177,16 +175,32 @@ __device__ __forceinline__ void tc_synth_item(const LegArgs<float> &a, const int
     const uint32_t tmem = tmem_base;
     bool ok = true;
     const int T = active ? (L - l_first) / TCT + 1 : 0;
-    float4 *cf_all = reinterpret_cast<float4 *>(smem + 2 * S::BUF);
+    unsigned char *bring = smem + S::OFF_B;                                    // B slots
+    float4 *craw = reinterpret_cast<float4 *>(smem + S::OFF_CRAW);              // raw coefficient slots
+    float4 *cf_all = reinterpret_cast<float4 *>(smem + S::OFF_CF);
     float4 *cfd_all = cf_all + 2 * TCT;
+    const int g = r0 / RG;
+    // copies of tile j go to slot j mod 4, three tiles ahead of the one being computed; one copy
+    // group per tile (empty past the last), so that cp.async.wait_group 2 leaves only the two
+    // newest in flight
+    auto prefetch = [&](int j) {
+        if (j < T) tc_prefetch<RG>(a, m, mbase, l0, g, l_first + j * TCT, bring + (j & 3) * S::B_SLOT, craw + (j & 3) * TCT);
+        tc::cp_async_commit();
+    };
     if (active) {
-        tc_stage<RG>(a, m, mbase, r0, l_first, smem, cf_all, cfd_all, blk_diff);
+        prefetch(0);
+        prefetch(1);
+        prefetch(2);
+        tc::cp_async_wait<2>();                                   // this thread's copies of tile 0
+        tc_coefs(craw, cf_all, cfd_all, blk_diff);
+        tc::fence_async_smem();
         __syncthreads();
     }
     const uint32_t idesc = tc::idesc_tf32(128, N);
     for (int t = 0; t < T; t++) {
         const int lt = l_first + t * TCT, b = t & 1;
-        unsigned char *buf = smem + b * S::BUF;
+        unsigned char *buf = smem + b * S::A_BUF;
+        unsigned char *bslot = bring + (t & 3) * S::B_SLOT;
         const float4 *cf = cf_all + b * TCT;
         const float4 *cfd = cfd_all + b * TCT;
         f2_start_pairs<1>(a.seeds, a.start, (size_t)m * nunit_all, tbound, lt, uid1, gs1, V, VO, e1);
@@ -239,10 +253,13 @@ __device__ __forceinline__ void tc_synth_item(const LegArgs<float> &a, const int
             }
         }
         if (t + 1 < T) {
-            // the other buffer is free once the MMAs of tile t-1 have completed
+            // the other A buffer and B slot (t + 3) mod 4 are free once the MMAs of tile t-1 have
+            // completed; then tile t+3's copies go out and tile t+1's (issued at t-2) are waited for
             if (t >= 1) ok &= tc::mbar_wait(&s_mbar[(t + 1) & 1], ((t - 1) >> 1) & 1, kWaitLimit, a.err);
-            tc_stage<RG>(a, m, mbase, r0, lt + TCT, smem + ((t + 1) & 1) * S::BUF, cf_all + ((t + 1) & 1) * TCT,
-                         cfd_all + ((t + 1) & 1) * TCT, blk_diff);
+            prefetch(t + 3);
+            tc::cp_async_wait<2>();
+            tc_coefs(craw + ((t + 1) & 3) * TCT, cf_all + ((t + 1) & 1) * TCT, cfd_all + ((t + 1) & 1) * TCT,
+                     blk_diff);
         }
         tc::fence_async_smem();
         tc::fence_before();
@@ -256,8 +273,8 @@ __device__ __forceinline__ void tc_synth_item(const LegArgs<float> &a, const int
                     const uint32_t d = tmem + (uint32_t)((s * 2 + p) * N);
                     const uint64_t ah = tc::sdesc(tc::smem_u32(tc_a(buf, s, p, 0)));
                     const uint64_t al = tc::sdesc(tc::smem_u32(tc_a(buf, s, p, 1)));
-                    const uint64_t bh = tc::sdesc(tc::smem_u32(tc_b<RG>(buf, p, 0)));
-                    const uint64_t bl = tc::sdesc(tc::smem_u32(tc_b<RG>(buf, p, 1)));
+                    const uint64_t bh = tc::sdesc(tc::smem_u32(tc_b<RG>(bslot, p, 0)));
+                    const uint64_t bl = tc::sdesc(tc::smem_u32(tc_b<RG>(bslot, p, 1)));
                     tc::mma_tf32(d, ah, bh, idesc, t > 0 ? 1u : 0u);
                     tc::mma_tf32(d, ah, bl, idesc, 1u);
                     tc::mma_tf32(d, al, bh, idesc, 1u);
@@ -272,6 +289,7 @@ __device__ __forceinline__ void tc_synth_item(const LegArgs<float> &a, const int
         ok &= tc::mbar_wait(&s_mbar[(T - 1) & 1], ((T - 1) >> 1) & 1, kWaitLimit, a.err);
         tc::fence_after();
         if (!ok && a.err) atomicExch(a.err, 1);
+        tc::cp_async_wait<0>();   // only empty groups can remain; none may outlive the item
     }
 
     // Φ(±m) of both rings of this row's pair, per RHS
@@ -396,13 +414,73 @@ k_leg_synth_tc_queue(const LegArgs<float> *__restrict__ insts, const int4 *__res
     tc_block_free<RG>(tmem);
 }
 
+// B operand tiles of one plan's alm for RHS groups of RG, in the shared-memory layout of a tile:
+// [tile][group][parity][head, rest][N rows x 8 K] (K-major canonical core matrices, tile_off),
+// tiles of 16 l-steps from l0 = max(m, 2), values f_l σ_l s_l (E ± iB) with s_l the state sign
+// relative to the tile start.  One block row per m; consecutive threads write consecutive words.
+template <int RG>
+__global__ void __launch_bounds__(256) k_tc_bstage(LegArgs<float> a, float *out)
+{
+    using S = TcSynth<RG>;
+    constexpr int N = S::N;
+    const int m = blockIdx.x, L = a.L, R = a.R;
+    const int l0 = m > 2 ? m : 2;
+    const long long ntri = a.ntri, mbase = (long long)m * (2 * L + 1 - m) / 2;
+    const int ntile = (L - l0) / TCT + 1;
+    const long long per_tile = (long long)a.tc_groups * 16 * N;
+    const long long tb = a.tc_tilebase[AKRA_IX(m, L + 1, kDbgBpre)];
+    const long long obound = a.tc_tiles * a.tc_groups * (S::B_SLOT / 4);
+    const long long abound = (long long)R * 2 * ntri;
+    (void)obound;
+    (void)abound;
+    for (long long idx = threadIdx.x + (long long)blockIdx.y * blockDim.x; idx < ntile * per_tile;
+         idx += (long long)blockDim.x * gridDim.y) {
+        const int q = (int)(idx / per_tile);
+        const long long rem = idx - q * per_tile;
+        const int g = (int)(rem / (16 * N)), e = (int)(rem - (long long)g * 16 * N);
+        // e bits 0-1: k mod 4, 2-4: row mod 8, 5: k / 4, 6: parity, 7+: row / 8
+        const int kq = e & 3, r8 = (e >> 2) & 7, kh = (e >> 5) & 1, p = (e >> 6) & 1, rb = e >> 7;
+        const int row = rb * 8 + r8, k = kh * 4 + kq, i = p + 2 * k;
+        const int rr = row >> 2, c = row & 3;
+        const int l = l0 + q * TCT + i, r = g * RG + rr;
+        float v = 0.f;
+        if (l <= L && r < R) {
+            float2 E = a.alm[AKRA_IX(((size_t)r * 2 + 0) * ntri + mbase + l, abound, kDbgAlm)];
+            float2 B = a.alm[AKRA_IX(((size_t)r * 2 + 1) * ntri + mbase + l, abound, kDbgAlm)];
+            const float f = (a.fl ? a.fl[AKRA_IX(l, L + 1, kDbgKsFactor)] : -1.f) *
+                            a.coef[AKRA_IX(mbase + l, ntri, kDbgCoef)].z * f2_sign(i);
+            if (m == 0) E.y = B.y = 0.f;
+            // rows c = 0..3 of an RHS: c = f (E + iB) re, im; d = f (E - iB) re, im
+            v = c == 0 ? f * (E.x - B.y) : c == 1 ? f * (E.y + B.x) : c == 2 ? f * (E.x + B.y) : f * (E.y - B.x);
+        }
+        const float hd = tc::tf32_head(v);
+        const long long o = ((tb + q) * a.tc_groups + g) * (S::B_SLOT / 4) + p * (S::B_TILE / 2) +
+                            tc::tile_off(row, k) / 4;
+        out[AKRA_IX(o, obound, kDbgBpre)] = hd;
+        out[AKRA_IX(o + S::B_TILE / 4, obound, kDbgBpre)] = v - hd;
+    }
+}
+
+template <int RG>
+static akra_status launch_bstage(const LegArgs<float> &a, cudaStream_t st)
+{
+    k_tc_bstage<RG><<<dim3((unsigned)a.L + 1, 4), 256, 0, st>>>(a, const_cast<float *>(a.bpre));
+    AKRA_CUDA_TRY(cudaGetLastError());
+    return AKRA_OK;
+}
+
 template <int RG>
 static akra_status launch_synth_tc(akra_plan p, LegMode mode, const void *alm, void *phi, int R,
                                    const int *units, int nunits, cudaStream_t st)
 {
+    AKRA_TRY(tc_reserve(p, RG, R));
     LegArgs<float> a = leg_args<float>(p, LegShape{1, TC_NT, RG}, mode, units, nunits, R);
     a.alm = (const float2 *)alm;
     a.phi = (float2 *)phi;
+    a.bpre = (const float *)p->bpre.ptr;
+    a.tc_groups = (R + RG - 1) / RG;
+    AKRA_TRY(launch_bstage<RG>(a, st));
+    p->launches++;
     dim3 grid((unsigned)(p->lmax + 1) * a.nchunks, (R + RG - 1) / RG);
     k_leg_synth_tc<RG><<<grid, TC_NT, TcSynth<RG>::SMEM, st>>>(a);
     AKRA_CUDA_TRY(cudaGetLastError());
@@ -428,11 +506,18 @@ template <int RG>
 static akra_status launch_tc_queue(const LegArgs<float> *insts, const int4 *items, int nitems, int *counter,
                                    cudaStream_t st)
 {
-    int dev = 0, nsm = 1, per_sm = 0;
+    // resident blocks per SM from shared memory (dynamic + static + the per-block reservation)
+    // and TMEM columns; blocks beyond what fits simply start later (no block waits on another)
+    int dev = 0, nsm = 1, smem_sm = 0, reserved = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_leg_synth_tc_queue<RG>, TC_NT, TcSynth<RG>::SMEM);
-    const int grid = std::max(1, std::min(nitems, nsm * std::max(per_sm, 1)));
+    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+    cudaFuncAttributes fa{};
+    cudaFuncGetAttributes(&fa, k_leg_synth_tc_queue<RG>);
+    const int per_blk = TcSynth<RG>::SMEM + (int)fa.sharedSizeBytes + reserved;
+    const int per_sm = std::max(1, std::min(smem_sm / std::max(per_blk, 1), 512 / (int)TcSynth<RG>::NCOL));
+    const int grid = std::max(1, std::min(nitems, nsm * per_sm));
     k_leg_synth_tc_queue<RG><<<grid, TC_NT, TcSynth<RG>::SMEM, st>>>(insts, items, nitems, counter);
     AKRA_CUDA_TRY(cudaGetLastError());
     return AKRA_OK;
@@ -446,6 +531,31 @@ akra_status legendre_synth_tc_queue(int tcg, const LegArgs<float> *insts, const 
     case 8: return launch_tc_queue<8>(insts, items, nitems, counter, st);
     case 16: return launch_tc_queue<16>(insts, items, nitems, counter, st);
     case 32: return launch_tc_queue<32>(insts, items, nitems, counter, st);
+    default:
+        set_error("no tensor-core synthesis for an RHS group of %d", tcg);
+        return AKRA_EINVAL;
+    }
+}
+
+size_t tc_bpre_bytes(akra_plan p, int tcg, int R)
+{
+    if (tcg <= 0) return 0;
+    return (size_t)p->tc_tiles * (size_t)((R + tcg - 1) / tcg) * (size_t)(128 * 4 * tcg);
+}
+
+akra_status tc_reserve(akra_plan p, int tcg, int R)
+{
+    if (tcg <= 0) return AKRA_OK;
+    return ws_reserve(p, p->bpre, tc_bpre_bytes(p, tcg, R));
+}
+
+akra_status legendre_tc_bstage(int tcg, const LegArgs<float> &a, cudaStream_t st)
+{
+    switch (tcg) {
+    case 4: return launch_bstage<4>(a, st);
+    case 8: return launch_bstage<8>(a, st);
+    case 16: return launch_bstage<16>(a, st);
+    case 32: return launch_bstage<32>(a, st);
     default:
         set_error("no tensor-core synthesis for an RHS group of %d", tcg);
         return AKRA_EINVAL;

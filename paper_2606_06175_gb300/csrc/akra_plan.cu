@@ -442,7 +442,7 @@ akra_status tc_error_check(akra_plan p)
 size_t plan_device_bytes(akra_plan p)
 {
     return p->bytes_tables + p->phi.bytes + p->partial.bytes + p->cg.bytes + p->red.bytes +
-           p->xsave.bytes + p->red_cl.bytes;
+           p->xsave.bytes + p->red_cl.bytes + p->bpre.bytes;
 }
 
 LegShape leg_shape(akra_plan p, akra_prec prec, int R)
@@ -632,6 +632,18 @@ static akra_status plan_build(akra_plan p)
     AKRA_TRY(ring_fft_prepare(p));
     AKRA_TRY(ring_fft32_build(p));
     AKRA_TRY(legendre_tc_prepare());
+    {
+        // 16-step l-tiles of every m (from l0 = max(m, 2)), the tensor-core synthesis' B operand grid
+        std::vector<long long> tb(L + 1);
+        long long acc = 0;
+        for (int m = 0; m <= L; m++) {
+            tb[m] = acc;
+            acc += (L - std::max(m, 2)) / 16 + 1;
+        }
+        p->tc_tiles = acc;
+        AKRA_TRY(dev_alloc(p, &p->d_tc_tilebase, sizeof(long long) * (L + 1)));
+        AKRA_CUDA_TRY(cudaMemcpy(p->d_tc_tilebase, tb.data(), sizeof(long long) * (L + 1), cudaMemcpyHostToDevice));
+    }
     AKRA_CUDA_TRY(cudaStreamCreateWithFlags(&p->stream, cudaStreamNonBlocking));
     AKRA_CUDA_TRY(cudaEventCreateWithFlags(&p->ev_a, cudaEventDisableTiming));
     AKRA_CUDA_TRY(cudaEventCreateWithFlags(&p->ev_b, cudaEventDisableTiming));
@@ -691,7 +703,8 @@ extern "C" void akra_plan_destroy(akra_plan p)
                     p->d_fft32_off, p->d_fft32_tw2, p->d_fft32_bhat, p->d_seed32, p->d_seed64,
                     p->d_start32, p->d_start64, p->d_steps, p->d_pw64, p->d_pw32, p->d_ftw64,
                     p->d_ftw32, p->d_fWt64, p->d_fWt32,
-                    p->d_fft32_rings_all, p->d_fft32_rings_act, p->d_tc_err, p->d_dseed32, p->d_blue64};
+                    p->d_fft32_rings_all, p->d_fft32_rings_act, p->d_tc_err, p->d_dseed32, p->d_blue64,
+                    p->bpre.ptr, p->d_tc_tilebase};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     if (p->stream) cudaStreamDestroy(p->stream);
@@ -735,7 +748,7 @@ extern "C" akra_status akra_plan_fill_workspaces(akra_plan p, int byte, void *st
         return AKRA_EINVAL;
     }
     cudaStream_t st = (cudaStream_t)stream;
-    akra::Workspace *ws[] = {&p->phi, &p->partial, &p->cg, &p->red, &p->xsave, &p->red_cl};
+    akra::Workspace *ws[] = {&p->phi, &p->partial, &p->cg, &p->red, &p->xsave, &p->red_cl, &p->bpre};
     for (akra::Workspace *w : ws)
         if (w->ptr && w->bytes) AKRA_CUDA_TRY(cudaMemsetAsync(w->ptr, byte, w->bytes, st));
     return AKRA_OK;

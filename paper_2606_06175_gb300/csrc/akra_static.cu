@@ -64,7 +64,9 @@ static akra_status synth_static(akra_plan p, const void *alm, void *map, int R, 
     AKRA_TRY(scratch_address(&phi));
     // every Φ entry the ring FFT reads is written first by the Legendre kernel of this call
     // (all m of all rings), so nothing needs clearing between calls
-    const LegShape s = leg_shape(p, PrecIdxStatic<T>::prec, R);
+    // the CUDA-core synthesis: the tensor-core one stages its operand in a plan workspace
+    LegShape s = leg_shape(p, PrecIdxStatic<T>::prec, R);
+    s.TC = 0;
     AKRA_TRY(legendre_synth<T>(p, s, LegMode::Synth, alm, phi, R, p->d_all_units, p->nunit, st));
     return ring_fft<T>(p, FftMode::Synth, phi, nullptr, map, false, R, p->d_all_rings, p->nring, st);
 }

@@ -112,6 +112,17 @@ __device__ __forceinline__ void tmem_ld4(uint32_t taddr, float (&v)[4])
     v[3] = __uint_as_float(r3);
 }
 
+// 16-byte asynchronous copy global -> shared (cp.async, L2 only); src_bytes = 0 zero-fills the
+// destination without reading the source
+__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gsrc, uint32_t src_bytes)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;"
+                 :: "r"(smem_u32(smem_dst)), "l"(__cvta_generic_to_global(gsrc)), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+// wait until at most N of this thread's committed copy groups are still pending
+template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" :: "n"(N) : "memory"); }
+
 // split x into a TF32 head (the top 11 significant bits, exactly representable) and the FP32
 // remainder x - head (exact); the tensor core reads the remainder's top 11 bits, so
 // head*b_head + head*b_rest + rest*b_head carries ~21 bits of each product

@@ -39,6 +39,8 @@ def main():
     ap.add_argument("--tc", type=int, default=0, metavar="G",
                     help="FP32 synthesis on the tensor core with RHS groups of G (with --rhs)")
     ap.add_argument("--rhs", type=int, default=1, help="right-hand sides of the H applications")
+    ap.add_argument("--stages", action="store_true",
+                    help="print the CUDA-event stage times of one H (akra_time_H_stages, 5 runs) as JSON")
     ap.add_argument("--batch", action="store_true",
                     help="one batched FP32 H over two instances (Nside and Nside/2, --rhs RHS each) instead")
     args = ap.parse_args()
@@ -88,6 +90,12 @@ def main():
     x64 = torch.from_numpy(np.stack([kE, np.zeros_like(kE)])[None]).to(dev)
     if args.cufft:
         print(json.dumps(cufft_comparison(plan, sv["ninv"], N, dev)))
+        return
+    if args.stages:
+        st = A.akra_time_H_stages(plan, prec, R, 5)
+        print(json.dumps({"nside": N, "lmax": L, "prec": args.prec, "rhs": R, "tc_group": args.tc,
+                          "shape": A.akra_plan_get_shape(plan, prec, R), "stage_ms": st,
+                          "per_rhs_ms": {k: v / R for k, v in st.items()}}))
         return
     if args.solve:
         y = A.akra_apply_A(plan, A.F64, x64)

@@ -48,12 +48,23 @@ def main():
             assert info["status"] == 0, info
         xs32, info = A.akra_cg_solve(p, A.F32, y.float(), tol=1e-4, maxiter=3000)
         assert info["status"] == 0, info
-        # the persistent work-queue kernels and the batched FFT
+        # the persistent work-queue kernels and the batched FFT, with the CUDA-core and the
+        # tensor-core synthesis (its operand staging kernel and prefetch ring included)
         bt = A.akra_batch_create([p], [R])
         xb = x.to(torch.complex64)
-        yb = A.akra_batch_apply_H(bt, [xb])[0]
-        out["errors"]["batch_H_%d" % N] = rel(yb[R - 1].to(torch.complex128).cpu().numpy(), h)
+        for group in (0, 4):
+            A.akra_batch_set_tc_synthesis(bt, group)
+            yb = A.akra_batch_apply_H(bt, [xb])[0]
+            e = rel(yb[R - 1].to(torch.complex128).cpu().numpy(), h)
+            out["errors"]["batch_H_%d_tc%d" % (N, group)] = e
+            assert e < 4 * 2.0 ** -24 * 64, (N, group, e)
         del bt
+        # the single-plan tensor-core synthesis, RHS groups partly filled
+        for group in (4, 8):
+            A.akra_plan_set_tc_synthesis(p, R, group)
+            s = A.akra_synth_spin2(p, A.F32, x.to(torch.complex64))[R - 1].double().cpu().numpy()
+            out["errors"]["synth_tc%d_%d" % (group, N)] = rel(s, g)
+            assert rel(s, g) < 4 * 2.0 ** -24 * 64, (N, group, rel(s, g))
     torch.cuda.synchronize()
     out["violations"] = A.akra_debug_violations()
     print(json.dumps(out))

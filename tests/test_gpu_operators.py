@@ -431,3 +431,23 @@ def test_empty_footprint_gives_zero_operator_and_zero_solution():
     for prec in (A.F64, A.MIXED):
         xs, info = A.akra_cg_solve(p, prec, shear, tol=1e-6, maxiter=50)
         assert info["status"] == 0 and torch.count_nonzero(xs) == 0
+
+
+def test_lane_steps_count_the_plans_steps():
+    """The work accounting of a Legendre launch: its counted steps are the plan's start-table
+    steps for every layout, and no layout executes fewer lane-steps than it counts."""
+    N, L = 64, 128
+    p = A.akra_plan_create(N, L)
+    th, _ = O.pixel_angles(N)
+    ninv = np.where(np.cos(th) < -0.2, 1.0, 0.0)
+    A.akra_plan_set_weights(p, torch.from_numpy(ninv).to(DEV), 1e-3)
+    d = A.akra_plan_describe(p)
+    for prec, key in ((A.F32, "legendre_steps_f32"), (A.F64, "legendre_steps_f64")):
+        for adj in (False, True):
+            for P in (1, 3, 4, 8):
+                w = A.akra_legendre_lane_steps(p, prec, adj, P)
+                assert w["steps"] == d[key], (prec, adj, P, w, d[key])
+                assert w["lane_steps"] >= w["steps"]
+                # a warp executes at most 32 P lanes over the whole triangle's l-range per m
+                nw = -(-d["n_active_units"] // (128 * P)) * 4
+                assert w["lane_steps"] <= nw * 32 * P * sum(L - max(m, 2) + 1 for m in range(L + 1))
