@@ -542,8 +542,10 @@ def main():
     dom = "legendre_adjoint" if st32["legendre_adjoint"] >= st32["legendre_synth"] else "legendre_synth"
     kname = {"legendre_adjoint": "k_leg_adjoint<float>", "legendre_synth": "k_leg_synth<float>"}[dom]
     shape = A.akra_plan_get_shape(plan, A.F32, 1)
+    rga = A.akra_plan_get_adjoint_shape(plan, A.F32, 1)["RGA"]
     kfull = "%s<float,%d,%d,128>" % ("k_leg_adjoint" if dom == "legendre_adjoint" else "k_leg_synth",
-                                     shape["PA"] if dom == "legendre_adjoint" else shape["P"], shape["RG"])
+                                     shape["PA"] if dom == "legendre_adjoint" else shape["P"],
+                                     rga if dom == "legendre_adjoint" else shape["RG"])
     achieved = work["model_flops"] / (st32[dom] * 1e-3) / 1e12
     traffic, traffic_note = captured_traffic(kfull)
     f32_meas = A.akra_fma_rate(A.F32)

@@ -368,6 +368,15 @@ akra_status akra_plan_get_shape(akra_plan plan, akra_prec prec, int R, int *P, i
  * The results do not depend on the shape beyond rounding order.  Errors: EINVAL. */
 akra_status akra_plan_set_shape(akra_plan plan, akra_prec prec, int R, int P, int PA, int RG);
 
+/* The adjoint's own tile shape for (prec, R): ring pairs per thread PA and RHS per block RGA,
+ * which may differ from the synthesis' RG (the synthesis amortises its recurrence over the RHS
+ * of a block, the adjoint's per-step warp reduction grows with them).  akra_plan_set_shape sets
+ * RGA = RG; akra_autotune picks synthesis and adjoint shapes independently; the defaults take
+ * PA = 5, RGA = 1 (FP32) and PA = 2, RGA = 2 (FP64) for several RHS.  (PA, RGA) must be a
+ * compiled shape (list above).  Errors: EINVAL. */
+akra_status akra_plan_set_adjoint_shape(akra_plan plan, akra_prec prec, int R, int PA, int RGA);
+akra_status akra_plan_get_adjoint_shape(akra_plan plan, akra_prec prec, int R, int *PA, int *RGA);
+
 /* FP32 Legendre synthesis on the tensor core (the paper has no counterpart; an implementation
  * choice of the FP32 operator).  group = 4, 8, 16 or 32 runs the synthesis of every FP32
  * operator with (prec, R) = (AKRA_F32, R) on tcgen05 tensor cores, RHS taken `group` at a time:

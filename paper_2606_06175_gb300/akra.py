@@ -57,7 +57,8 @@ EXPORTS = ["akra_plan_create", "akra_plan_destroy", "akra_last_error", "akra_ver
            "akra_cg_solve_fields", "akra_shuffle_shear", "akra_cl_spectra",
            "akra_plan_set_preconditioner", "akra_flat_plan_create", "akra_plan_fill_workspaces",
            "akra_debug_violations", "akra_plan_set_tc_synthesis", "akra_plan_get_tc_synthesis",
-           "akra_batch_set_tc_synthesis", "akra_batch_get_tc_synthesis", "akra_legendre_lane_steps"]
+           "akra_batch_set_tc_synthesis", "akra_batch_get_tc_synthesis", "akra_legendre_lane_steps",
+           "akra_plan_set_adjoint_shape", "akra_plan_get_adjoint_shape"]
 
 _lib_handle = None
 
@@ -114,6 +115,8 @@ def load(build_if_missing: bool = False):
         "akra_batch_get_tc_synthesis": ([vp, ctypes.POINTER(i)], i),
         "akra_legendre_lane_steps": ([vp, i, i, i, i, ctypes.POINTER(ctypes.c_longlong),
                                       ctypes.POINTER(ctypes.c_longlong)], i),
+        "akra_plan_set_adjoint_shape": ([vp, i, i, i, i], i),
+        "akra_plan_get_adjoint_shape": ([vp, i, i, ctypes.POINTER(i), ctypes.POINTER(i)], i),
         "akra_time_H_stages": ([vp, i, i, i, vp, ctypes.POINTER(ctypes.c_double)], i),
         "akra_synth_spin2_static": ([vp, i, vp, vp, i, vp], i),
         "akra_cg_solve_adjoint": ([vp, i, vp, vp, i, d, i, ctypes.POINTER(CgInfo), vp], i),
@@ -417,6 +420,17 @@ def akra_plan_get_shape(plan: Plan, prec: int, R: int = 1) -> dict:
     _check(load().akra_plan_get_shape(plan.handle, prec, R, ctypes.byref(P), ctypes.byref(PA),
                                       ctypes.byref(RG)))
     return {"P": P.value, "PA": PA.value, "RG": RG.value}
+
+
+def akra_plan_set_adjoint_shape(plan: Plan, prec: int, R: int, PA: int, RGA: int):
+    """The adjoint's ring pairs per thread and RHS per block for (prec, R)."""
+    _check(load().akra_plan_set_adjoint_shape(plan.handle, prec, R, PA, RGA))
+
+
+def akra_plan_get_adjoint_shape(plan: Plan, prec: int, R: int = 1) -> dict:
+    pa, rga = ctypes.c_int(), ctypes.c_int()
+    _check(load().akra_plan_get_adjoint_shape(plan.handle, prec, R, ctypes.byref(pa), ctypes.byref(rga)))
+    return {"PA": pa.value, "RGA": rga.value}
 
 
 def akra_plan_set_tc_synthesis(plan: Plan, R: int, group: int):

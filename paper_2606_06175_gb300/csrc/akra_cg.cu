@@ -29,6 +29,15 @@ __device__ __forceinline__ double wdot(bool m0, cx_t<T> a, cx_t<T> b)
     return m0 ? (double)a.x * (double)b.x : 2.0 * ((double)a.x * (double)b.x + (double)a.y * (double)b.y);
 }
 
+// FP32 vectors: the element's product in FP32 (relative rounding 2^-24, far below the FP32 CG's
+// inner tolerances), the sums in FP64 -- one conversion per element instead of four, which the
+// FP64 pipe executes
+template <>
+__device__ __forceinline__ double wdot<float>(bool m0, float2 a, float2 b)
+{
+    return (double)(m0 ? a.x * b.x : 2.f * fmaf(a.x, b.x, a.y * b.y));
+}
+
 // block-reduce one double per slot into scratch[k * RED_NB + blockIdx.x]; returns true on the
 // last block to finish (which may then read every partial)
 __device__ bool block_partials(double *vals, int nslots, double *scratch, CgCtl *ctl)

@@ -175,7 +175,9 @@ struct LegShape {
     int PA = 0;            // ring pairs per thread of the adjoint (0: same as P)
     int TC = 0;            // FP32 synthesis on the tensor core with RHS groups of TC (4, 8, 16,
                            // 32); 0: CUDA-core synthesis of shape (P, RG)
+    int RGA = 0;           // RHS per block of the adjoint (0: same as RG)
     int adjP() const { return PA > 0 ? PA : P; }
+    int adjRG() const { return RGA > 0 ? RGA : RG; }
 };
 
 // arguments of one Legendre kernel instance (one plan; the batched launches hold an array)

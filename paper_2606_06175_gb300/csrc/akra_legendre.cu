@@ -168,7 +168,7 @@ akra_status legendre_adjoint(akra_plan p, const LegShape &s, const void *phi, vo
     if (nunits <= 0) return AKRA_OK;
     const int pa = s.adjP();
 #define AKRA_A(PP, RR)                                                                      \
-    if (pa == PP && s.RG == RR) {                                                           \
+    if (pa == PP && s.adjRG() == RR) {                                                      \
         *nchunks_out = launch_adjoint<T, PP, RR, 128>(p, phi, partial, R, units, nunits, st); \
         AKRA_CUDA_TRY(cudaGetLastError());                                                  \
         p->launches++;                                                                      \
@@ -177,7 +177,7 @@ akra_status legendre_adjoint(akra_plan p, const LegShape &s, const void *phi, vo
     AKRA_A(1, 1) AKRA_A(2, 1) AKRA_A(4, 1) AKRA_A(1, 2) AKRA_A(2, 2) AKRA_A(1, 4)
     if constexpr (std::is_same<T, float>::value) { AKRA_A(3, 1) AKRA_A(5, 1) AKRA_A(6, 1) AKRA_A(8, 1) }
 #undef AKRA_A
-    set_error("no adjoint kernel for P=%d RG=%d", pa, s.RG);
+    set_error("no adjoint kernel for P=%d RG=%d", pa, s.adjRG());
     return AKRA_EINVAL;
 }
 

@@ -450,11 +450,18 @@ LegShape leg_shape(akra_plan p, akra_prec prec, int R)
     const long long key = (long long)prec * 1000 + (R > 999 ? 999 : R);
     auto it = p->shapes.find(key);
     if (it != p->shapes.end()) return it->second;
-    // defaults: FP32 4 ring pairs per thread, FP64 2 (DFMA-bound; fewer registers)
-    if (prec == AKRA_F64) return R >= 2 ? LegShape{1, 128, 2} : LegShape{2, 128, 1};
-    if (R >= 4) return LegShape{1, 128, 4};
-    if (R >= 2) return LegShape{2, 128, 2};
-    return LegShape{4, 128, 1};
+    // defaults (measured on the DES-like footprint at Nside 1024-2048; akra_autotune refines):
+    // FP32 synthesis one ring pair per thread, with up to 4 RHS per block, and the paired adjoint
+    // at 5 pairs per thread, one RHS per block; FP64 synthesis up to 4 RHS per block, adjoint 2
+    // pairs per thread and 2 RHS per block (4 pairs, 1 RHS at R = 1)
+    if (prec == AKRA_F64) {
+        if (R >= 4) return LegShape{1, 128, 4, 2, 0, 2};
+        if (R >= 2) return LegShape{1, 128, 2, 2, 0, 2};
+        return LegShape{1, 128, 1, 4};
+    }
+    if (R >= 4) return LegShape{1, 128, 4, 5, 0, 1};
+    if (R >= 2) return LegShape{1, 128, 2, 5, 0, 1};
+    return LegShape{1, 128, 1, 5};
 }
 
 template <typename T> static akra_prec prec_of();
@@ -1030,16 +1037,16 @@ static akra_status tune_one(akra_plan p, akra_prec prec, int R, cudaStream_t st)
     AKRA_TRY(tc_error_check(p));
     LegShape pick = cands.back();
     float best = 1e30f;
-    for (size_t j = 0; j < cands.size(); j++) {      // adjoint shape j ...
-        for (size_t k = 0; k < cands.size(); k++) {  // ... with a CUDA-core synthesis of the same RG
-            if (cands[j].RG != cands[k].RG || ts[k] + ta[j] >= best) continue;
+    for (size_t j = 0; j < cands.size(); j++) {      // adjoint shape j (its own RHS group) ...
+        for (size_t k = 0; k < cands.size(); k++) {  // ... with a CUDA-core synthesis shape k
+            if (ts[k] + ta[j] >= best) continue;
             best = ts[k] + ta[j];
-            pick = LegShape{cands[k].P, cands[k].NT, cands[k].RG, cands[j].P};
+            pick = LegShape{cands[k].P, cands[k].NT, cands[k].RG, cands[j].P, 0, cands[j].RG};
         }
         for (size_t q = 0; q < tcs.size(); q++) {    // ... or with the tensor-core synthesis
             if (ttc[q] + ta[j] >= best) continue;
             best = ttc[q] + ta[j];
-            pick = LegShape{cands[j].P, cands[j].NT, cands[j].RG, cands[j].P, tcs[q]};
+            pick = LegShape{cands[j].P, cands[j].NT, cands[j].RG, cands[j].P, tcs[q], cands[j].RG};
         }
     }
     p->shapes[(long long)prec * 1000 + (R > 999 ? 999 : R)] = pick;
@@ -1092,6 +1099,34 @@ extern "C" akra_status akra_plan_set_shape(akra_plan p, akra_prec prec, int R, i
     }
     p->shapes[(long long)prec * 1000 + (R > 999 ? 999 : R)] = LegShape{P, 128, RG, PA};
     p->ws_gen++;   // captured CG iterations used the previous shape
+    return AKRA_OK;
+}
+
+extern "C" akra_status akra_plan_set_adjoint_shape(akra_plan p, akra_prec prec, int R, int PA, int RGA)
+{
+    AKRA_TRY(reject_flat(p, "akra_plan_set_adjoint_shape"));
+    if (!p || R < 1 || R > 65535 || (prec != AKRA_F64 && prec != AKRA_F32) || !shape_compiled(prec, PA, RGA)) {
+        set_error("akra_plan_set_adjoint_shape: invalid argument or no compiled adjoint for P=%d RG=%d", PA, RGA);
+        return AKRA_EINVAL;
+    }
+    LegShape s = leg_shape(p, prec, R);
+    s.PA = PA;
+    s.RGA = RGA;
+    p->shapes[(long long)prec * 1000 + (R > 999 ? 999 : R)] = s;
+    p->ws_gen++;   // captured CG iterations used the previous shape
+    return AKRA_OK;
+}
+
+extern "C" akra_status akra_plan_get_adjoint_shape(akra_plan p, akra_prec prec, int R, int *PA, int *RGA)
+{
+    AKRA_TRY(reject_flat(p, "akra_plan_get_adjoint_shape"));
+    if (!p || !PA || !RGA || R < 1 || (prec != AKRA_F64 && prec != AKRA_F32)) {
+        set_error("akra_plan_get_adjoint_shape: invalid argument");
+        return AKRA_EINVAL;
+    }
+    const LegShape s = leg_shape(p, prec, R);
+    *PA = s.adjP();
+    *RGA = s.adjRG();
     return AKRA_OK;
 }
 

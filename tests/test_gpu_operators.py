@@ -451,3 +451,64 @@ def test_lane_steps_count_the_plans_steps():
                 # a warp executes at most 32 P lanes over the whole triangle's l-range per m
                 nw = -(-d["n_active_units"] // (128 * P)) * 4
                 assert w["lane_steps"] <= nw * 32 * P * sum(L - max(m, 2) + 1 for m in range(L + 1))
+
+
+@pytest.mark.parametrize("prec,RG,RGA", [(A.F32, 4, 1), (A.F32, 2, 1), (A.F64, 4, 2), (A.F64, 1, 2)])
+def test_adjoint_rhs_group_differs_from_synthesis(prec, RG, RGA):
+    """H with the synthesis taking RG right-hand sides per block and the adjoint RGA (R = 5: both
+    groups partly filled), against the oracle; then the default shape and the autotuned one."""
+    N, L, R = 16, 40, 5
+    p = A.akra_plan_create(N, L)
+    rng = np.random.default_rng(300 + RG * 10 + RGA)
+    th, ph = O.pixel_angles(N)
+    ninv = np.where(np.cos(th) < 0.4, 1.0 + rng.random(12 * N * N), 0.0)
+    A.akra_plan_set_weights(p, torch.from_numpy(ninv).to(DEV), 1e-3)
+    pa = 5 if prec == A.F32 and RGA == 1 else (2 if RGA == 2 else 1)
+    A.akra_plan_set_shape(p, prec, R, 1, 1, RG)
+    A.akra_plan_set_adjoint_shape(p, prec, R, pa, RGA)
+    assert A.akra_plan_get_adjoint_shape(p, prec, R) == {"PA": pa, "RGA": RGA}
+    assert A.akra_plan_get_shape(p, prec, R) == {"P": 1, "PA": pa, "RG": RG}
+    pairs = [(S.random_alm(L, rng), S.random_alm(L, rng)) for _ in range(R)]
+    w = O.Weights(N, ninv, 1e-3)
+    refs = [np.stack(O.apply_H(N, L, w, *q)) for q in pairs]
+    tol = TOL64 if prec == A.F64 else tol32(L)
+    y = A.akra_apply_H(p, prec, alm_dev(pairs, prec)).to(torch.complex128).cpu().numpy()
+    for r in range(R):
+        assert rel(y[r], refs[r]) < tol, (prec, RG, RGA, r)
+    with pytest.raises(A.AkraError):
+        A.akra_plan_set_adjoint_shape(p, prec, R, pa, 3)
+    # a fresh plan's default shape and the autotuner's pick give the same operator
+    q = A.akra_plan_create(N, L)
+    A.akra_plan_set_weights(q, torch.from_numpy(ninv).to(DEV), 1e-3)
+    for tune in (False, True):
+        if tune:
+            A.akra_autotune(q, prec, R)
+        y = A.akra_apply_H(q, prec, alm_dev(pairs, prec)).to(torch.complex128).cpu().numpy()
+        for r in range(R):
+            assert rel(y[r], refs[r]) < tol, (prec, tune, r)
+
+
+@pytest.mark.parametrize("hemi", ["north", "south", "north_with_equator"])
+@pytest.mark.parametrize("prec", [A.F64, A.F32])
+def test_one_hemisphere_footprint_matches_oracle(hemi, prec):
+    """Footprints in one hemisphere: every active ring pair needs one ring only, and the Legendre
+    kernels take the one-ring contraction (the equator ring, alone in its pair, counts as north).
+    H and the weighted adjoint against the oracle for several tile shapes, 2 RHS."""
+    N, L, R = 16, 40, 2
+    rng = np.random.default_rng({"north": 7, "south": 8, "north_with_equator": 9}[hemi])
+    th, ph = O.pixel_angles(N)
+    z = np.cos(th)
+    sel = {"north": z > 0.05, "south": z < -0.05, "north_with_equator": z > -1e-12}[hemi]
+    ninv = np.where(sel, 1.0 + rng.random(12 * N * N), 0.0)
+    w = O.Weights(N, ninv, 1e-3)
+    pairs = [(S.random_alm(L, rng), S.random_alm(L, rng)) for _ in range(R)]
+    refs = [np.stack(O.apply_H(N, L, w, *q)) for q in pairs]
+    tol = TOL64 if prec == A.F64 else tol32(L)
+    shapes = [(1, 1, 1), (2, 4, 1), (1, 2, 2)] if prec == A.F64 else [(1, 5, 1), (2, 3, 1), (1, 1, 2)]
+    for P, PA, RG in shapes:
+        p = A.akra_plan_create(N, L)
+        A.akra_plan_set_weights(p, torch.from_numpy(ninv).to(DEV), 1e-3)
+        A.akra_plan_set_shape(p, prec, R, P, PA if RG == 1 else 1, RG)
+        y = A.akra_apply_H(p, prec, alm_dev(pairs, prec)).to(torch.complex128).cpu().numpy()
+        for r in range(R):
+            assert rel(y[r], refs[r]) < tol, (hemi, prec, P, PA, RG, r, rel(y[r], refs[r]))
