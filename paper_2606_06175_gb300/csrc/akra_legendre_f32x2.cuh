@@ -114,6 +114,10 @@ __device__ __forceinline__ void leg_adjoint_item_f2(const LegArgs<float> &a, con
     bool dk[P];                  // this warp's pairs of slot k run the difference form (warp-uniform)
     int my_first = kNeverLive;
     bool any_diff = false;
+    int my_side = 3;
+    int rn[P], rs[P];            // the pair's north and south rings
+    // Q: the spin-paired Φ' data; with one ring per pair (side 1: north, 2: south) only Q[.][.][0..1]
+    // = ((Xa.re, Xb.re), (Xa.im, Xb.im)), Xa / Xb the partners of 2λ / (-2)λ
     float2 Q[P][RG][4];
 #pragma unroll
     for (int k = 0; k < P; k++) {
@@ -132,6 +136,7 @@ __device__ __forceinline__ void leg_adjoint_item_f2(const LegArgs<float> &a, con
             ui = uinfo[AKRA_IX(u, nunit_all, kDbgUnitInfo)];
             polar = ui.x >= kDiffX;
             gs[k] = start[AKRA_IX((size_t)m * nunit_all + u, tbound, kDbgStart)].x;
+            my_side = side_join(my_side, unit_side(ui, ring_active, nring));
         }
         dk[k] = __any_sync(0xffffffffu, polar);
         any_diff |= dk[k];
@@ -141,35 +146,53 @@ __device__ __forceinline__ void leg_adjoint_item_f2(const LegArgs<float> &a, con
             X2[k] = make_float2(x, x);
         }
         my_first = min(my_first, gs[k]);
+        rn[k] = ui.ring_n;
+        rs[k] = ui.ring_s;
+    }
+    // one ring per pair over the whole warp (a footprint in one hemisphere): the contraction keeps
+    // a = Σ 2λ Xa and b = Σ (-2)λ Xb and forms E and B from them after the sum over the pairs
+    const int side = warp_side(my_side);
+#pragma unroll
+    for (int k = 0; k < P; k++) {
 #pragma unroll
         for (int rr = 0; rr < RG; rr++) {
             const int r = r0 + rr;
             float2 Pv[2], Qv[2];
 #pragma unroll
-            for (int side = 0; side < 2; side++) {
-                const int ring = side == 0 ? ui.ring_n : ui.ring_s;
-                Pv[side] = make_float2(0.f, 0.f);
-                Qv[side] = make_float2(0.f, 0.f);
+            for (int sd = 0; sd < 2; sd++) {
+                const int ring = sd == 0 ? rn[k] : rs[k];
+                Pv[sd] = make_float2(0.f, 0.f);
+                Qv[sd] = make_float2(0.f, 0.f);
                 if (ring < 0 || r >= R) continue;
                 if (ring_active && !ring_active[AKRA_IX(ring, nring, kDbgRingActive)]) continue;
                 const size_t pb = ((size_t)r * nring + ring) * row + L;   // Φ'(ring, m = 0)
                 const float2 g = phi[AKRA_IX(pb + m, pbound, kDbgPhiRead)];
                 const float2 gm = phi[AKRA_IX(pb - m, pbound, kDbgPhiRead)];
-                Pv[side] = g;
-                Qv[side] = make_float2(gm.x, -gm.y);
+                Pv[sd] = g;
+                Qv[sd] = make_float2(gm.x, -gm.y);
             }
-            const float2 u1 = make_float2(Pv[0].x + Qv[1].x, Pv[0].y + Qv[1].y);
-            const float2 u2 = make_float2(Qv[0].x + Pv[1].x, Qv[0].y + Pv[1].y);
-            const float2 u3 = make_float2(Pv[0].x - Qv[1].x, Pv[0].y - Qv[1].y);
-            const float2 u4 = make_float2(Pv[1].x - Qv[0].x, Pv[1].y - Qv[0].y);
-            const float2 x1 = swap ? u3 : u1;
-            const float2 x2 = swap ? make_float2(-u4.x, -u4.y) : u2;
-            const float2 x3 = swap ? u1 : u3;
-            const float2 x4 = swap ? make_float2(-u2.x, -u2.y) : u4;
-            Q[k][rr][0] = make_float2(x1.x, x2.x);
-            Q[k][rr][1] = make_float2(x1.y, x2.y);
-            Q[k][rr][2] = make_float2(x3.x, x4.x);
-            Q[k][rr][3] = make_float2(x3.y, x4.y);
+            if (side == 1) {          // north: Xa = P_N, Xb = Q_N
+                Q[k][rr][0] = make_float2(Pv[0].x, Qv[0].x);
+                Q[k][rr][1] = make_float2(Pv[0].y, Qv[0].y);
+                Q[k][rr][2] = Q[k][rr][3] = make_float2(0.f, 0.f);
+            } else if (side == 2) {   // south: Xa = Q_S, Xb = P_S
+                Q[k][rr][0] = make_float2(Qv[1].x, Pv[1].x);
+                Q[k][rr][1] = make_float2(Qv[1].y, Pv[1].y);
+                Q[k][rr][2] = Q[k][rr][3] = make_float2(0.f, 0.f);
+            } else {
+                const float2 u1 = make_float2(Pv[0].x + Qv[1].x, Pv[0].y + Qv[1].y);
+                const float2 u2 = make_float2(Qv[0].x + Pv[1].x, Qv[0].y + Pv[1].y);
+                const float2 u3 = make_float2(Pv[0].x - Qv[1].x, Pv[0].y - Qv[1].y);
+                const float2 u4 = make_float2(Pv[1].x - Qv[0].x, Pv[1].y - Qv[0].y);
+                const float2 x1 = swap ? u3 : u1;
+                const float2 x2 = swap ? make_float2(-u4.x, -u4.y) : u2;
+                const float2 x3 = swap ? u1 : u3;
+                const float2 x4 = swap ? make_float2(-u2.x, -u2.y) : u4;
+                Q[k][rr][0] = make_float2(x1.x, x2.x);
+                Q[k][rr][1] = make_float2(x1.y, x2.y);
+                Q[k][rr][2] = make_float2(x3.x, x4.x);
+                Q[k][rr][3] = make_float2(x3.y, x4.y);
+            }
         }
     }
 
@@ -216,7 +239,7 @@ __device__ __forceinline__ void leg_adjoint_item_f2(const LegArgs<float> &a, con
 
         // K l-steps (slot of step kk = parity of kk), each step's 4 RG sums stored at once into
         // this lane's column of the warp's transpose buffer, then the warp reduction
-#define AKRA_F2_ADJ_KBLOCK(GATED, DIFF)                                                         \
+#define AKRA_F2_ADJ_KBLOCK(GATED, DIFF, SIDE)                                                   \
     for (int kb = 0; kb < nkb; kb++) {                                                          \
         _Pragma("unroll") for (int kk = 0; kk < K; kk++) {                                      \
             const bool slotA = (kk & 1) == 0;                                                   \
@@ -237,13 +260,26 @@ __device__ __forceinline__ void leg_adjoint_item_f2(const LegArgs<float> &a, con
                     const float2 cx = (DIFF && dk[k] && ((kb * K + kk) & 2)) ? make_float2(-cur.x, -cur.y) : cur; \
                     const float2 lam = (GATED && e[k] != 0) ? make_float2(0.f, 0.f) : cx;       \
                     _Pragma("unroll") for (int rr = 0; rr < RG; rr++)                           \
-                        _Pragma("unroll") for (int j = 0; j < 4; j++)                           \
+                        _Pragma("unroll") for (int j = 0; j < ((SIDE) == 0 ? 4 : 2); j++)       \
                             F[rr][j] = f2fma(lam, Q[k][rr][j], F[rr][j]);                       \
                 }                                                                               \
             }                                                                                   \
             _Pragma("unroll") for (int rr = 0; rr < RG; rr++) {                                 \
                 float *col = &tr[(kk * RG + rr) * 4][lane];                                     \
-                if (slotA) {                                                                    \
+                if ((SIDE) == 1) {                                                              \
+                    /* north: E = a + b, B = a - b */                                           \
+                    col[0 * 36] = F[rr][0].x + F[rr][0].y;                                      \
+                    col[1 * 36] = F[rr][1].x + F[rr][1].y;                                      \
+                    col[2 * 36] = F[rr][0].x - F[rr][0].y;                                      \
+                    col[3 * 36] = F[rr][1].x - F[rr][1].y;                                      \
+                } else if ((SIDE) == 2) {                                                       \
+                    /* south: E = s (a + b), B = s (b - a), s = +1 in slot A unless swapped */  \
+                    const float sg = (slotA != swap) ? 1.f : -1.f;                              \
+                    col[0 * 36] = sg * (F[rr][0].x + F[rr][0].y);                               \
+                    col[1 * 36] = sg * (F[rr][1].x + F[rr][1].y);                               \
+                    col[2 * 36] = sg * (F[rr][0].y - F[rr][0].x);                               \
+                    col[3 * 36] = sg * (F[rr][1].y - F[rr][1].x);                               \
+                } else if (slotA) {                                                             \
                     col[0 * 36] = F[rr][0].x + F[rr][0].y;                                      \
                     col[1 * 36] = F[rr][1].x + F[rr][1].y;                                      \
                     col[2 * 36] = F[rr][2].x + F[rr][2].y;                                      \
@@ -297,13 +333,18 @@ __device__ __forceinline__ void leg_adjoint_item_f2(const LegArgs<float> &a, con
         }                                                                                       \
     }
 
+#define AKRA_F2_ADJ_SIDES(GATED, DIFF)                                                          \
+    if (side == 2) { AKRA_F2_ADJ_KBLOCK(GATED, DIFF, 2) }                                       \
+    else if (side == 1) { AKRA_F2_ADJ_KBLOCK(GATED, DIFF, 1) }                                  \
+    else { AKRA_F2_ADJ_KBLOCK(GATED, DIFF, 0) }
         if (blk_diff) {
-            AKRA_F2_ADJ_KBLOCK(true, true)   // a block with pairs near a pole (rare)
+            AKRA_F2_ADJ_SIDES(true, true)   // a block with pairs near a pole (rare)
         } else if (all_live) {
-            AKRA_F2_ADJ_KBLOCK(false, false)
+            AKRA_F2_ADJ_SIDES(false, false)
         } else {
-            AKRA_F2_ADJ_KBLOCK(true, false)
+            AKRA_F2_ADJ_SIDES(true, false)
         }
+#undef AKRA_F2_ADJ_SIDES
 #undef AKRA_F2_ADJ_KBLOCK
         }
         __syncthreads();

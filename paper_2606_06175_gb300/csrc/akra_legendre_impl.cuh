@@ -64,6 +64,29 @@ __device__ __forceinline__ void start_diff(const float2 *__restrict__ dseeds, si
     }
 }
 
+// which rings of a unit the operator needs (weighted operators list only the active rings):
+// 0 both (or every ring), 1 the north ring alone (or the equator ring), 2 the south ring alone,
+// 3 no unit.  The warp takes the one-ring contraction when all its units are of one such kind.
+__device__ __forceinline__ int unit_side(const UnitInfo &ui, const unsigned char *ring_active, int nring)
+{
+    (void)nring;
+    if (!ring_active) return 0;
+    const bool an = ring_active[AKRA_IX(ui.ring_n, nring, kDbgRingActive)] != 0;
+    const bool as = ui.ring_s >= 0 && ring_active[AKRA_IX(ui.ring_s, nring, kDbgRingActive)] != 0;
+    return an && as ? 0 : an ? 1 : as ? 2 : 0;
+}
+
+__device__ __forceinline__ int warp_side(int mine)
+{
+    // mine: this lane's common side over its slots (3: no unit); 0 unless the warp agrees
+    const bool all1 = __all_sync(0xffffffffu, mine == 1 || mine == 3);
+    const bool all2 = __all_sync(0xffffffffu, mine == 2 || mine == 3);
+    return all1 ? 1 : all2 ? 2 : 0;
+}
+
+// fold one slot's side into the lane's common side (3: none yet, 0: mixed)
+__device__ __forceinline__ int side_join(int acc, int s) { return acc == 3 ? s : (acc == s ? acc : 0); }
+
 }  // namespace akra
 
 #include "akra_legendre_f32x2.cuh"   // FP32 items with paired FMAs (use TL, block_min_start)
@@ -71,7 +94,10 @@ __device__ __forceinline__ void start_diff(const float2 *__restrict__ dseeds, si
 namespace akra {
 
 // ---------------------------------------------------------------------------
-// synthesis: Φ(ring, ±m) for every ring of the listed units
+// synthesis: Φ(ring, ±m) for every ring of the listed units.  Where only one ring of a pair is
+// needed (a footprint in one hemisphere), a warp whose pairs all need the same single ring
+// accumulates that ring's two sums directly -- the north ring takes even + odd terms, the south
+// ring even - odd (sign folded per slot) -- 4 FMA per step and RHS instead of 8.
 // ---------------------------------------------------------------------------
 template <typename T, int P, int RG, int NT>
 __device__ __forceinline__ void leg_synth_item(const LegArgs<T> &a, const int m, const int chunk,
@@ -103,6 +129,7 @@ __device__ __forceinline__ void leg_synth_item(const LegArgs<T> &a, const int m,
     T acc[P][RG][16];
     int my_first = kNeverLive;
     bool any_diff = false;
+    int my_side = 3;
 #pragma unroll
     for (int k = 0; k < P; k++) {
         const int iu = (chunk * P + k) * NT + tid;
@@ -114,6 +141,7 @@ __device__ __forceinline__ void leg_synth_item(const LegArgs<T> &a, const int m,
         bool polar = false;
         if (uid[k] >= 0) {
             const UnitInfo ui = uinfo[AKRA_IX(uid[k], nunit_all, kDbgUnitInfo)];
+            my_side = side_join(my_side, unit_side(ui, ring_active, nring));
             x[k] = (T)ui.x;
             y[k] = (T)(-exp2(2.0 * ui.ls + 1.0));   // x - 1 = -2 sin^2(θ/2), accurate near the pole
             polar = std::is_same<T, float>::value && ui.x >= kDiffX;
@@ -128,6 +156,7 @@ __device__ __forceinline__ void leg_synth_item(const LegArgs<T> &a, const int m,
             for (int j = 0; j < 16; j++) acc[k][r][j] = 0;
     }
     const int warp_first = __reduce_min_sync(0xffffffffu, my_first);
+    const int side = warp_side(my_side);
     const int l_first = block_min_start<NT>(my_first);
     const bool blk_diff = __syncthreads_or(any_diff) != 0;   // block-uniform
     __shared__ float2 s_cb[TL];   // difference form: {(A'-2) + c', (A'-2) - c'} per step
@@ -175,7 +204,7 @@ __device__ __forceinline__ void leg_synth_item(const LegArgs<T> &a, const int m,
         // one l-step: contract at l (slot S = parity of l - l0), then recur to l+1.
         // vp = 2λ, vm = (-2)λ; accumulators per slot: P1 = Σ c 2λ, P2 = Σ d (-2)λ,
         // P3 = Σ c (-2)λ, P4 = Σ d 2λ (complex)
-#define AKRA_SYNTH_STEP(I, S, GATED, CA, CC, DIFF)                                                  \
+#define AKRA_SYNTH_STEP(I, S, GATED, CA, CC, DIFF, SIDE)                                            \
     {                                                                                       \
         bool any = true;                                                                    \
         if (GATED) {                                                                        \
@@ -189,15 +218,27 @@ __device__ __forceinline__ void leg_synth_item(const LegArgs<T> &a, const int m,
                 const T lm = (GATED && e[k] != 0) ? T(0) : ((S) == 0 ? vm[k] : vmo[k]);     \
                 _Pragma("unroll") for (int r = 0; r < RG; r++) {                            \
                     const V4 a = s_alm[I][r];                                               \
-                    T *ac = &acc[k][r][(S) * 8];                                            \
-                    ac[0] = fma(a.x, lp, ac[0]);                                            \
-                    ac[1] = fma(a.y, lp, ac[1]);                                            \
-                    ac[2] = fma(a.z, lm, ac[2]);                                            \
-                    ac[3] = fma(a.w, lm, ac[3]);                                            \
-                    ac[4] = fma(a.x, lm, ac[4]);                                            \
-                    ac[5] = fma(a.y, lm, ac[5]);                                            \
-                    ac[6] = fma(a.z, lp, ac[6]);                                            \
-                    ac[7] = fma(a.w, lp, ac[7]);                                            \
+                    if ((SIDE) == 0) {                                                      \
+                        T *ac = &acc[k][r][(S) * 8];                                        \
+                        ac[0] = fma(a.x, lp, ac[0]);                                        \
+                        ac[1] = fma(a.y, lp, ac[1]);                                        \
+                        ac[2] = fma(a.z, lm, ac[2]);                                        \
+                        ac[3] = fma(a.w, lm, ac[3]);                                        \
+                        ac[4] = fma(a.x, lm, ac[4]);                                        \
+                        ac[5] = fma(a.y, lm, ac[5]);                                        \
+                        ac[6] = fma(a.z, lp, ac[6]);                                        \
+                        ac[7] = fma(a.w, lp, ac[7]);                                        \
+                    } else {                                                                \
+                        /* one ring: north P1 = Σ c 2λ, P2 = Σ d (-2)λ over both parities;  */ \
+                        /* south P3 = Σ ± c (-2)λ, P4 = Σ ± d 2λ, + for slot A, - for slot B */ \
+                        const T u = (SIDE) == 1 ? lp : ((S) == 0 ? lm : -lm);               \
+                        const T v = (SIDE) == 1 ? lm : ((S) == 0 ? lp : -lp);               \
+                        T *ac = &acc[k][r][0];                                              \
+                        ac[0] = fma(a.x, u, ac[0]);                                         \
+                        ac[1] = fma(a.y, u, ac[1]);                                         \
+                        ac[2] = fma(a.z, v, ac[2]);                                         \
+                        ac[3] = fma(a.w, v, ac[3]);                                         \
+                    }                                                                       \
                 }                                                                           \
             }                                                                               \
         }                                                                                   \
@@ -230,28 +271,28 @@ __device__ __forceinline__ void leg_synth_item(const LegArgs<T> &a, const int m,
         }                                                                                   \
     }
 
+#define AKRA_SYNTH_LOOP(GATED, DIFF, SIDE)                                                  \
+    for (int i = 0; i < nl; i += 2) {                                                       \
+        const V4 cc = s_coef[i >> 1];                                                       \
+        AKRA_SYNTH_STEP(i, 0, GATED, cc.x, cc.y, DIFF, SIDE)                                \
+        AKRA_SYNTH_STEP(i + 1, 1, GATED, cc.z, cc.w, DIFF, SIDE)                            \
+    }
+#define AKRA_SYNTH_SIDES(GATED, DIFF)                                                       \
+    if (side == 2) { AKRA_SYNTH_LOOP(GATED, DIFF, 2) }                                      \
+    else if (side == 1) { AKRA_SYNTH_LOOP(GATED, DIFF, 1) }                                 \
+    else { AKRA_SYNTH_LOOP(GATED, DIFF, 0) }
         if (!(std::is_same<T, float>::value && blk_diff)) {
             if (all_live) {
-                for (int i = 0; i < nl; i += 2) {
-                    const V4 cc = s_coef[i >> 1];
-                    AKRA_SYNTH_STEP(i, 0, false, cc.x, cc.y, false)
-                    AKRA_SYNTH_STEP(i + 1, 1, false, cc.z, cc.w, false)
-                }
+                AKRA_SYNTH_SIDES(false, false)
             } else {
-                for (int i = 0; i < nl; i += 2) {
-                    const V4 cc = s_coef[i >> 1];
-                    AKRA_SYNTH_STEP(i, 0, true, cc.x, cc.y, false)
-                    AKRA_SYNTH_STEP(i + 1, 1, true, cc.z, cc.w, false)
-                }
+                AKRA_SYNTH_SIDES(true, false)
             }
         } else if constexpr (std::is_same<T, float>::value) {
             // a block with pairs near a pole (rare): some warps run the difference form
-            for (int i = 0; i < nl; i += 2) {
-                const V4 cc = s_coef[i >> 1];
-                AKRA_SYNTH_STEP(i, 0, true, cc.x, cc.y, true)
-                AKRA_SYNTH_STEP(i + 1, 1, true, cc.z, cc.w, true)
-            }
+            AKRA_SYNTH_SIDES(true, true)
         }
+#undef AKRA_SYNTH_SIDES
+#undef AKRA_SYNTH_LOOP
 #undef AKRA_SYNTH_STEP
     }
 
@@ -268,6 +309,19 @@ __device__ __forceinline__ void leg_synth_item(const LegArgs<T> &a, const int m,
         for (int rr = 0; rr < RG; rr++) {
             const int r = r0 + rr;
             if (r >= R) continue;
+            if (side != 0) {
+                // one ring: its Φ(m) and conj Φ(-m) directly (south: even - odd, i.e. the sign of
+                // slot A, which holds odd l + m when l0 + m is odd)
+                const int ring = side == 1 ? ui.ring_n : ui.ring_s;
+                if (ring < 0) continue;
+                if (ring_active && !ring_active[AKRA_IX(ring, nring, kDbgRingActive)]) continue;
+                const T sg = (side == 2 && swap) ? T(-1) : T(1);
+                const T *ac = acc[k][rr];
+                const size_t pb = ((size_t)r * nring + ring) * row + L;   // Φ(ring, m = 0)
+                phi[AKRA_IX(pb + m, pbound, kDbgPhiWrite)] = C2{sg * ac[0], sg * ac[1]};
+                if (m > 0) phi[AKRA_IX(pb - m, pbound, kDbgPhiWrite)] = C2{sg * ac[2], -(sg * ac[3])};
+                continue;
+            }
             T se[8], so[8];
 #pragma unroll
             for (int j = 0; j < 8; j++) {
@@ -277,12 +331,12 @@ __device__ __forceinline__ void leg_synth_item(const LegArgs<T> &a, const int m,
             // north: Φ(m) = P1,  conj Φ(-m) = P2        (even + odd)
             // south: Φ(m) = P3,  conj Φ(-m) = P4        (even - odd)
 #pragma unroll
-            for (int side = 0; side < 2; side++) {
-                const int ring = side == 0 ? ui.ring_n : ui.ring_s;
+            for (int sd = 0; sd < 2; sd++) {
+                const int ring = sd == 0 ? ui.ring_n : ui.ring_s;
                 if (ring < 0) continue;
                 if (ring_active && !ring_active[AKRA_IX(ring, nring, kDbgRingActive)]) continue;
-                const int o = side == 0 ? 0 : 4;
-                const T sg = side == 0 ? T(1) : T(-1);
+                const int o = sd == 0 ? 0 : 4;
+                const T sg = sd == 0 ? T(1) : T(-1);
                 const T fr = se[o + 0] + sg * so[o + 0], fi = se[o + 1] + sg * so[o + 1];
                 const T gr = se[o + 2] + sg * so[o + 2], gi = se[o + 3] + sg * so[o + 3];
                 const size_t pb = ((size_t)r * nring + ring) * row + L;   // Φ(ring, m = 0)
@@ -391,6 +445,8 @@ __device__ __forceinline__ void leg_adjoint_item(
     //   E += 2λ X1 + (-2)λ X2,  B += 2λ X3 + (-2)λ X4;   slot B: E += 2λ X3 - (-2)λ X4,
     //   B += 2λ X1 - (-2)λ X2   (X = U1..U4, or U3, -U4, U1, -U2 when l0+m is odd)
     C2 X1[P][RG], X2[P][RG], X3[P][RG], X4[P][RG];
+    int rn[P], rs[P];
+    int my_side = 3;
 #pragma unroll
     for (int k = 0; k < P; k++) {
         // each warp holds 32 P consecutive pairs (close in latitude, so close in start point)
@@ -401,39 +457,57 @@ __device__ __forceinline__ void leg_adjoint_item(
         vp[k] = vm[k] = vpo[k] = vmo[k] = 0;
         e[k] = 0;
         gs[k] = kNeverLive;
-        UnitInfo ui;
-        ui.ring_n = ui.ring_s = -1;
+        rn[k] = rs[k] = -1;
         if (u >= 0) {
-            ui = uinfo[AKRA_IX(u, nunit_all, kDbgUnitInfo)];
+            const UnitInfo ui = uinfo[AKRA_IX(u, nunit_all, kDbgUnitInfo)];
             x[k] = (T)ui.x;
             gs[k] = start[AKRA_IX((size_t)m * nunit_all + u, tbound, kDbgStart)].x;
+            rn[k] = ui.ring_n;
+            rs[k] = ui.ring_s;
+            my_side = side_join(my_side, unit_side(ui, ring_active, nring));
         }
         my_first = min(my_first, gs[k]);
+    }
+    // one ring per pair over the whole warp: X1 holds Xa (partner of 2λ), X2 Xb (of (-2)λ), and the
+    // contraction keeps a = Σ 2λ Xa, b = Σ (-2)λ Xb, from which E and B follow
+    const int side = warp_side(my_side);
+#pragma unroll
+    for (int k = 0; k < P; k++) {
 #pragma unroll
         for (int rr = 0; rr < RG; rr++) {
             const int r = r0 + rr;
             C2 Pv[2], Qv[2];
 #pragma unroll
-            for (int side = 0; side < 2; side++) {
-                const int ring = side == 0 ? ui.ring_n : ui.ring_s;
-                Pv[side] = C2{0, 0};
-                Qv[side] = C2{0, 0};
+            for (int sd = 0; sd < 2; sd++) {
+                const int ring = sd == 0 ? rn[k] : rs[k];
+                Pv[sd] = C2{0, 0};
+                Qv[sd] = C2{0, 0};
                 if (ring < 0 || r >= R) continue;
                 if (ring_active && !ring_active[AKRA_IX(ring, nring, kDbgRingActive)]) continue;
                 const size_t pb = ((size_t)r * nring + ring) * row + L;   // Φ'(ring, m = 0)
                 const C2 g = phi[AKRA_IX(pb + m, pbound, kDbgPhiRead)];
                 const C2 gm = phi[AKRA_IX(pb - m, pbound, kDbgPhiRead)];
-                Pv[side] = g;
-                Qv[side] = C2{gm.x, -gm.y};
+                Pv[sd] = g;
+                Qv[sd] = C2{gm.x, -gm.y};
             }
-            const C2 u1{Pv[0].x + Qv[1].x, Pv[0].y + Qv[1].y};
-            const C2 u2{Qv[0].x + Pv[1].x, Qv[0].y + Pv[1].y};
-            const C2 u3{Pv[0].x - Qv[1].x, Pv[0].y - Qv[1].y};
-            const C2 u4{Pv[1].x - Qv[0].x, Pv[1].y - Qv[0].y};
-            X1[k][rr] = swap ? u3 : u1;
-            X2[k][rr] = swap ? C2{-u4.x, -u4.y} : u2;
-            X3[k][rr] = swap ? u1 : u3;
-            X4[k][rr] = swap ? C2{-u2.x, -u2.y} : u4;
+            if (side == 1) {          // north: Xa = P_N, Xb = Q_N
+                X1[k][rr] = Pv[0];
+                X2[k][rr] = Qv[0];
+                X3[k][rr] = X4[k][rr] = C2{0, 0};
+            } else if (side == 2) {   // south: Xa = Q_S, Xb = P_S
+                X1[k][rr] = Qv[1];
+                X2[k][rr] = Pv[1];
+                X3[k][rr] = X4[k][rr] = C2{0, 0};
+            } else {
+                const C2 u1{Pv[0].x + Qv[1].x, Pv[0].y + Qv[1].y};
+                const C2 u2{Qv[0].x + Pv[1].x, Qv[0].y + Pv[1].y};
+                const C2 u3{Pv[0].x - Qv[1].x, Pv[0].y - Qv[1].y};
+                const C2 u4{Pv[1].x - Qv[0].x, Pv[1].y - Qv[0].y};
+                X1[k][rr] = swap ? u3 : u1;
+                X2[k][rr] = swap ? C2{-u4.x, -u4.y} : u2;
+                X3[k][rr] = swap ? u1 : u3;
+                X4[k][rr] = swap ? C2{-u2.x, -u2.y} : u4;
+            }
         }
     }
 
@@ -469,7 +543,7 @@ __device__ __forceinline__ void leg_adjoint_item(
         const int nkb = (nl + K - 1) / K;
 
         // K l-steps into ta[K][RG][4] (slot of step kk = parity of kk), then recur
-#define AKRA_ADJ_KBLOCK(GATED)                                                                  \
+#define AKRA_ADJ_KBLOCK(GATED, SIDE)                                                            \
     for (int kb = 0; kb < nkb; kb++) {                                                          \
         T ta[K][RG][4];                                                                         \
         _Pragma("unroll") for (int kk = 0; kk < K; kk++)                                        \
@@ -490,15 +564,23 @@ __device__ __forceinline__ void leg_adjoint_item(
                     const T lm0 = (GATED && e[k] != 0) ? T(0) : (slotA ? vm[k] : vmo[k]);       \
                     const T lm = slotA ? lm0 : -lm0;                                            \
                     _Pragma("unroll") for (int rr = 0; rr < RG; rr++) {                         \
-                        const C2 eP = slotA ? X1[k][rr] : X3[k][rr];                            \
-                        const C2 eM = slotA ? X2[k][rr] : X4[k][rr];                            \
-                        const C2 bP = slotA ? X3[k][rr] : X1[k][rr];                            \
-                        const C2 bM = slotA ? X4[k][rr] : X2[k][rr];                            \
                         T *t = ta[kk][rr];                                                      \
-                        t[0] = fma(lp, eP.x, fma(lm, eM.x, t[0]));                              \
-                        t[1] = fma(lp, eP.y, fma(lm, eM.y, t[1]));                              \
-                        t[2] = fma(lp, bP.x, fma(lm, bM.x, t[2]));                              \
-                        t[3] = fma(lp, bP.y, fma(lm, bM.y, t[3]));                              \
+                        if ((SIDE) == 0) {                                                      \
+                            const C2 eP = slotA ? X1[k][rr] : X3[k][rr];                        \
+                            const C2 eM = slotA ? X2[k][rr] : X4[k][rr];                        \
+                            const C2 bP = slotA ? X3[k][rr] : X1[k][rr];                        \
+                            const C2 bM = slotA ? X4[k][rr] : X2[k][rr];                        \
+                            t[0] = fma(lp, eP.x, fma(lm, eM.x, t[0]));                          \
+                            t[1] = fma(lp, eP.y, fma(lm, eM.y, t[1]));                          \
+                            t[2] = fma(lp, bP.x, fma(lm, bM.x, t[2]));                          \
+                            t[3] = fma(lp, bP.y, fma(lm, bM.y, t[3]));                          \
+                        } else {                                                                \
+                            /* one ring: a = Σ 2λ Xa, b = Σ (-2)λ Xb */                         \
+                            t[0] = fma(lp, X1[k][rr].x, t[0]);                                  \
+                            t[1] = fma(lp, X1[k][rr].y, t[1]);                                  \
+                            t[2] = fma(lm0, X2[k][rr].x, t[2]);                                 \
+                            t[3] = fma(lm0, X2[k][rr].y, t[3]);                                 \
+                        }                                                                       \
                     }                                                                           \
                 }                                                                               \
             }                                                                                   \
@@ -520,6 +602,19 @@ __device__ __forceinline__ void leg_adjoint_item(
                 }                                                                               \
             }                                                                                   \
         }                                                                                       \
+        if ((SIDE) != 0) {                                                                      \
+            /* (a, b) -> (E, B): north E = a + b, B = a - b; south E = s (a + b), B = s (b - a) */ \
+            _Pragma("unroll") for (int kk = 0; kk < K; kk++)                                    \
+                _Pragma("unroll") for (int rr = 0; rr < RG; rr++) {                             \
+                    T *t = ta[kk][rr];                                                          \
+                    const T sg = (SIDE) == 1 ? T(1) : ((((kk & 1) == 0) != swap) ? T(1) : T(-1)); \
+                    const T ar = t[0], ai = t[1], br = t[2], bi = t[3];                         \
+                    t[0] = sg * (ar + br);                                                      \
+                    t[1] = sg * (ai + bi);                                                      \
+                    t[2] = (SIDE) == 1 ? ar - br : sg * (br - ar);                              \
+                    t[3] = (SIDE) == 1 ? ai - bi : sg * (bi - ai);                              \
+                }                                                                               \
+        }                                                                                       \
         /* warp transpose through shared memory: lane L's value i goes to tr[i][L]; lane j */  \
         /* then sums row j, i.e. value j over all lanes */                                       \
         _Pragma("unroll") for (int kk = 0; kk < K; kk++)                                        \
@@ -536,11 +631,16 @@ __device__ __forceinline__ void leg_adjoint_item(
         }                                                                                       \
     }
 
+#define AKRA_ADJ_SIDES(GATED)                                                                   \
+    if (side == 2) { AKRA_ADJ_KBLOCK(GATED, 2) }                                                \
+    else if (side == 1) { AKRA_ADJ_KBLOCK(GATED, 1) }                                           \
+    else { AKRA_ADJ_KBLOCK(GATED, 0) }
         if (all_live) {
-            AKRA_ADJ_KBLOCK(false)
+            AKRA_ADJ_SIDES(false)
         } else {
-            AKRA_ADJ_KBLOCK(true)
+            AKRA_ADJ_SIDES(true)
         }
+#undef AKRA_ADJ_SIDES
 #undef AKRA_ADJ_KBLOCK
         }
         __syncthreads();
