@@ -309,6 +309,7 @@ struct akra_plan_s {
     int n_active_rings = 0;
     int *d_active_units = nullptr;           // units with an active ring
     int n_active_units = 0;
+    int one_side = 0;                        // every active unit needs only its north (1) / south (2) ring
     unsigned char *d_ring_active = nullptr;  // [nring] flag
 
     // workspaces (grown on demand)

@@ -125,7 +125,7 @@ static void launch_synth(akra_plan p, LegMode mode, const void *alm, void *phi, 
     k_leg_synth<T, P, RG, NT><<<grid, NT, 0, st>>>(a);
 }
 
-template <typename T, int P, int RG, int NT>
+template <typename T, int P, int RG, int NT, int ONE = 0>
 static int launch_adjoint(akra_plan p, const void *phi, void *partial, int R, const int *units,
                           int nunits, cudaStream_t st)
 {
@@ -133,7 +133,7 @@ static int launch_adjoint(akra_plan p, const void *phi, void *partial, int R, co
     a.phi_in = (const cx_t<T> *)phi;
     a.partial = (T *)partial;
     dim3 grid((unsigned)(p->lmax + 1) * a.nchunks, (R + RG - 1) / RG);
-    k_leg_adjoint<T, P, RG, NT><<<grid, NT, 0, st>>>(a);
+    k_leg_adjoint<T, P, RG, NT, ONE><<<grid, NT, 0, st>>>(a);
     return a.nchunks;
 }
 
@@ -167,6 +167,23 @@ akra_status legendre_adjoint(akra_plan p, const LegShape &s, const void *phi, vo
     *nchunks_out = 0;
     if (nunits <= 0) return AKRA_OK;
     const int pa = s.adjP();
+    {
+        // the active ring pairs of a one-hemisphere footprint all need the same single ring: the
+        // kernel compiled for that form alone (fewer registers); FP32 at 3-8 ring pairs per
+        // thread, FP64 at 1, 2 and 4, one RHS per block
+        const int one = (units != p->d_all_units && s.adjRG() == 1) ? p->one_side : 0;
+#define AKRA_A1(PP)                                                                          \
+        if (one && pa == PP) {                                                               \
+            *nchunks_out = one == 1 ? launch_adjoint<T, PP, 1, 128, 1>(p, phi, partial, R, units, nunits, st) \
+                                    : launch_adjoint<T, PP, 1, 128, 2>(p, phi, partial, R, units, nunits, st); \
+            AKRA_CUDA_TRY(cudaGetLastError());                                               \
+            p->launches++;                                                                   \
+            return AKRA_OK;                                                                  \
+        }
+        if constexpr (std::is_same<T, float>::value) { AKRA_A1(3) AKRA_A1(4) AKRA_A1(5) AKRA_A1(6) AKRA_A1(8) }
+        else { AKRA_A1(1) AKRA_A1(2) AKRA_A1(4) }
+#undef AKRA_A1
+    }
 #define AKRA_A(PP, RR)                                                                      \
     if (pa == PP && s.adjRG() == RR) {                                                      \
         *nchunks_out = launch_adjoint<T, PP, RR, 128>(p, phi, partial, R, units, nunits, st); \

@@ -77,7 +77,9 @@ __device__ __forceinline__ void f2_rescale(int k, float2 (&V)[P], float2 (&VO)[P
 // and B = (F2.x + F2.y) + i (F3.x + F3.y); for l - l0 odd, E = (F2.x - F2.y) + i (F3.x - F3.y) and
 // B = (F0.x - F0.y) + i (F1.x - F1.y).
 // ---------------------------------------------------------------------------
-template <int P, int RG, int NT>
+// ONE = 1 or 2: every ring pair of the launch needs only its north (1) or south (2) ring, so only
+// that form is compiled (half the Φ' registers); ONE = 0 decides per warp.
+template <int P, int RG, int NT, int ONE = 0>
 __device__ __forceinline__ void leg_adjoint_item_f2(const LegArgs<float> &a, const int m, const int chunk,
                                                     const int r0, float4 *s_cf, float *s_sig,
                                                     float (*s_red)[TL][RG][4], float (*s_tr)[32][36],
@@ -118,7 +120,7 @@ __device__ __forceinline__ void leg_adjoint_item_f2(const LegArgs<float> &a, con
     int rn[P], rs[P];            // the pair's north and south rings
     // Q: the spin-paired Φ' data; with one ring per pair (side 1: north, 2: south) only Q[.][.][0..1]
     // = ((Xa.re, Xb.re), (Xa.im, Xb.im)), Xa / Xb the partners of 2λ / (-2)λ
-    float2 Q[P][RG][4];
+    float2 Q[P][RG][ONE ? 2 : 4];
 #pragma unroll
     for (int k = 0; k < P; k++) {
         // each warp holds 32 P consecutive pairs (close in latitude, so close in start point)
@@ -151,7 +153,8 @@ __device__ __forceinline__ void leg_adjoint_item_f2(const LegArgs<float> &a, con
     }
     // one ring per pair over the whole warp (a footprint in one hemisphere): the contraction keeps
     // a = Σ 2λ Xa and b = Σ (-2)λ Xb and forms E and B from them after the sum over the pairs
-    const int side = warp_side(my_side);
+    const int side = ONE ? ONE : warp_side(my_side);
+    (void)my_side;
 #pragma unroll
     for (int k = 0; k < P; k++) {
 #pragma unroll
@@ -174,12 +177,10 @@ __device__ __forceinline__ void leg_adjoint_item_f2(const LegArgs<float> &a, con
             if (side == 1) {          // north: Xa = P_N, Xb = Q_N
                 Q[k][rr][0] = make_float2(Pv[0].x, Qv[0].x);
                 Q[k][rr][1] = make_float2(Pv[0].y, Qv[0].y);
-                Q[k][rr][2] = Q[k][rr][3] = make_float2(0.f, 0.f);
             } else if (side == 2) {   // south: Xa = Q_S, Xb = P_S
                 Q[k][rr][0] = make_float2(Qv[1].x, Pv[1].x);
                 Q[k][rr][1] = make_float2(Qv[1].y, Pv[1].y);
-                Q[k][rr][2] = Q[k][rr][3] = make_float2(0.f, 0.f);
-            } else {
+            } else if constexpr (ONE == 0) {
                 const float2 u1 = make_float2(Pv[0].x + Qv[1].x, Pv[0].y + Qv[1].y);
                 const float2 u2 = make_float2(Qv[0].x + Pv[1].x, Qv[0].y + Pv[1].y);
                 const float2 u3 = make_float2(Pv[0].x - Qv[1].x, Pv[0].y - Qv[1].y);
@@ -334,9 +335,13 @@ __device__ __forceinline__ void leg_adjoint_item_f2(const LegArgs<float> &a, con
     }
 
 #define AKRA_F2_ADJ_SIDES(GATED, DIFF)                                                          \
-    if (side == 2) { AKRA_F2_ADJ_KBLOCK(GATED, DIFF, 2) }                                       \
-    else if (side == 1) { AKRA_F2_ADJ_KBLOCK(GATED, DIFF, 1) }                                  \
-    else { AKRA_F2_ADJ_KBLOCK(GATED, DIFF, 0) }
+    if constexpr (ONE == 1) { AKRA_F2_ADJ_KBLOCK(GATED, DIFF, 1) }                              \
+    else if constexpr (ONE == 2) { AKRA_F2_ADJ_KBLOCK(GATED, DIFF, 2) }                         \
+    else {                                                                                      \
+        if (side == 2) { AKRA_F2_ADJ_KBLOCK(GATED, DIFF, 2) }                                   \
+        else if (side == 1) { AKRA_F2_ADJ_KBLOCK(GATED, DIFF, 1) }                              \
+        else { AKRA_F2_ADJ_KBLOCK(GATED, DIFF, 0) }                                             \
+    }
         if (blk_diff) {
             AKRA_F2_ADJ_SIDES(true, true)   // a block with pairs near a pole (rare)
         } else if (all_live) {

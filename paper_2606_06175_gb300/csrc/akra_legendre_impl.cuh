@@ -404,7 +404,7 @@ template <> struct TrStride<double> { static constexpr int v = 34; };
 // adjoint l-tile: 64 steps, shorter for FP64 with several RHS (48 KB of static smem)
 template <typename T, int RG> struct AdjTile { static constexpr int v = sizeof(T) == 8 ? 64 / RG : TL; };
 
-template <typename T, int P, int RG, int NT>
+template <typename T, int P, int RG, int NT, int ONE = 0>
 __device__ __forceinline__ void leg_adjoint_item(
     const LegArgs<T> &a, const int m, const int chunk, const int r0, v4_t<T> *s_coef,
     T (*s_red)[AdjTile<T, RG>::v][RG][4], T (*s_tr)[32][TrStride<T>::v])
@@ -444,6 +444,8 @@ __device__ __forceinline__ void leg_adjoint_item(
     // per unit and RHS, the partners of 2λ and (-2)λ in slot A (l - l0 even):
     //   E += 2λ X1 + (-2)λ X2,  B += 2λ X3 + (-2)λ X4;   slot B: E += 2λ X3 - (-2)λ X4,
     //   B += 2λ X1 - (-2)λ X2   (X = U1..U4, or U3, -U4, U1, -U2 when l0+m is odd)
+    // ONE = 1 or 2: every pair needs only its north / south ring (only the one-ring form is
+    // compiled, and X3, X4 are dead)
     C2 X1[P][RG], X2[P][RG], X3[P][RG], X4[P][RG];
     int rn[P], rs[P];
     int my_side = 3;
@@ -470,7 +472,8 @@ __device__ __forceinline__ void leg_adjoint_item(
     }
     // one ring per pair over the whole warp: X1 holds Xa (partner of 2λ), X2 Xb (of (-2)λ), and the
     // contraction keeps a = Σ 2λ Xa, b = Σ (-2)λ Xb, from which E and B follow
-    const int side = warp_side(my_side);
+    const int side = ONE ? ONE : warp_side(my_side);
+    (void)my_side;
 #pragma unroll
     for (int k = 0; k < P; k++) {
 #pragma unroll
@@ -632,9 +635,13 @@ __device__ __forceinline__ void leg_adjoint_item(
     }
 
 #define AKRA_ADJ_SIDES(GATED)                                                                   \
-    if (side == 2) { AKRA_ADJ_KBLOCK(GATED, 2) }                                                \
-    else if (side == 1) { AKRA_ADJ_KBLOCK(GATED, 1) }                                           \
-    else { AKRA_ADJ_KBLOCK(GATED, 0) }
+    if constexpr (ONE == 1) { AKRA_ADJ_KBLOCK(GATED, 1) }                                       \
+    else if constexpr (ONE == 2) { AKRA_ADJ_KBLOCK(GATED, 2) }                                  \
+    else {                                                                                      \
+        if (side == 2) { AKRA_ADJ_KBLOCK(GATED, 2) }                                            \
+        else if (side == 1) { AKRA_ADJ_KBLOCK(GATED, 1) }                                       \
+        else { AKRA_ADJ_KBLOCK(GATED, 0) }                                                      \
+    }
         if (all_live) {
             AKRA_ADJ_SIDES(false)
         } else {
@@ -659,8 +666,8 @@ __device__ __forceinline__ void leg_adjoint_item(
     }
 }
 
-// one adjoint work item: FP32 with paired FMAs, FP64 scalar
-template <typename T, int P, int RG, int NT>
+// one adjoint work item: FP32 with paired FMAs (ONE: see leg_adjoint_item_f2), FP64 scalar
+template <typename T, int P, int RG, int NT, int ONE = 0>
 __device__ __forceinline__ void adjoint_item(const LegArgs<T> &a, int m, int chunk, int r0)
 {
     if constexpr (std::is_same<T, float>::value) {
@@ -669,21 +676,21 @@ __device__ __forceinline__ void adjoint_item(const LegArgs<T> &a, int m, int chu
         __shared__ float s_red[NT / 32][TL][RG][4];
         __shared__ __align__(16) float s_tr[NT / 32][32][36];
         __shared__ float4 s_cfd[TL];
-        leg_adjoint_item_f2<P, RG, NT>(a, m, chunk, r0, s_cf, s_sig, s_red, s_tr, s_cfd);
+        leg_adjoint_item_f2<P, RG, NT, ONE>(a, m, chunk, r0, s_cf, s_sig, s_red, s_tr, s_cfd);
     } else {
         __shared__ v4_t<T> s_coef[AdjTile<T, RG>::v];
         __shared__ T s_red[NT / 32][AdjTile<T, RG>::v][RG][4];
         __shared__ __align__(16) T s_tr[NT / 32][32][TrStride<T>::v];
-        leg_adjoint_item<T, P, RG, NT>(a, m, chunk, r0, s_coef, s_red, s_tr);
+        leg_adjoint_item<T, P, RG, NT, ONE>(a, m, chunk, r0, s_coef, s_red, s_tr);
     }
 }
 
-template <typename T, int P, int RG, int NT>
+template <typename T, int P, int RG, int NT, int ONE = 0>
 __global__ void __launch_bounds__(NT) k_leg_adjoint(LegArgs<T> a)
 {
     if (a.skip && *a.skip) return;
     const int m = blockIdx.x / a.nchunks;
-    adjoint_item<T, P, RG, NT>(a, m, blockIdx.x - m * a.nchunks, blockIdx.y * RG);
+    adjoint_item<T, P, RG, NT, ONE>(a, m, blockIdx.x - m * a.nchunks, blockIdx.y * RG);
 }
 
 template <typename T, int P, int RG, int NT>

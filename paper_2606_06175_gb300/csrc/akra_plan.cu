@@ -844,10 +844,17 @@ extern "C" akra_status akra_plan_set_weights(akra_plan p, const double *d_ninv, 
     }
     std::vector<int> units;
     const int N = p->nside;
+    int one = -1;   // the common single ring side of the active units (-1: none yet, 0: mixed)
     for (int u = 0; u < p->nunit; u++) {
         const int rn = u, rs = (u + 1 < 2 * N) ? 4 * N - (u + 1) - 1 : -1;
-        if (active[rn] || (rs >= 0 && active[rs])) units.push_back(u);
+        const bool an = active[rn] != 0, as = rs >= 0 && active[rs] != 0;
+        if (an || as) {
+            units.push_back(u);
+            const int side = an && as ? 0 : an ? 1 : 2;
+            one = one < 0 ? side : (one == side ? one : 0);
+        }
     }
+    p->one_side = one > 0 ? one : 0;
     AKRA_CUDA_TRY(cudaMemcpy(p->d_ring_active, active.data(), nr, cudaMemcpyHostToDevice));
     if (!rings.empty())
         AKRA_CUDA_TRY(cudaMemcpy(p->d_active_rings, rings.data(), sizeof(int) * rings.size(),
