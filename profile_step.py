@@ -39,6 +39,8 @@ def main():
     ap.add_argument("--tc", type=int, default=0, metavar="G",
                     help="FP32 synthesis on the tensor core with RHS groups of G (with --rhs)")
     ap.add_argument("--rhs", type=int, default=1, help="right-hand sides of the H applications")
+    ap.add_argument("--south-only", action="store_true",
+                    help="drop the footprint's pixels at dec >= 0 (every active ring pair then needs its south ring alone)")
     ap.add_argument("--stages", action="store_true",
                     help="print the CUDA-event stage times of one H (akra_time_H_stages, 5 runs) as JSON")
     ap.add_argument("--batch", action="store_true",
@@ -76,8 +78,12 @@ def main():
         print("ok", A.akra_plan_describe(fp)["kernel_launches"])
         return
     sv = S.survey(N, "des", S.SEEDS["des2048"])
+    ninv = sv["ninv"]
+    if args.south_only:
+        z = S.pixel_positions(N)[0]
+        ninv = np.where(z < 0, ninv, 0.0)
     plan = A.akra_plan_create(N, L)
-    A.akra_plan_set_weights(plan, torch.from_numpy(sv["ninv"]).to(dev), 1e-3)
+    A.akra_plan_set_weights(plan, torch.from_numpy(ninv).to(dev), 1e-3)
     prec = A.F32 if args.prec == "f32" else A.F64
     R = args.rhs
     if args.shape:
