@@ -86,6 +86,9 @@ typedef struct {
                                          starts where its harmonics exceed 2^-40 (Sec. II B
                                          recurrences; the terms below are negligible) */
     long long legendre_steps_f64;     /* the same for FP64 (threshold 2^-90) */
+    long long legendre_steps_f32_one_ring;  /* the part of legendre_steps_f32 over pairs that need
+                                               one ring only (one-ring contraction, half the FMAs) */
+    long long legendre_steps_f64_one_ring;  /* the same for FP64 */
 } akra_plan_desc;
 
 /* Create a plan for (nside, lmax): HEALPix ring tables, spin-2 recurrence tables, ring

@@ -43,7 +43,9 @@ class PlanDesc(ctypes.Structure):
                 ("lambda_", ctypes.c_double), ("lambda_eff", ctypes.c_double),
                 ("precond", ctypes.c_double), ("omega", ctypes.c_double),
                 ("device_bytes", ctypes.c_size_t), ("kernel_launches", ctypes.c_longlong),
-                ("legendre_steps_f32", ctypes.c_longlong), ("legendre_steps_f64", ctypes.c_longlong)]
+                ("legendre_steps_f32", ctypes.c_longlong), ("legendre_steps_f64", ctypes.c_longlong),
+                ("legendre_steps_f32_one_ring", ctypes.c_longlong),
+                ("legendre_steps_f64_one_ring", ctypes.c_longlong)]
 
 
 EXPORTS = ["akra_plan_create", "akra_plan_destroy", "akra_last_error", "akra_version",

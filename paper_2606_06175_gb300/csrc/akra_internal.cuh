@@ -264,6 +264,7 @@ struct akra_plan_s {
     unsigned long long *d_steps = nullptr;   // [2 nunit] Σ_m (lmax + 1 - g) per ring pair, FP32 / FP64
     std::vector<unsigned long long> steps32, steps64;   // host copies
     std::vector<int> h_active_units;         // host copy of the active pairs
+    std::vector<unsigned char> h_unit_one_ring;   // per active unit: needs one ring only
     double *d_D64 = nullptr;                 // [lmax + 1] KS kernel D_l
     float *d_D32 = nullptr;
     double2 *d_tw64 = nullptr;               // ring twiddles e^{iπ t/n}

@@ -782,11 +782,16 @@ extern "C" akra_status akra_plan_describe(akra_plan p, akra_plan_desc *out)
     out->omega = p->omega;
     out->device_bytes = plan_device_bytes(p);
     out->kernel_launches = p->launches;
-    long long s32 = 0, s64 = 0;
+    long long s32 = 0, s64 = 0, o32 = 0, o64 = 0;
     if (p->has_weights) {
-        for (int u : p->h_active_units) {
+        for (size_t k = 0; k < p->h_active_units.size(); k++) {
+            const int u = p->h_active_units[k];
             s32 += (long long)p->steps32[u];
             s64 += (long long)p->steps64[u];
+            if (p->h_unit_one_ring[k]) {
+                o32 += (long long)p->steps32[u];
+                o64 += (long long)p->steps64[u];
+            }
         }
     } else {
         for (int u = 0; u < p->nunit; u++) {
@@ -796,6 +801,8 @@ extern "C" akra_status akra_plan_describe(akra_plan p, akra_plan_desc *out)
     }
     out->legendre_steps_f32 = s32;
     out->legendre_steps_f64 = s64;
+    out->legendre_steps_f32_one_ring = o32;
+    out->legendre_steps_f64_one_ring = o64;
     return AKRA_OK;
 }
 
@@ -843,6 +850,7 @@ extern "C" akra_status akra_plan_set_weights(akra_plan p, const double *d_ninv, 
         return AKRA_EINVAL;
     }
     std::vector<int> units;
+    std::vector<unsigned char> one_ring;
     const int N = p->nside;
     int one = -1;   // the common single ring side of the active units (-1: none yet, 0: mixed)
     for (int u = 0; u < p->nunit; u++) {
@@ -850,6 +858,7 @@ extern "C" akra_status akra_plan_set_weights(akra_plan p, const double *d_ninv, 
         const bool an = active[rn] != 0, as = rs >= 0 && active[rs] != 0;
         if (an || as) {
             units.push_back(u);
+            one_ring.push_back(an && as ? 0 : 1);
             const int side = an && as ? 0 : an ? 1 : 2;
             one = one < 0 ? side : (one == side ? one : 0);
         }
@@ -865,6 +874,7 @@ extern "C" akra_status akra_plan_set_weights(akra_plan p, const double *d_ninv, 
     p->n_active_rings = (int)rings.size();
     p->n_active_units = (int)units.size();
     p->h_active_units = units;
+    p->h_unit_one_ring = one_ring;
     p->lambda = lambda;
     p->lambda_eff = cnt > 0 ? lambda * sum / cnt : 0.0;
     p->precond = 1.0 / (sum / (double)p->npix + p->lambda_eff);

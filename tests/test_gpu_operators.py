@@ -442,6 +442,9 @@ def test_lane_steps_count_the_plans_steps():
     ninv = np.where(np.cos(th) < -0.2, 1.0, 0.0)
     A.akra_plan_set_weights(p, torch.from_numpy(ninv).to(DEV), 1e-3)
     d = A.akra_plan_describe(p)
+    # a southern footprint: every active pair needs its south ring only
+    assert d["legendre_steps_f32_one_ring"] == d["legendre_steps_f32"] > 0
+    assert d["legendre_steps_f64_one_ring"] == d["legendre_steps_f64"] > 0
     for prec, key in ((A.F32, "legendre_steps_f32"), (A.F64, "legendre_steps_f64")):
         for adj in (False, True):
             for P in (1, 3, 4, 8):
