@@ -515,3 +515,38 @@ def test_one_hemisphere_footprint_matches_oracle(hemi, prec):
         y = A.akra_apply_H(p, prec, alm_dev(pairs, prec)).to(torch.complex128).cpu().numpy()
         for r in range(R):
             assert rel(y[r], refs[r]) < tol, (hemi, prec, P, PA, RG, r, rel(y[r], refs[r]))
+
+
+@pytest.mark.parametrize("prec", [A.F32, A.F64])
+def test_mostly_one_ring_footprint_matches_oracle(prec):
+    """A southern footprint with a thin band just north of the equator: nearly every active ring
+    pair needs its south ring only and one needs both, so one warp of the Legendre kernels takes
+    the two-ring contraction and the rest the one-ring one. H against the oracle for every
+    adjoint width."""
+    N, L, R = 16, 40, 2
+    rng = np.random.default_rng(41)
+    th, ph = O.pixel_angles(N)
+    z = np.cos(th)
+    ninv = np.where(z < 0.08, 1.0 + rng.random(12 * N * N), 0.0)
+    # the unit mix the test relies on: at least 90 % of the active pairs need one ring, not all
+    act = [bool(np.any(ninv[first:first + n] > 0)) for _, _, n, _, first in O.rings(N)]
+    nr = len(act)
+    units = [(act[u], act[nr - 1 - u] if nr - 1 - u != u else False) for u in range((nr + 1) // 2)]
+    both = sum(1 for a, b in units if a and b)
+    active = sum(1 for a, b in units if a or b)
+    assert 0 < both and (active - both) * 10 >= active * 9, (both, active)
+    w = O.Weights(N, ninv, 1e-3)
+    pairs = [(S.random_alm(L, rng), S.random_alm(L, rng)) for _ in range(R)]
+    refs = [np.stack(O.apply_H(N, L, w, *q)) for q in pairs]
+    tol = TOL64 if prec == A.F64 else tol32(L)
+    p = A.akra_plan_create(N, L)
+    A.akra_plan_set_weights(p, torch.from_numpy(ninv).to(DEV), 1e-3)
+    d = A.akra_plan_describe(p)
+    assert 0 < d["legendre_steps_f32_one_ring"] < d["legendre_steps_f32"]
+    widths = (3, 4, 5, 6, 8) if prec == A.F32 else (1, 2, 4)
+    for PA in widths:
+        A.akra_plan_set_shape(p, prec, R, 1, PA, 1)
+        A.akra_plan_set_adjoint_shape(p, prec, R, PA, 1)
+        y = A.akra_apply_H(p, prec, alm_dev(pairs, prec)).to(torch.complex128).cpu().numpy()
+        for r in range(R):
+            assert rel(y[r], refs[r]) < tol, (prec, PA, r, rel(y[r], refs[r]))
