@@ -88,7 +88,7 @@ __device__ __forceinline__ void leg_adjoint_item_f2(const LegArgs<float> &a, con
     // s_cfd: difference-form coefficients {A', A', (A'-2) + c', (A'-2) - c'} per step, staged only in
     // blocks that hold ring pairs near a pole
     constexpr int NW = NT / 32;
-    constexpr int K = 8 / RG;   // l-steps per reduction block: K * 4 * RG = 32 values per lane
+    constexpr int K = 8 / RG;   // l-steps per block of the step loop (one or two reduction groups)
     static_assert(K >= 2 && K * 4 * RG == 32, "RG must be 1, 2 or 4");
     const int L = a.L, nring = a.nring, nunits = a.nunits, nunit_all = a.nunit_all, R = a.R;
     const long long ntri = a.ntri;
@@ -238,10 +238,12 @@ __device__ __forceinline__ void leg_adjoint_item_f2(const LegArgs<float> &a, con
         const bool all_live = __all_sync(0xffffffffu, live);
         const int nkb = (nl + K - 1) / K;
 
-        // K l-steps (slot of step kk = parity of kk), each step's 4 RG sums stored at once into
-        // this lane's column of the warp's transpose buffer, then the warp reduction
+        // K l-steps (slot of step kk = parity of kk); every KR_ steps the warp sums its lanes' raw
+        // (λ+, λ-)-paired sums through the transpose buffer and forms E and B from the totals
 #define AKRA_F2_ADJ_KBLOCK(GATED, DIFF, SIDE)                                                   \
     for (int kb = 0; kb < nkb; kb++) {                                                          \
+        /* NV_ float2 sums per step and RHS; KR_ steps fill a reduction group of 16 float2 */     \
+        constexpr int NV_ = (SIDE) == 0 ? 4 : 2, KR_ = 16 / (NV_ * RG);                         \
         _Pragma("unroll") for (int kk = 0; kk < K; kk++) {                                      \
             const bool slotA = (kk & 1) == 0;                                                   \
             float2 F[RG][4];                                                                    \
@@ -265,32 +267,13 @@ __device__ __forceinline__ void leg_adjoint_item_f2(const LegArgs<float> &a, con
                             F[rr][j] = f2fma(lam, Q[k][rr][j], F[rr][j]);                       \
                 }                                                                               \
             }                                                                                   \
+            /* this lane's raw sums of the step go to its row of the warp's buffer (row-major, */ \
+            /* 16-byte stores); E and B are formed after the sum over the lanes */                \
             _Pragma("unroll") for (int rr = 0; rr < RG; rr++) {                                 \
-                float *col = &tr[(kk * RG + rr) * 4][lane];                                     \
-                if ((SIDE) == 1) {                                                              \
-                    /* north: E = a + b, B = a - b */                                           \
-                    col[0 * 36] = F[rr][0].x + F[rr][0].y;                                      \
-                    col[1 * 36] = F[rr][1].x + F[rr][1].y;                                      \
-                    col[2 * 36] = F[rr][0].x - F[rr][0].y;                                      \
-                    col[3 * 36] = F[rr][1].x - F[rr][1].y;                                      \
-                } else if ((SIDE) == 2) {                                                       \
-                    /* south: E = s (a + b), B = s (b - a), s = +1 in slot A unless swapped */  \
-                    const float sg = (slotA != swap) ? 1.f : -1.f;                              \
-                    col[0 * 36] = sg * (F[rr][0].x + F[rr][0].y);                               \
-                    col[1 * 36] = sg * (F[rr][1].x + F[rr][1].y);                               \
-                    col[2 * 36] = sg * (F[rr][0].y - F[rr][0].x);                               \
-                    col[3 * 36] = sg * (F[rr][1].y - F[rr][1].x);                               \
-                } else if (slotA) {                                                             \
-                    col[0 * 36] = F[rr][0].x + F[rr][0].y;                                      \
-                    col[1 * 36] = F[rr][1].x + F[rr][1].y;                                      \
-                    col[2 * 36] = F[rr][2].x + F[rr][2].y;                                      \
-                    col[3 * 36] = F[rr][3].x + F[rr][3].y;                                      \
-                } else {                                                                        \
-                    col[0 * 36] = F[rr][2].x - F[rr][2].y;                                      \
-                    col[1 * 36] = F[rr][3].x - F[rr][3].y;                                      \
-                    col[2 * 36] = F[rr][0].x - F[rr][0].y;                                      \
-                    col[3 * 36] = F[rr][1].x - F[rr][1].y;                                      \
-                }                                                                               \
+                float4 *dst = reinterpret_cast<float4 *>(                                       \
+                    &tr[lane][((kk % KR_) * RG + rr) * NV_ * 2]);                               \
+                dst[0] = make_float4(F[rr][0].x, F[rr][0].y, F[rr][1].x, F[rr][1].y);           \
+                if ((SIDE) == 0) dst[1] = make_float4(F[rr][2].x, F[rr][2].y, F[rr][3].x, F[rr][3].y); \
             }                                                                                   \
             const float4 cf = s_cf[kb * K + kk];                                                \
             _Pragma("unroll") for (int k = 0; k < P; k++) {                                     \
@@ -321,16 +304,33 @@ __device__ __forceinline__ void leg_adjoint_item_f2(const LegArgs<float> &a, con
                     }                                                                           \
                 }                                                                               \
             }                                                                                   \
-        }                                                                                       \
-        /* warp transpose through shared memory: lane L's value i went to tr[i][L]; lane j */  \
-        /* now sums row j, i.e. value j over all lanes */                                        \
-        __syncwarp();                                                                           \
-        float sum = 0.f;                                                                        \
-        _Pragma("unroll") for (int i = 0; i < 32; i++) sum += tr[lane][i];                      \
-        __syncwarp();                                                                           \
-        {                                                                                       \
-            const int kk = lane / (4 * RG), rr = (lane / 4) % RG, q = lane & 3;                 \
-            s_red[warp][kb * K + kk][rr][q] = sum;                                              \
+            if ((kk + 1) % KR_ == 0) {                                                          \
+                /* a group of KR_ steps: 16 float2 per lane.  Lane (h, v) sums value v over the */ \
+                /* rows (lanes) 16h .. 16h+15, the two halves are added, and half h forms the */  \
+                /* E part (h = 0) or the B part (h = 1) of that value */                          \
+                __syncwarp();                                                                   \
+                const int h_ = lane >> 4, v_ = lane & 15;                                       \
+                const float2 *c2 = reinterpret_cast<const float2 *>(&tr[16 * h_][0]) + v_;      \
+                float2 sm = make_float2(0.f, 0.f);                                              \
+                _Pragma("unroll") for (int t = 0; t < 16; t++) sm = __fadd2_rn(sm, c2[t * 18]); \
+                sm.x += __shfl_xor_sync(0xffffffffu, sm.x, 16);                                 \
+                sm.y += __shfl_xor_sync(0xffffffffu, sm.y, 16);                                 \
+                __syncwarp();                                                                   \
+                const int pp = v_ / (NV_ * RG), rr = (v_ / NV_) % RG, j = v_ % NV_;             \
+                const int st = kb * K + kk + 1 - KR_ + pp;                                      \
+                const bool sa = (st & 1) == 0;                                                  \
+                if ((SIDE) == 1) {                                                              \
+                    /* north: E = a + b, B = a - b */                                           \
+                    s_red[warp][st][rr][j + 2 * h_] = h_ == 0 ? sm.x + sm.y : sm.x - sm.y;      \
+                } else if ((SIDE) == 2) {                                                       \
+                    /* south: E = s (a + b), B = s (b - a), s = +1 in slot A unless swapped */  \
+                    const float sg = (sa != swap) ? 1.f : -1.f;                                 \
+                    s_red[warp][st][rr][j + 2 * h_] = sg * (h_ == 0 ? sm.x + sm.y : sm.y - sm.x); \
+                } else if (h_ == 0) {                                                           \
+                    /* slot A: (E, B) = F0..F3 summed; slot B: E = F2, F3 and B = F0, F1 differenced */ \
+                    s_red[warp][st][rr][sa ? j : (j ^ 2)] = sa ? sm.x + sm.y : sm.x - sm.y;     \
+                }                                                                               \
+            }                                                                                   \
         }                                                                                       \
     }
 
