@@ -605,19 +605,6 @@ __device__ __forceinline__ void leg_adjoint_item(
                 }                                                                               \
             }                                                                                   \
         }                                                                                       \
-        if ((SIDE) != 0) {                                                                      \
-            /* (a, b) -> (E, B): north E = a + b, B = a - b; south E = s (a + b), B = s (b - a) */ \
-            _Pragma("unroll") for (int kk = 0; kk < K; kk++)                                    \
-                _Pragma("unroll") for (int rr = 0; rr < RG; rr++) {                             \
-                    T *t = ta[kk][rr];                                                          \
-                    const T sg = (SIDE) == 1 ? T(1) : ((((kk & 1) == 0) != swap) ? T(1) : T(-1)); \
-                    const T ar = t[0], ai = t[1], br = t[2], bi = t[3];                         \
-                    t[0] = sg * (ar + br);                                                      \
-                    t[1] = sg * (ai + bi);                                                      \
-                    t[2] = (SIDE) == 1 ? ar - br : sg * (br - ar);                              \
-                    t[3] = (SIDE) == 1 ? ai - bi : sg * (bi - ai);                              \
-                }                                                                               \
-        }                                                                                       \
         /* warp transpose through shared memory: lane L's value i goes to tr[i][L]; lane j */  \
         /* then sums row j, i.e. value j over all lanes */                                       \
         _Pragma("unroll") for (int kk = 0; kk < K; kk++)                                        \
@@ -630,7 +617,20 @@ __device__ __forceinline__ void leg_adjoint_item(
         __syncwarp();                                                                           \
         {                                                                                       \
             const int kk = lane / (4 * RG), rr = (lane / 4) % RG, q = lane & 3;                 \
-            s_red[warp][kb * K + kk][rr][q] = sum;                                              \
+            T val = sum;                                                                        \
+            if ((SIDE) != 0) {                                                                  \
+                /* one ring: the lanes hold the totals of (a.re, a.im, b.re, b.im); with the */  \
+                /* partner's (lane ^ 2): north E = a + b, B = a - b; south E = s (a + b), */     \
+                /* B = s (b - a), s = +1 in slot A unless swapped */                            \
+                const T other = __shfl_xor_sync(0xffffffffu, sum, 2);                           \
+                if ((SIDE) == 1) {                                                              \
+                    val = q < 2 ? sum + other : other - sum;                                    \
+                } else {                                                                        \
+                    const T sg = (((kk & 1) == 0) != swap) ? T(1) : T(-1);                      \
+                    val = sg * (q < 2 ? sum + other : sum - other);                             \
+                }                                                                               \
+            }                                                                                   \
+            s_red[warp][kb * K + kk][rr][q] = val;                                              \
         }                                                                                       \
     }
 
