@@ -74,13 +74,19 @@ def fp32_peak_tflops(sm_count, mhz):
 
 def kernel_source_sha():
     """Short hash of the CUDA-core Legendre kernels' device code (scalar items and the paired
-    FP32 adjoint): a DRAM-traffic capture is only valid for the kernel code it was taken with."""
+    FP32 adjoint): a DRAM-traffic capture is only valid for the kernel code it was taken with.
+    Comments and blank lines are left out, so that an edit of the comments keeps a capture."""
     import hashlib
+    import re
 
     h = hashlib.sha256()
     for f in ("akra_legendre_impl.cuh", "akra_legendre_f32x2.cuh"):
-        with open(os.path.join(ROOT, "paper_2606_06175_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_2606_06175_gb300", "csrc", f), encoding="utf-8") as fh:
+            src = fh.read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", "", src)
+        code = "\n".join(ln.rstrip() for ln in src.splitlines() if ln.strip())
+        h.update(code.encode("utf-8"))
     return h.hexdigest()[:12]
 
 

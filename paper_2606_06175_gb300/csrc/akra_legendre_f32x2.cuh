@@ -6,8 +6,8 @@
 //   * recurrence: T = (A'x + c', A'x - c') is one paired FMA, the update another (2 issues per
 //     pair-step instead of 4);
 //   * contraction: the ring-pair data are paired across the spins, (X+, X-), and
-//     (Σ λ+ X+, Σ λ- X-) += (λ+, λ-)·(X+, X-), the two halves added once per step after the
-//     sum over the thread's pairs: 4 paired FMAs per pair-step and RHS instead of 8.
+//     (Σ λ+ X+, Σ λ- X-) += (λ+, λ-)·(X+, X-), the two halves added once per value after the
+//     warp's sum over its lanes: 4 paired FMAs per pair-step and RHS instead of 8.
 // The adjoint, which also spends issue slots on its warp reduction, gains from the freed
 // slots (12.77 -> 12.08 ms at Nside 2048 / lmax 4096); the synthesis, bound by the FMA pipe
 // itself, does not and keeps the scalar form.  The recurrences round every product and sum as
