@@ -395,8 +395,9 @@ k_leg_synth_queue(const LegArgs<T> *__restrict__ insts, const int4 *__restrict__
     }
 }
 
-// row stride (in elements) of the per-warp transpose buffer: conflict-free scalar stores of
-// one value per lane and 16-byte row loads (36 floats, 34 doubles)
+// row stride (in elements) of the per-warp transpose buffer, conflict-free for both uses: the
+// FP64 item stores one scalar per lane into a column and loads 16-byte rows (34 doubles); the
+// FP32 paired item stores 16-byte rows and loads 8-byte columns (36 floats)
 template <typename T> struct TrStride;
 template <> struct TrStride<float> { static constexpr int v = 36; };
 template <> struct TrStride<double> { static constexpr int v = 34; };
